@@ -1,0 +1,125 @@
+"""Seeded synthetic workloads shared by the tests, the benchmark and the oracle.
+
+This module only *describes* problems (mesh sizes, degree, which geometry map
+and which diffusion coefficient, with their parameters) and draws seeded
+random vectors.  It holds none of the method's arithmetic: the oracle
+(``oracle/``) and the CUDA library (``paper_1904_06971_gb300``) each turn a
+``Problem`` into their own input structures.
+
+Workload recipe (stand-ins for the paper's Poisson experiments, Sec. 7.3):
+smooth, non-affine single-patch maps of the unit square / cube onto itself,
+x_a = xi_a + amp * prod_j sin(pi xi_j), and smooth diffusion coefficients
+evaluated at the physical point.  Right-hand sides are discrete load vectors
+f_i ~ U[-1, 1]; SpMV inputs are x_i ~ N(0, 1); all drawn from
+``numpy.random.default_rng(seed)`` with seed 0 unless stated.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, replace
+from typing import Optional, Tuple
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Problem:
+    dim: int
+    p: int
+    n_el: Tuple[int, ...]
+    map_kind: str = "identity"          # identity | affine | sinprod
+    map_amp: float = 0.0
+    affine: Optional[Tuple[float, ...]] = None   # 3x3 row-major matrix then 3-vector offset
+    kappa_kind: str = "const"           # const | sin2d | expsin3d | poly
+    kappa_a: float = 1.0
+    kappa_b: float = 0.0
+    kappa_deg: int = 0
+    kappa_poly: Optional[Tuple[float, ...]] = None
+
+    @property
+    def m(self) -> Tuple[int, ...]:
+        return tuple(e + self.p for e in self.n_el)
+
+    @property
+    def N(self) -> int:
+        return int(np.prod(self.m))
+
+    @property
+    def S(self) -> int:
+        return (2 * self.p + 1) ** self.dim
+
+    @property
+    def nnz(self) -> int:
+        """Structural nonzeros of the banded tensor pattern: prod_d (m_d(2p+1) - p(p+1))."""
+        return int(np.prod([mm * (2 * self.p + 1) - self.p * (self.p + 1) for mm in self.m]))
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    problem: Problem
+    M: int
+    q: int
+    dtype: str          # "f64" or "f32": storage type of the matrix values
+    seed: int = 0
+
+
+# 2D: unit square mapped by x = xi + 0.05 sin(pi xi) sin(pi eta) (both components),
+# kappa = 1 + 0.5 sin(2 pi x) sin(2 pi y); p = 2, 32 x 32 elements; M = 4, q = 3.
+CFG_2D_P2 = Workload(
+    "2d_p2_32x32_M4_q3",
+    Problem(dim=2, p=2, n_el=(32, 32), map_kind="sinprod", map_amp=0.05,
+            kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.5),
+    M=4, q=3, dtype="f64")
+
+# 3D: x_i = xi_i + 0.03 prod_j sin(pi xi_j), kappa = exp(0.5 sin(2 pi x) cos(2 pi y) sin(2 pi z));
+# p = 3, 64^3 elements; M = 8, q = 3; FP64 values.
+CFG_3D_P3 = Workload(
+    "3d_p3_64cube_M8_q3",
+    Problem(dim=3, p=3, n_el=(64, 64, 64), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="expsin3d", kappa_b=0.5),
+    M=8, q=3, dtype="f64")
+
+# 3D precision case: same map family, p = 4, 96^3 elements; M = 8, q = 3; FP32 values.
+CFG_3D_P4 = Workload(
+    "3d_p4_96cube_M8_q3_f32",
+    Problem(dim=3, p=4, n_el=(96, 96, 96), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="expsin3d", kappa_b=0.5),
+    M=8, q=3, dtype="f32")
+
+WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4)}
+
+
+def scaled(w: Workload, n_el: Tuple[int, ...], M: Optional[int] = None, p: Optional[int] = None) -> Workload:
+    """Same map / coefficient family at another mesh size (small parity cases)."""
+    prob = replace(w.problem, n_el=tuple(n_el), p=(p if p is not None else w.problem.p))
+    return replace(w, name=f"{w.name}@{'x'.join(map(str, n_el))}", problem=prob,
+                   M=(M if M is not None else w.M))
+
+
+def rhs_vector(N: int, seed: int = 0) -> np.ndarray:
+    """Discrete load vector f_i ~ U[-1, 1]."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=N)
+
+
+def normal_vector(N: int, seed: int = 0) -> np.ndarray:
+    """SpMV input x_i ~ N(0, 1)."""
+    return np.random.default_rng(seed).standard_normal(N)
+
+
+def sample_rows(N: int, k: int, seed: int = 0) -> np.ndarray:
+    """k distinct row indices, sorted (for sampled parity checks at full size)."""
+    rng = np.random.default_rng(seed)
+    k = min(k, N)
+    return np.sort(rng.choice(N, size=k, replace=False)).astype(np.int64)
+
+
+def random_problem(rng: np.random.Generator, dim: int, p: int, n_el_range=(5, 12),
+                   amp_max: float = 0.05) -> Problem:
+    """A small random sine-product patch (used by the randomized parity tests)."""
+    n_el = tuple(int(rng.integers(n_el_range[0], n_el_range[1] + 1)) for _ in range(dim))
+    amp = float(rng.uniform(0.0, amp_max))
+    if dim == 2:
+        return Problem(dim=2, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp,
+                       kappa_kind="sin2d", kappa_a=1.0, kappa_b=float(rng.uniform(0, 0.5)))
+    return Problem(dim=3, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp,
+                   kappa_kind="expsin3d", kappa_b=float(rng.uniform(0, 0.5)))
