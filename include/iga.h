@@ -1,0 +1,176 @@
+/*
+ * iga.h -- C ABI of libiga: GPU (sm_103a) assembly of exact and surrogate
+ * stiffness matrices for isogeometric analysis on one mapped tensor-product
+ * B-spline patch, and the stencil SpMV with the result.
+ *
+ * The operator is the variable-coefficient diffusion form pulled back to the
+ * parametric domain (0,1)^n (Drzisga, Keith & Wohlmuth, "The surrogate matrix
+ * methodology: low-cost assembly for isogeometric analysis", Sec. 3.2,
+ * eq. BilinearFormPoissonTensor):
+ *
+ *   A_ij = int grad B_i^T K grad B_j,  K = kappa(phi) |det Dphi| Dphi^{-1} Dphi^{-T},
+ *
+ * with the open uniform B-spline basis of Sec. 2.2 (degree p, n_el elements
+ * and m = n_el + p functions per direction, colexicographic global numbering
+ * i = i_0 + m_0 (i_1 + m_1 i_2), 0-based) and (p+1)-point Gauss-Legendre
+ * quadrature on every element.
+ *
+ * Matrix storage ("stencil-ELL", index free): values[s * N + i] holds
+ * A_{i, i + delta_s} where the slot s = sum_d (delta_d + p)(2p+1)^d enumerates
+ * the (2p+1)^n offsets delta in {-p..p}^n colexicographically (Sec. 3.2: the
+ * set D of relevant translations).  Slots whose column leaves the index
+ * range hold 0.  The centre slot (S-1)/2 is the diagonal; slot s > (S-1)/2
+ * means j > i, and slot S-1-s is the transposed offset.
+ *
+ * Conventions for every call:
+ *   - return value: IGA_OK (0) or a negative IGA_E* code; iga_last_error()
+ *     gives a message for the calling thread.  No call traps the device or
+ *     throws across the ABI.
+ *   - stream: a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it; results are valid once it has been
+ *     synchronised.  Host-side argument checks happen before anything is
+ *     enqueued.
+ *   - device memory: the library allocates the matrix values and its scratch
+ *     from a library-owned stream-ordered memory pool on the current device;
+ *     the pool keeps released blocks for reuse.  Caller pointers (x, y) are
+ *     never freed by the library.
+ *   - the matrix is the full pure-Neumann matrix; Dirichlet elimination is
+ *     the solver's business (Sec. 6, Remark with eq. BlockSystem).
+ */
+#ifndef IGA_H
+#define IGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define IGA_OK            0
+#define IGA_EINVAL       (-1)   /* bad argument (null pointer, size, kind) */
+#define IGA_ENOMEM       (-2)   /* device allocation failed */
+#define IGA_ECUDA        (-3)   /* a CUDA runtime call or launch failed */
+#define IGA_EUNSUPPORTED (-4)   /* valid request outside what is built (p, n, q range) */
+#define IGA_ETIMEOUT     (-5)   /* a bounded device wait gave up */
+
+/* storage type of matrix values and of the SpMV vectors */
+#define IGA_F64 0
+#define IGA_F32 1
+
+/* geometry maps phi: (0,1)^n -> R^n */
+#define IGA_MAP_IDENTITY 0      /* x = xi */
+#define IGA_MAP_AFFINE   1      /* x = A xi + b; affine[0..8] = A row-major (3x3; 2-D uses the top-left 2x2), affine[9..11] = b */
+#define IGA_MAP_SINPROD  2      /* x_a = xi_a + amp * prod_j sin(pi xi_j) */
+
+/* diffusion coefficients kappa(x), evaluated at the physical point x = phi(xi) */
+#define IGA_KAPPA_CONST    0    /* a */
+#define IGA_KAPPA_SIN2D    1    /* a + b sin(2 pi x) sin(2 pi y) */
+#define IGA_KAPPA_EXPSIN3D 2    /* exp(b sin(2 pi x) cos(2 pi y) sin(2 pi z)) */
+#define IGA_KAPPA_POLY     3    /* sum_{a,b,c <= deg} poly[a + (deg+1)(b + (deg+1)c)] x^a y^b z^c, deg <= 3 */
+
+typedef struct {
+    int32_t dim;        /* n: 2 or 3 */
+    int32_t n_el[3];    /* elements per direction (entries beyond dim ignored); n_el >= p + 1 (m >= 2p+1, Sec. 2.2) */
+} iga_patch_t;
+
+typedef struct {
+    int32_t kind;       /* IGA_MAP_* */
+    double amp;         /* IGA_MAP_SINPROD amplitude */
+    double affine[12];  /* IGA_MAP_AFFINE coefficients */
+} iga_map_t;
+
+typedef struct {
+    int32_t kind;       /* IGA_KAPPA_* */
+    int32_t deg;        /* IGA_KAPPA_POLY degree per direction (0..3) */
+    double a, b;        /* constants of the closed forms above */
+    double poly[64];    /* IGA_KAPPA_POLY coefficients */
+} iga_kappa_t;
+
+typedef struct iga_matrix* iga_matrix_t;   /* opaque; owns device storage */
+
+/*
+ * Exact assembly (Sec. 6: the matrix A every entry of which comes from
+ * quadrature; eq. ChangeOfVars).  Every row is computed by sum-factorised
+ * Gauss quadrature on the GPU.
+ *   patch, map, kappa: host pointers, read during the call only.
+ *   p: degree 1..5.  dtype: IGA_F64 or IGA_F32 (quadrature is FP64 either way).
+ *   A: in/out.  *A == NULL: a new matrix is created.  *A != NULL: a matrix
+ *   from an earlier call with the same patch, p and dtype, whose storage is
+ *   reused (its previous values are overwritten); otherwise IGA_EINVAL.
+ */
+int iga_assemble_exact(const iga_patch_t* patch, int p, const iga_map_t* map,
+                       const iga_kappa_t* kappa, int dtype, void* stream,
+                       iga_matrix_t* A);
+
+/*
+ * Surrogate assembly, eq. DefinitionOfSurrogateMatrixSymmetricKernel
+ * (Sec. 5.3) with the sampling of Sec. 6:
+ *   - Omega~ (Sec. 4) is the index box [2p, m-2p-1] per direction;
+ *   - rows with an index outside it ("frame" rows) are exact;
+ *   - samples: every M-th index of the box from its first index, plus its
+ *     last index; the stencil values Phi_delta at the sample rows are exact;
+ *   - per upper offset delta, a degree-q tensor-product B-spline interpolant
+ *     through the samples (not-a-knot knots at the sample indices, odd q, or
+ *     at their midpoints, even q; degree lowered to n_s - 1 with fewer than
+ *     q + 1 samples) gives A~_ij for i < j with i, j in Omega~;
+ *   - A~_ij for i > j in Omega~ is the copy A~_ji; every other off-diagonal
+ *     entry is exact; every diagonal entry is minus its row's off-diagonal sum.
+ *   M >= 1 (M = 1 reproduces the exact matrix), 0 <= q <= 7.  Other arguments
+ *   as for iga_assemble_exact.
+ */
+int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map,
+                           const iga_kappa_t* kappa, int M, int q, int dtype,
+                           void* stream, iga_matrix_t* A);
+
+/*
+ * y = A x (eq. DiscreteVariationalProblems), stencil SpMV.  x and y are
+ * caller-owned DEVICE arrays of N elements of the matrix dtype (double for
+ * IGA_F64, float for IGA_F32); x and y must not overlap.
+ */
+int iga_apply(iga_matrix_t A, const void* x, void* y, void* stream);
+
+/*
+ * y = A x with HOST arrays (pinned or pageable): the call copies x to the
+ * device, runs the SpMV and copies y back on `stream`, and returns after the
+ * stream has been synchronised.  Uses a library-owned device staging buffer.
+ */
+int iga_apply_host(iga_matrix_t A, const void* x_host, void* y_host, void* stream);
+
+/* Sizes: N dofs, S slots, structural nonzeros prod_d(m_d(2p+1) - p(p+1)), dtype. Any out pointer may be NULL. */
+int iga_matrix_info(iga_matrix_t A, int64_t* N, int32_t* S, int64_t* nnz, int32_t* dtype);
+
+/* Device pointer to the values array [S][N] (owned by A; valid until destroy or re-assembly). */
+int iga_matrix_values(iga_matrix_t A, const void** values);
+
+/* Copy all S*N values to dst (host if dst_on_host != 0, else device); synchronises `stream`. */
+int iga_matrix_copy_values(iga_matrix_t A, void* dst, int dst_on_host, void* stream);
+
+/* Release A and its device storage (stream-ordered on the stream of its last assembly). NULL is a no-op. */
+int iga_matrix_destroy(iga_matrix_t A);
+
+/*
+ * Counters for benchmarking: number of kernels this library launched in the
+ * calling process since start (monotone), and per-kernel device time.
+ * iga_profile_enable(1) makes every later launch record a pair of CUDA
+ * events on its stream; iga_profile_read() synchronises those events and
+ * returns, for kernel id k < n, the number of launches and total
+ * milliseconds, then clears them.  Names come from iga_kernel_name(k).
+ */
+int64_t iga_launch_count(void);
+int iga_profile_enable(int on);
+int iga_profile_read(int n, int64_t* launches, double* ms);
+int iga_num_kernels(void);
+const char* iga_kernel_name(int k);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* iga_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int iga_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGA_H */

@@ -1,0 +1,244 @@
+"""Python binding of libiga: GPU exact / surrogate IGA stiffness assembly and stencil SpMV.
+
+Thin ctypes marshalling over the C ABI in ``include/iga.h``; every step of the
+computation runs in the CUDA kernels of ``csrc/``.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the in-tree ``libiga.so``
+cannot be built or loaded, every call raises.
+
+Problems are described by any object with the attributes ``dim, p, n_el,
+map_kind ('identity'|'affine'|'sinprod'), map_amp, affine, kappa_kind
+('const'|'sin2d'|'expsin3d'|'poly'), kappa_a, kappa_b, kappa_deg,
+kappa_poly``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "load", "launch_count",
+           "profile_enable", "profile_read", "kernel_names", "F64", "F32"]
+
+F64, F32 = 0, 1
+_MAP = {"identity": 0, "affine": 1, "sinprod": 2}
+_KAPPA = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3}
+_lock = threading.Lock()
+_lib = None
+
+
+class IgaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libiga error {code}: {msg}")
+        self.code = code
+
+
+class Patch(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_el", ctypes.c_int32 * 3)]
+
+
+class Map(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("amp", ctypes.c_double), ("affine", ctypes.c_double * 12)]
+
+
+class Kappa(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("deg", ctypes.c_int32), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("poly", ctypes.c_double * 64)]
+
+
+def load():
+    """Build (if stale) and load the in-tree libiga.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        so = _build.build()
+        if not os.path.exists(so):
+            raise ImportError(f"libiga.so missing at {so}")
+        L = ctypes.CDLL(so)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        H = ctypes.c_void_p
+        L.iga_assemble_exact.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                         ctypes.POINTER(Kappa), ctypes.c_int, vp, ctypes.POINTER(H)]
+        L.iga_assemble_surrogate.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                             ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             vp, ctypes.POINTER(H)]
+        L.iga_apply.argtypes = [H, vp, vp, vp]
+        L.iga_apply_host.argtypes = [H, vp, vp, vp]
+        L.iga_matrix_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i32)]
+        L.iga_matrix_values.argtypes = [H, ctypes.POINTER(vp)]
+        L.iga_matrix_copy_values.argtypes = [H, vp, ctypes.c_int, vp]
+        L.iga_matrix_destroy.argtypes = [H]
+        L.iga_launch_count.restype = i64
+        L.iga_profile_enable.argtypes = [ctypes.c_int]
+        L.iga_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+        L.iga_kernel_name.restype = ctypes.c_char_p
+        L.iga_kernel_name.argtypes = [ctypes.c_int]
+        L.iga_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise IgaError(rc, load().iga_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _structs(prob):
+    pt = Patch()
+    pt.dim = int(prob.dim)
+    for d in range(3):
+        pt.n_el[d] = int(prob.n_el[d]) if d < prob.dim else 1
+    mp = Map()
+    mp.kind = _MAP[prob.map_kind]
+    mp.amp = float(getattr(prob, "map_amp", 0.0))
+    aff = getattr(prob, "affine", None) or (1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0)
+    for k in range(12):
+        mp.affine[k] = float(aff[k])
+    kp = Kappa()
+    kp.kind = _KAPPA[prob.kappa_kind]
+    kp.deg = int(getattr(prob, "kappa_deg", 0))
+    kp.a = float(getattr(prob, "kappa_a", 1.0))
+    kp.b = float(getattr(prob, "kappa_b", 0.0))
+    poly = getattr(prob, "kappa_poly", None) or ()
+    for k in range(64):
+        kp.poly[k] = float(poly[k]) if k < len(poly) else 0.0
+    return pt, mp, kp
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in ("f64", F64, np.float64):
+        return F64
+    if dtype in ("f32", F32, np.float32):
+        return F32
+    raise ValueError(f"dtype must be 'f64' or 'f32', got {dtype!r}")
+
+
+class Matrix:
+    """A stencil-ELL matrix owned by libiga (values [S][N] on the device)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        N, S, nnz, dt = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(load().iga_matrix_info(self._h, ctypes.byref(N), ctypes.byref(S), ctypes.byref(nnz), ctypes.byref(dt)))
+        self.N, self.S, self.nnz, self.dtype_code = N.value, S.value, nnz.value, dt.value
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def np_dtype(self):
+        return np.float32 if self.dtype_code == F32 else np.float64
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float32 if self.dtype_code == F32 else torch.float64
+
+    def apply(self, x, y=None, stream=None):
+        """y = A x for device tensors x (and optional y) of the matrix dtype."""
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == self.torch_dtype and x.numel() == self.N
+                and x.is_contiguous()):
+            raise ValueError("x must be a contiguous CUDA tensor of N elements of the matrix dtype")
+        if y is None:
+            y = torch.empty_like(x)
+        _check(load().iga_apply(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                ctypes.c_void_p(_stream_ptr(stream))))
+        return y
+
+    def apply_host(self, x: np.ndarray, y: Optional[np.ndarray] = None, stream=None) -> np.ndarray:
+        """y = A x with host arrays (copies inside the call; returns after the stream syncs)."""
+        x = np.ascontiguousarray(x, dtype=self.np_dtype)
+        if y is None:
+            y = np.empty_like(x)
+        _check(load().iga_apply_host(self._h, ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(y.ctypes.data),
+                                     ctypes.c_void_p(_stream_ptr(stream))))
+        return y
+
+    def values(self, stream=None):
+        """A device copy of the values as a torch tensor [S, N]."""
+        import torch
+        out = torch.empty((self.S, self.N), dtype=self.torch_dtype, device="cuda")
+        _check(load().iga_matrix_copy_values(self._h, ctypes.c_void_p(out.data_ptr()), 0,
+                                             ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def values_host(self, stream=None) -> np.ndarray:
+        out = np.empty((self.S, self.N), dtype=self.np_dtype)
+        _check(load().iga_matrix_copy_values(self._h, ctypes.c_void_p(out.ctypes.data), 1,
+                                             ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check(load().iga_matrix_values(self._h, ctypes.byref(p)))
+        return p.value
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            _check(load().iga_matrix_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def assemble_exact(prob, dtype="f64", stream=None, out: Optional[Matrix] = None) -> Matrix:
+    """Exact Gauss-quadrature stiffness matrix on the GPU (iga_assemble_exact)."""
+    pt, mp, kp = _structs(prob)
+    h = ctypes.c_void_p(out.handle.value if out is not None else None)
+    _check(load().iga_assemble_exact(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
+                                     _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return out if out is not None else Matrix(h.value)
+
+
+def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Optional[Matrix] = None) -> Matrix:
+    """Symmetric kernel-preserving surrogate stiffness matrix on the GPU (iga_assemble_surrogate)."""
+    pt, mp, kp = _structs(prob)
+    h = ctypes.c_void_p(out.handle.value if out is not None else None)
+    _check(load().iga_assemble_surrogate(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
+                                         int(M), int(q), _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)),
+                                         ctypes.byref(h)))
+    return out if out is not None else Matrix(h.value)
+
+
+def launch_count() -> int:
+    return int(load().iga_launch_count())
+
+
+def kernel_names():
+    L = load()
+    return [L.iga_kernel_name(k).decode() for k in range(L.iga_num_kernels())]
+
+
+def profile_enable(on: bool = True):
+    _check(load().iga_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """{kernel name: (launches, total ms)} since the last read (synchronises the recorded events)."""
+    L = load()
+    n = L.iga_num_kernels()
+    la = (ctypes.c_int64 * n)()
+    ms = (ctypes.c_double * n)()
+    _check(L.iga_profile_read(n, la, ms))
+    return {L.iga_kernel_name(k).decode(): (int(la[k]), float(ms[k])) for k in range(n)}

@@ -1,0 +1,548 @@
+// libiga C ABI (include/iga.h): argument checks, planning of the quadrature
+// boxes and the sampling lattice, scratch layout, and the launch sequence.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "iga_internal.cuh"
+
+using namespace iga;
+
+struct iga_matrix {
+    int dim, p, dtype;
+    int n_el[3], m[3];
+    int64_t N, nnz;
+    int S;
+    void* values;             // [S][N], cudaMalloc'd
+    size_t bytes;
+    int device;
+};
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? IGA_ENOMEM : IGA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---- launch counting and optional per-kernel event timing ----
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_profile{0};
+std::mutex g_prof_mu;
+struct Pending { int kid; cudaEvent_t a, b; };
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_events;
+thread_local cudaEvent_t t_begin = nullptr;
+
+const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
+                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv"};
+
+cudaEvent_t take_event()
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_events.empty()) {
+        cudaEvent_t e = g_events.back();
+        g_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// ---- library-owned stream-ordered pool per device (keeps freed blocks) ----
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[128] = {};
+
+cudaError_t device_pool(int dev, cudaMemPool_t* out)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&g_pools[dev], &props);
+        if (e != cudaSuccess) { g_pools[dev] = nullptr; return e; }
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t align_up(int64_t a, int64_t b) { return div_up(a, b) * b; }
+
+int check_geometry(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, Geo& g)
+{
+    if (!patch || !map || !kappa) return fail(IGA_EINVAL, "patch, map and kappa must be non-null");
+    if (patch->dim != 2 && patch->dim != 3) return fail(IGA_EUNSUPPORTED, "dim must be 2 or 3 (got %d)", patch->dim);
+    if (p < 1 || p > kMaxP) return fail(IGA_EUNSUPPORTED, "degree p must be in 1..%d (got %d)", kMaxP, p);
+    memset(&g, 0, sizeof(g));
+    g.dim = patch->dim;
+    g.p = p;
+    for (int d = 0; d < 3; ++d) {
+        if (d < g.dim) {
+            if (patch->n_el[d] < p + 1)
+                return fail(IGA_EINVAL, "n_el[%d] = %d: need at least p + 1 = %d elements (m >= 2p + 1)", d, patch->n_el[d], p + 1);
+            if (patch->n_el[d] > (1 << 22)) return fail(IGA_EINVAL, "n_el[%d] too large", d);
+            g.n_el[d] = patch->n_el[d];
+            g.m[d] = patch->n_el[d] + p;
+        } else {
+            g.n_el[d] = 1;
+            g.m[d] = 1;
+        }
+    }
+    if (map->kind != IGA_MAP_IDENTITY && map->kind != IGA_MAP_AFFINE && map->kind != IGA_MAP_SINPROD)
+        return fail(IGA_EINVAL, "unknown map kind %d", map->kind);
+    g.map_kind = map->kind;
+    g.amp = map->amp;
+    for (int k = 0; k < 12; ++k) g.aff[k] = map->affine[k];
+    switch (kappa->kind) {
+    case IGA_KAPPA_CONST: case IGA_KAPPA_SIN2D: break;
+    case IGA_KAPPA_EXPSIN3D:
+        if (g.dim != 3) return fail(IGA_EINVAL, "IGA_KAPPA_EXPSIN3D needs dim 3");
+        break;
+    case IGA_KAPPA_POLY:
+        if (kappa->deg < 0 || kappa->deg > 3) return fail(IGA_EINVAL, "polynomial kappa degree must be 0..3");
+        break;
+    default:
+        return fail(IGA_EINVAL, "unknown kappa kind %d", kappa->kind);
+    }
+    g.kappa_kind = kappa->kind;
+    g.kappa_deg = kappa->deg;
+    g.ka = kappa->a;
+    g.kb = kappa->b;
+    for (int k = 0; k < 64; ++k) g.poly[k] = kappa->poly[k];
+    return IGA_OK;
+}
+
+void make_box(const Geo& g, Box& b, const int lo[3], const int R[3])
+{
+    memset(&b, 0, sizeof(b));
+    for (int d = 0; d < 3; ++d) {
+        if (d < g.dim) {
+            b.rlo[d] = lo[d];
+            b.R[d] = R[d];
+            b.elo[d] = std::max(0, lo[d] - g.p);
+            const int ehi = std::min(g.n_el[d] - 1, lo[d] + R[d] - 1);
+            b.E[d] = ehi - b.elo[d] + 1;
+        } else {
+            b.rlo[d] = 0; b.R[d] = 1; b.elo[d] = 0; b.E[d] = 1;
+        }
+    }
+}
+
+struct Layout {
+    int64_t total = 0;
+    int64_t take(int64_t n_doubles) { int64_t o = total; total += align_up(std::max<int64_t>(n_doubles, 1), 32); return o; }
+};
+
+int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
+             int M, int q, int dtype, void* stream_v, iga_matrix_t* out)
+{
+    t_err.clear();
+    Geo g;
+    int rc = check_geometry(patch, p, map, kappa, g);
+    if (rc) return rc;
+    if (dtype != IGA_F64 && dtype != IGA_F32) return fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
+    if (!out) return fail(IGA_EINVAL, "output handle pointer is null");
+    if (surrogate) {
+        if (M < 1) return fail(IGA_EINVAL, "sampling parameter M must be >= 1 (got %d)", M);
+        if (q < 0 || q > kMaxQ) return fail(IGA_EUNSUPPORTED, "interpolation degree q must be in 0..%d (got %d)", kMaxQ, q);
+    }
+    const int dim = g.dim, W = 2 * p + 1, Q = p + 1, TT = Q * Q;
+    const int S = (dim == 3) ? W * W * W : W * W;
+    int64_t N = 1, nnz = 1;
+    for (int d = 0; d < dim; ++d) {
+        N *= g.m[d];
+        nnz *= (int64_t)g.m[d] * W - (int64_t)p * (p + 1);
+    }
+    const size_t esz = (dtype == IGA_F32) ? 4 : 8;
+    cudaStream_t st = (cudaStream_t)stream_v;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+
+    iga_matrix* A = *out;
+    if (A) {
+        bool same = A->dim == dim && A->p == p && A->dtype == dtype && A->device == dev;
+        for (int d = 0; d < dim; ++d) same = same && A->n_el[d] == g.n_el[d];
+        if (!same) return fail(IGA_EINVAL, "matrix handle passed for reuse has another patch, degree, dtype or device");
+    }
+
+    // ---------------- plan: boxes and sampling lattice ----------------
+    BoxSet bs;
+    memset(&bs, 0, sizeof(bs));
+    SplinePlan sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.dim = dim; sp.q = q; sp.S = S; sp.c = (S - 1) / 2;
+    int empty = 0;
+    bool do_spline = false;
+    std::vector<Box> boxes;
+    if (surrogate) {
+        int k0 = 2 * p, k1[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            k1[d] = g.m[d] - 2 * p - 1;
+            if (k1[d] < k0) empty = 1;
+        }
+        if (!empty) {
+            for (int d = 0; d < dim; ++d) {
+                sp.k0[d] = k0;
+                sp.L[d] = k1[d] - k0 + 1;
+                const int span = k1[d] - k0;
+                sp.ns[d] = span / M + 1 + ((span % M) ? 1 : 0);
+                sp.qe[d] = std::min(q, sp.ns[d] - 1);
+                if (sp.ns[d] > 4096) return fail(IGA_EUNSUPPORTED, "more than 4096 samples per direction");
+                bs.ns[d] = sp.ns[d];
+                bs.k0[d] = k0;
+                bs.k1[d] = k1[d];
+            }
+            for (int d = dim; d < 3; ++d) { bs.ns[d] = 1; sp.ns[d] = 1; sp.L[d] = 1; }
+            bs.M = M;
+            sp.n_samples = 1;
+            for (int d = 0; d < dim; ++d) sp.n_samples *= sp.ns[d];
+            bs.n_samples = sp.n_samples;
+            do_spline = true;
+            // frame = rows with an index outside [k0, k1], as disjoint slabs
+            Box b;
+            const int full = 0;
+            (void)full;
+            if (dim == 3) {
+                int lo[3], R[3];
+                // slabs normal to direction 2
+                lo[0] = 0; R[0] = g.m[0]; lo[1] = 0; R[1] = g.m[1];
+                lo[2] = 0; R[2] = k0; make_box(g, b, lo, R); boxes.push_back(b);
+                lo[2] = k1[2] + 1; R[2] = g.m[2] - 1 - k1[2]; make_box(g, b, lo, R); boxes.push_back(b);
+                // normal to direction 1, inside the box in direction 2
+                lo[2] = k0; R[2] = k1[2] - k0 + 1;
+                lo[1] = 0; R[1] = k0; make_box(g, b, lo, R); boxes.push_back(b);
+                lo[1] = k1[1] + 1; R[1] = g.m[1] - 1 - k1[1]; make_box(g, b, lo, R); boxes.push_back(b);
+                // normal to direction 0
+                lo[1] = k0; R[1] = k1[1] - k0 + 1;
+                lo[0] = 0; R[0] = k0; make_box(g, b, lo, R); boxes.push_back(b);
+                lo[0] = k1[0] + 1; R[0] = g.m[0] - 1 - k1[0]; make_box(g, b, lo, R); boxes.push_back(b);
+            } else {
+                int lo[3] = {0, 0, 0}, R[3] = {g.m[0], k0, 1};
+                make_box(g, b, lo, R); boxes.push_back(b);
+                lo[1] = k1[1] + 1; R[1] = g.m[1] - 1 - k1[1]; make_box(g, b, lo, R); boxes.push_back(b);
+                lo[1] = k0; R[1] = k1[1] - k0 + 1;
+                lo[0] = 0; R[0] = k0; make_box(g, b, lo, R); boxes.push_back(b);
+                lo[0] = k1[0] + 1; R[0] = g.m[0] - 1 - k1[0]; make_box(g, b, lo, R); boxes.push_back(b);
+            }
+        }
+    }
+    if (!surrogate || empty) {
+        Box b;
+        int lo[3] = {0, 0, 0}, R[3] = {g.m[0], g.m[1], g.m[2]};
+        make_box(g, b, lo, R);
+        boxes.push_back(b);
+    }
+    if ((int)boxes.size() > kMaxBoxes) return fail(IGA_EINVAL, "internal: too many boxes");
+
+    // ---------------- scratch layout ----------------
+    Layout lay;
+    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3];
+    for (int d = 0; d < 3; ++d) {
+        const int64_t G = (d < dim) ? (int64_t)g.n_el[d] * Q : 1;
+        const int64_t nX = (d < dim) ? (int64_t)4 * g.m[d] * W * TT : 1;
+        o_gx[d] = lay.take(G); o_sx[d] = lay.take(G); o_cx[d] = lay.take(G); o_wq[d] = lay.take(G);
+        o_bv[d] = lay.take(G * Q); o_bd[d] = lay.take(G * Q); o_X[d] = lay.take(nX);
+    }
+    int64_t nblk[4] = {0, 0, 0, 0};
+    bs.nb = (int)boxes.size();
+    for (int k = 0; k < bs.nb; ++k) {
+        Box& b = boxes[k];
+        b.out_kind = 0;
+        b.c_off = lay.take(box_coef_len(dim, p, b));
+        b.t1_off = lay.take(box_t1_len(dim, p, b));
+        b.t2_off = lay.take(box_t2_len(dim, p, b));
+        for (int s = 0; s < 4; ++s) {
+            b.blk[s] = nblk[s];
+            nblk[s] += div_up(box_items(dim, p, b, s), kBlock);
+        }
+        bs.box[k] = b;
+    }
+    int64_t o_samples = 0, o_lu[3] = {0, 0, 0}, o_eval[3] = {0, 0, 0}, o_partial = 0, o_ints = 0;
+    if (do_spline) {
+        Box sbx;                         // shape of every sample box
+        int lo[3] = {2 * p, 2 * p, 2 * p}, R[3] = {1, 1, 1};
+        make_box(g, sbx, lo, R);
+        bs.s_c_len = align_up(box_coef_len(dim, p, sbx), 32);
+        bs.s_t1_len = align_up(box_t1_len(dim, p, sbx), 32);
+        bs.s_t2_len = align_up(box_t2_len(dim, p, sbx), 32);
+        bs.s_c_off = lay.take(bs.s_c_len * sp.n_samples);
+        bs.s_t1_off = lay.take(bs.s_t1_len * sp.n_samples);
+        bs.s_t2_off = lay.take(bs.s_t2_len * sp.n_samples);
+        for (int s = 0; s < 4; ++s) {
+            bs.blk_s[s] = nblk[s];
+            bs.bper_s[s] = div_up(box_items(dim, p, sbx, s), kBlock);
+            nblk[s] += bs.bper_s[s] * sp.n_samples;
+        }
+        o_samples = lay.take((int64_t)S * sp.n_samples);
+        for (int d = 0; d < dim; ++d) {
+            o_lu[d] = lay.take((int64_t)sp.ns[d] * sp.ns[d]);
+            o_eval[d] = lay.take((int64_t)sp.L[d] * (sp.qe[d] + 1));
+        }
+        const int64_t S_up = S - 1 - sp.c;
+        o_partial = lay.take(S_up * (dim == 3 ? sp.L[2] : 1) * (int64_t)sp.L[1] * sp.ns[0]);
+        int64_t nints = 8;
+        for (int d = 0; d < dim; ++d) nints += sp.L[d] + 8;
+        o_ints = lay.take(div_up(nints, 2));
+    }
+    for (int s = 0; s < 4; ++s)
+        if (nblk[s] > 0x7fffffffLL) return fail(IGA_EUNSUPPORTED, "problem too large for one launch");
+
+    // ---------------- storage ----------------
+    bool created = false;
+    if (!A) {
+        A = new (std::nothrow) iga_matrix;
+        if (!A) return fail(IGA_ENOMEM, "host allocation failed");
+        memset(A, 0, sizeof(*A));
+        A->dim = dim; A->p = p; A->dtype = dtype; A->device = dev;
+        for (int d = 0; d < 3; ++d) { A->n_el[d] = g.n_el[d]; A->m[d] = g.m[d]; }
+        A->N = N; A->S = S; A->nnz = nnz;
+        A->bytes = (size_t)S * (size_t)N * esz;
+        ce = cudaMalloc(&A->values, A->bytes);
+        if (ce != cudaSuccess) { delete A; return cuda_fail(ce, "allocating matrix values"); }
+        created = true;
+    }
+    cudaMemPool_t pool;
+    if ((ce = device_pool(dev, &pool)) != cudaSuccess) {
+        if (created) { cudaFree(A->values); delete A; }
+        return cuda_fail(ce, "creating the memory pool");
+    }
+    double* scratch = nullptr;
+    ce = cudaMallocFromPoolAsync((void**)&scratch, (size_t)lay.total * sizeof(double), pool, st);
+    if (ce != cudaSuccess) {
+        if (created) { cudaFree(A->values); delete A; }
+        return cuda_fail(ce, "allocating scratch");
+    }
+
+    // ---------------- launches ----------------
+    auto P = [&](int64_t off) { return scratch + off; };
+    double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
+    for (int d = 0; d < 3; ++d) {
+        gx[d] = P(o_gx[d]); sx[d] = P(o_sx[d]); cx[d] = P(o_cx[d]); wq[d] = P(o_wq[d]);
+        bv[d] = P(o_bv[d]); bd[d] = P(o_bd[d]); X[d] = P(o_X[d]);
+    }
+    Tables T;
+    for (int d = 0; d < 3; ++d) { T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; }
+    const char* stage = "basis tables";
+    ce = launch_basis(g, gx, sx, cx, bv, bd, wq, st);
+    if (ce == cudaSuccess) { stage = "pair tables"; ce = launch_pairs(g, bv, bd, wq, X, st); }
+    if (ce == cudaSuccess) { stage = "coefficient field"; ce = launch_coef(g, T, bs, nblk[0], scratch, st); }
+    double* samples = do_spline ? P(o_samples) : nullptr;
+    if (ce == cudaSuccess) {
+        stage = "quadrature stages";
+        ce = launch_stages(g, T, bs, nblk, scratch, A->values, dtype == IGA_F32, samples, st);
+    }
+    SplineBufs sb;
+    memset(&sb, 0, sizeof(sb));
+    if (do_spline) {
+        int* ints = (int*)P(o_ints);
+        sb.band = ints;
+        int64_t io = 8;
+        for (int d = 0; d < dim; ++d) {
+            sb.lu[d] = P(o_lu[d]);
+            sb.eval[d] = P(o_eval[d]);
+            sb.espan[d] = ints + io;
+            io += sp.L[d] + 8;
+        }
+        sb.partial = P(o_partial);
+        if (ce == cudaSuccess) { stage = "spline interpolation"; ce = launch_spline(g, sp, M, samples, sb, st); }
+    }
+    if (surrogate && ce == cudaSuccess) {
+        stage = "surrogate fill";
+        ce = launch_fill(g, sp, empty, sb, A->values, dtype == IGA_F32, st);
+    }
+    cudaError_t fe = cudaFreeAsync(scratch, st);
+    if (ce == cudaSuccess) ce = fe;
+    if (ce != cudaSuccess) {
+        if (created) { cudaFree(A->values); delete A; }
+        return cuda_fail(ce, stage);
+    }
+    *out = A;
+    return IGA_OK;
+}
+
+}  // namespace
+
+namespace iga {
+
+void launch_begin(int kid, cudaStream_t s)
+{
+    (void)kid;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_profile.load(std::memory_order_relaxed)) {
+        t_begin = take_event();
+        if (t_begin) cudaEventRecord(t_begin, s);
+    } else {
+        t_begin = nullptr;
+    }
+}
+
+void launch_end(int kid, cudaStream_t s)
+{
+    if (!t_begin) return;
+    cudaEvent_t e = take_event();
+    if (!e) return;
+    cudaEventRecord(e, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending.push_back({kid, t_begin, e});
+    t_begin = nullptr;
+}
+
+}  // namespace iga
+
+extern "C" {
+
+int iga_assemble_exact(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+                       int dtype, void* stream, iga_matrix_t* A)
+{
+    return assemble(patch, p, map, kappa, false, 1, 0, dtype, stream, A);
+}
+
+int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+                           int M, int q, int dtype, void* stream, iga_matrix_t* A)
+{
+    return assemble(patch, p, map, kappa, true, M, q, dtype, stream, A);
+}
+
+int iga_apply(iga_matrix_t A, const void* x, void* y, void* stream)
+{
+    t_err.clear();
+    if (!A || !x || !y) return fail(IGA_EINVAL, "iga_apply: null argument");
+    if (x == y) return fail(IGA_EINVAL, "iga_apply: x and y must not overlap");
+    cudaError_t e = launch_spmv(A->dim, A->p, A->m, A->values, A->dtype == IGA_F32, x, y, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil SpMV");
+    return IGA_OK;
+}
+
+int iga_apply_host(iga_matrix_t A, const void* x_host, void* y_host, void* stream)
+{
+    t_err.clear();
+    if (!A || !x_host || !y_host) return fail(IGA_EINVAL, "iga_apply_host: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemPool_t pool;
+    cudaError_t e = device_pool(A->device, &pool);
+    if (e != cudaSuccess) return cuda_fail(e, "memory pool");
+    const size_t vb = (size_t)A->N * (A->dtype == IGA_F32 ? 4 : 8);
+    void* buf = nullptr;
+    e = cudaMallocFromPoolAsync(&buf, 2 * align_up((int64_t)vb, 256), pool, st);
+    if (e != cudaSuccess) return cuda_fail(e, "staging buffers");
+    void* dx = buf;
+    void* dy = (char*)buf + align_up((int64_t)vb, 256);
+    e = cudaMemcpyAsync(dx, x_host, vb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_spmv(A->dim, A->p, A->m, A->values, A->dtype == IGA_F32, dx, dy, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_host, dy, vb, cudaMemcpyDeviceToHost, st);
+    cudaError_t fe = cudaFreeAsync(buf, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = fe;
+    if (e == cudaSuccess) e = se;
+    if (e != cudaSuccess) return cuda_fail(e, "iga_apply_host");
+    return IGA_OK;
+}
+
+int iga_matrix_info(iga_matrix_t A, int64_t* N, int32_t* S, int64_t* nnz, int32_t* dtype)
+{
+    t_err.clear();
+    if (!A) return fail(IGA_EINVAL, "null matrix");
+    if (N) *N = A->N;
+    if (S) *S = A->S;
+    if (nnz) *nnz = A->nnz;
+    if (dtype) *dtype = A->dtype;
+    return IGA_OK;
+}
+
+int iga_matrix_values(iga_matrix_t A, const void** values)
+{
+    t_err.clear();
+    if (!A || !values) return fail(IGA_EINVAL, "null argument");
+    *values = A->values;
+    return IGA_OK;
+}
+
+int iga_matrix_copy_values(iga_matrix_t A, void* dst, int dst_on_host, void* stream)
+{
+    t_err.clear();
+    if (!A || !dst) return fail(IGA_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(dst, A->values, A->bytes,
+                                    dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copying values");
+    return IGA_OK;
+}
+
+int iga_matrix_destroy(iga_matrix_t A)
+{
+    t_err.clear();
+    if (!A) return IGA_OK;
+    cudaError_t e = cudaFree(A->values);
+    delete A;
+    if (e != cudaSuccess) return cuda_fail(e, "freeing matrix values");
+    return IGA_OK;
+}
+
+int64_t iga_launch_count(void) { return g_launches.load(); }
+
+int iga_profile_enable(int on)
+{
+    g_profile.store(on ? 1 : 0);
+    return IGA_OK;
+}
+
+int iga_profile_read(int n, int64_t* launches, double* ms)
+{
+    t_err.clear();
+    if (n < 0 || (n > 0 && (!launches || !ms))) return fail(IGA_EINVAL, "iga_profile_read: bad arguments");
+    for (int k = 0; k < n; ++k) { launches[k] = 0; ms[k] = 0.0; }
+    std::vector<Pending> pend;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        pend.swap(g_pending);
+    }
+    int rc = IGA_OK;
+    for (auto& pd : pend) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(pd.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pd.a, pd.b);
+        if (e != cudaSuccess) rc = cuda_fail(e, "reading profile events");
+        else if (pd.kid < n) { launches[pd.kid] += 1; ms[pd.kid] += t; }
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& pd : pend) { g_events.push_back(pd.a); g_events.push_back(pd.b); }
+    return rc;
+}
+
+int iga_num_kernels(void) { return K_NUM; }
+
+const char* iga_kernel_name(int k) { return (k >= 0 && k < K_NUM) ? kNames[k] : ""; }
+
+const char* iga_last_error(void) { return t_err.c_str(); }
+
+int iga_version(void) { return 10000; }
+
+}  // extern "C"

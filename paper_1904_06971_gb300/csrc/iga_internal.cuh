@@ -1,0 +1,166 @@
+// Internal declarations of libiga (CUDA, sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "iga.h"
+
+namespace iga {
+
+constexpr int kMaxP = 5;          // degrees 1..5 are instantiated
+constexpr int kMaxQ = 7;          // interpolation degree 0..7
+constexpr int kBlock = 256;       // threads per block of the item-parallel kernels
+
+// Geometry map + diffusion coefficient + mesh; passed by value to kernels.
+struct Geo {
+    int dim, p;
+    int n_el[3], m[3];
+    int map_kind;
+    double amp;
+    double aff[12];
+    int kappa_kind, kappa_deg;
+    double ka, kb;
+    double poly[64];
+};
+
+// A rectangular block of rows whose full stencil rows are computed by the
+// sum-factorised quadrature, with the Gauss points it needs.
+struct Box {
+    int rlo[3], R[3];         // row index range per direction
+    int elo[3], E[3];         // element range per direction (covers the rows' supports)
+    int out_kind;             // 0: write rows into the ELL values; 1: into the FP64 sample table
+    int64_t sample_id;        // column of the sample table (out_kind 1; the box is one row)
+    int64_t c_off;            // offset (doubles) of the box's coefficient fields in scratch
+    int64_t t1_off, t2_off;   // offsets (doubles) of the stage intermediates
+    int64_t blk[4];           // first block of this box in the K2 / Z / Y / X launches
+};
+
+constexpr int kMaxBoxes = 7;
+
+// The boxes of one assembly: a few explicit boxes (the whole patch, or the
+// frame slabs) and an implicit batch of one-row boxes at the sample rows
+// s_d = min(k0_d + a_d M, k1_d), a_d = 0..ns_d-1 (sample id a_0 + ns_0 (a_1 + ns_1 a_2)).
+struct BoxSet {
+    int nb;
+    Box box[kMaxBoxes];
+    int64_t n_samples;
+    int ns[3], k0[3], k1[3], M;
+    int64_t s_c_off, s_t1_off, s_t2_off;      // scratch offsets of sample box 0
+    int64_t s_c_len, s_t1_len, s_t2_len;      // scratch per sample box
+    int64_t blk_s[4];                         // first block of the batch in launch k
+    int64_t bper_s[4];                        // blocks per sample box in launch k
+};
+
+// Box owning block `block` of launch `stage`.  Every thread of a block gets the same box.
+__device__ __forceinline__ void get_box(const BoxSet& bs, int dim, int p, int stage, int64_t block, Box& b)
+{
+    if (bs.n_samples > 0 && block >= bs.blk_s[stage]) {
+        const int64_t sid = (block - bs.blk_s[stage]) / bs.bper_s[stage];
+        int64_t rem = sid;
+        for (int d = 0; d < 3; ++d) {
+            int s = 0;
+            if (d < dim) {
+                const int a = (int)(rem % bs.ns[d]);
+                rem /= bs.ns[d];
+                s = bs.k0[d] + a * bs.M;
+                if (s > bs.k1[d]) s = bs.k1[d];
+            }
+            b.rlo[d] = s;
+            b.R[d] = 1;
+            b.elo[d] = (d < dim) ? s - p : 0;
+            b.E[d] = (d < dim) ? p + 1 : 1;
+        }
+        b.out_kind = 1;
+        b.sample_id = sid;
+        b.c_off = bs.s_c_off + sid * bs.s_c_len;
+        b.t1_off = bs.s_t1_off + sid * bs.s_t1_len;
+        b.t2_off = bs.s_t2_off + sid * bs.s_t2_len;
+        for (int k = 0; k < 4; ++k) b.blk[k] = bs.blk_s[k] + sid * bs.bper_s[k];
+        return;
+    }
+    int k = bs.nb - 1;
+    while (k > 0 && bs.box[k].blk[stage] > block) --k;
+    b = bs.box[k];
+}
+
+// Per-direction device tables written by the basis kernels.
+struct Tables {
+    const double* gx[3];      // [G]  Gauss point coordinates xi
+    const double* sx[3];      // [G]  sin(pi xi)
+    const double* cx[3];      // [G]  cos(pi xi)
+    const double* X[3];       // [4][m][2p+1][(p+1)^2] pair weights, see k_tables.cu
+};
+
+enum KernelId {
+    K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
+    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_NUM
+};
+
+// Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
+// brackets the launch with events on its stream.
+void launch_begin(int kid, cudaStream_t s);
+void launch_end(int kid, cudaStream_t s);
+
+// ---- launchers implemented in the kernel files; all return cudaError_t ----
+cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[3],
+                         double* bv[3], double* bd[3], double* wq[3], cudaStream_t s);
+cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
+                         double* const wq[3], double* X[3], cudaStream_t s);
+cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t nblocks,
+                        double* scratch, cudaStream_t s);
+cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
+                          double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
+
+struct SplinePlan {
+    int dim, q, k0[3], L[3], ns[3], qe[3];
+    int64_t n_samples;        // prod ns
+    int S, c;                 // slots and centre slot
+};
+// K4: collocation LU per direction, coefficient solves in place in the upper
+// slots of the sample table, evaluation tables and the partially evaluated field.
+struct SplineBufs {
+    double* lu[3];            // [ns][ns] LU factors (unit lower L below the diagonal)
+    int* band;                // [3][2] lower / upper bandwidth of the factors
+    int* espan[3];            // [L] first nonzero interpolation basis index at box index k0 + k
+    double* eval[3];          // [L][q+1] its values
+    double* partial;          // 3-D [S_up][L2][L1][ns0]; 2-D [S_up][L1][ns0]
+};
+cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* samples /* [S][n_samples] */,
+                          const SplineBufs& sb, cudaStream_t s);
+cudaError_t launch_fill(const Geo& g, const SplinePlan& sp, int empty_box, const SplineBufs& sb,
+                        void* ell, int ell_f32, cudaStream_t s);
+cudaError_t launch_spmv(int dim, int p, const int m[3], const void* values, int f32,
+                        const void* x, void* y, cudaStream_t s);
+
+// Scratch sizes (doubles) of a box for the quadrature stages.
+inline int64_t box_coef_len(int dim, int p, const Box& b) {
+    int Q = p + 1;
+    int64_t n = (dim == 3 ? 6 : 3);
+    for (int d = 0; d < dim; ++d) n *= (int64_t)b.E[d] * Q;
+    return n;
+}
+inline int64_t box_t1_len(int dim, int p, const Box& b) {
+    if (dim != 3) return 0;
+    int Q = p + 1, W = 2 * p + 1;
+    return (int64_t)8 * b.R[2] * W * ((int64_t)b.E[1] * Q) * ((int64_t)b.E[0] * Q);
+}
+inline int64_t box_t2_len(int dim, int p, const Box& b) {
+    int Q = p + 1, W = 2 * p + 1;
+    int64_t pairs3 = (dim == 3) ? (int64_t)b.R[2] * W : 1;
+    return (int64_t)4 * pairs3 * ((int64_t)b.R[1] * W) * ((int64_t)b.E[0] * Q);
+}
+// items of each launch for one box
+inline int64_t box_items(int dim, int p, const Box& b, int stage) {
+    int Q = p + 1, W = 2 * p + 1;
+    int64_t G0 = (int64_t)b.E[0] * Q, G1 = (int64_t)b.E[1] * Q, G2 = (dim == 3) ? (int64_t)b.E[2] * Q : 1;
+    int64_t P3 = (dim == 3) ? (int64_t)b.R[2] * W : 1;
+    switch (stage) {
+        case 0: return G0 * G1 * G2;                         // coefficient points
+        case 1: return (dim == 3) ? (int64_t)b.R[2] * G1 * G0 : 0;  // stage Z
+        case 2: return P3 * b.R[1] * G0;                     // stage Y
+        default: return P3 * ((int64_t)b.R[1] * W) * b.R[0]; // stage X
+    }
+}
+
+}  // namespace iga

@@ -1,0 +1,300 @@
+// K4: per-offset tensor-product B-spline interpolation of the stencil
+//     functions through their samples (Sec. 4.1, Sec. 6).
+// K5: surrogate rows of eq. DefinitionOfSurrogateMatrixSymmetricKernel
+//     (Sec. 5.3) written into the stencil-ELL values, with the
+//     kernel-preserving diagonal.
+//
+// Interpolation reading: abscissae are the sample indices t_a = min(k0 + a M, k1);
+// the knot vector of degree q has (q+1)-fold end knots at t_0 and t_{ns-1}
+// and interior knots at t_{(q+1)/2} .. t_{ns-1-(q+1)/2} (odd q) or at the
+// midpoints (t_r + t_{r+1})/2, r = q/2 .. ns-2-q/2 (even q) -- the not-a-knot
+// interpolating spline.  Spans are half-open [kn_mu, kn_mu+1) except the last.
+// The collocation matrix is totally positive and banded, so it is factored
+// without pivoting and the factors keep its band.
+#include "iga_internal.cuh"
+
+namespace iga {
+
+__device__ __forceinline__ double sample_pos(int a, int k0, int k1, int M)
+{
+    int s = k0 + a * M;
+    return (double)(s > k1 ? k1 : s);
+}
+
+__device__ int find_span(const double* kn, int ns, int q, double x)
+{
+    if (x >= kn[ns]) return ns - 1;
+    int lo = q, hi = ns;                 // kn[lo] <= x < kn[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (x < kn[mid]) hi = mid;
+        else lo = mid;
+    }
+    return lo;
+}
+
+// values of the q+1 B-splines mu-q..mu at x (local triangular Cox-de Boor)
+__device__ void spline_basis(const double* kn, int mu, int q, double x, double* N)
+{
+    double left[kMaxQ + 1], right[kMaxQ + 1];
+    N[0] = 1.0;
+    for (int k = 1; k <= q; ++k) {
+        left[k] = x - kn[mu + 1 - k];
+        right[k] = kn[mu + k] - x;
+        double saved = 0.0;
+        for (int r = 0; r < k; ++r) {
+            double tmp = N[r] / (right[r + 1] + left[k - r]);
+            N[r] = saved + right[r + 1] * tmp;
+            saved = left[k - r] * tmp;
+        }
+        N[k] = saved;
+    }
+}
+
+// One block per direction: knots, collocation matrix, banded LU, evaluation tables.
+__global__ void k_spline_setup(SplinePlan sp, int M, SplineBufs sb)
+{
+    extern __shared__ double kn[];
+    __shared__ int sbl, sbu;
+    const int d = blockIdx.x;
+    const int ns = sp.ns[d], q = sp.qe[d], k0 = sp.k0[d], L = sp.L[d];
+    const int k1 = k0 + L - 1;
+    const int nk = ns + q + 1;
+    if (threadIdx.x == 0) { sbl = 0; sbu = 0; }
+    for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+        double v;
+        if (r <= q) v = sample_pos(0, k0, k1, M);
+        else if (r >= ns) v = sample_pos(ns - 1, k0, k1, M);
+        else if (q & 1) v = sample_pos((q + 1) / 2 + (r - q - 1), k0, k1, M);
+        else {
+            const int a = q / 2 + (r - q - 1);
+            v = 0.5 * (sample_pos(a, k0, k1, M) + sample_pos(a + 1, k0, k1, M));
+        }
+        kn[r] = v;
+    }
+    double* B = sb.lu[d];
+    for (int64_t k = threadIdx.x; k < (int64_t)ns * ns; k += blockDim.x) B[k] = 0.0;
+    __syncthreads();
+    // collocation rows: B[r][c] = N_c(t_r)
+    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
+        const double x = sample_pos(r, k0, k1, M);
+        const int mu = find_span(kn, ns, q, x);
+        double N[kMaxQ + 1];
+        spline_basis(kn, mu, q, x, N);
+        for (int a = 0; a <= q; ++a) B[(int64_t)r * ns + mu - q + a] = N[a];
+        atomicMax(&sbl, r - (mu - q));
+        atomicMax(&sbu, mu - r);
+    }
+    __syncthreads();
+    const int bl = sbl, bu = sbu;
+    // banded LU without pivoting: B = L U, L unit lower (stored below the diagonal)
+    for (int k = 0; k < ns - 1; ++k) {
+        const double piv = B[(int64_t)k * ns + k];
+        const int rhi = min(ns, k + bl + 1), chi = min(ns, k + bu + 1);
+        for (int r = k + 1 + threadIdx.x; r < rhi; r += blockDim.x) {
+            const double l = B[(int64_t)r * ns + k] / piv;
+            B[(int64_t)r * ns + k] = l;
+            for (int c = k + 1; c < chi; ++c) B[(int64_t)r * ns + c] -= l * B[(int64_t)k * ns + c];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { sb.band[2 * d] = bl; sb.band[2 * d + 1] = bu; }
+    // evaluation at every box index k0 + k
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const double x = (double)(k0 + k);
+        const int mu = find_span(kn, ns, q, x);
+        double N[kMaxQ + 1];
+        spline_basis(kn, mu, q, x, N);
+        sb.espan[d][k] = mu - q;
+        for (int a = 0; a <= q; ++a) sb.eval[d][(int64_t)k * (q + 1) + a] = N[a];
+    }
+}
+
+// Solve the collocation system along direction d for every upper offset and line,
+// in place in the sample table rows c+1 .. S-1.
+__global__ void k_spline_solve(SplinePlan sp, int d, SplineBufs sb, double* samples)
+{
+    const int ns = sp.ns[d];
+    const int64_t lines = sp.n_samples / ns;
+    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= S_up * lines) return;
+    const int64_t u = idx / lines, l = idx % lines;
+    int64_t st = 1;
+    for (int e = 0; e < d; ++e) st *= sp.ns[e];
+    const int64_t base = (l % st) + (l / st) * st * ns;
+    double* v = samples + (sp.c + 1 + u) * sp.n_samples + base;
+    const double* B = sb.lu[d];
+    const int bl = sb.band[2 * d], bu = sb.band[2 * d + 1];
+    for (int r = 1; r < ns; ++r) {
+        double acc = v[r * st];
+        for (int c = max(0, r - bl); c < r; ++c) acc -= B[(int64_t)r * ns + c] * v[c * st];
+        v[r * st] = acc;
+    }
+    for (int r = ns - 1; r >= 0; --r) {
+        double acc = v[r * st];
+        for (int c = r + 1; c < min(ns, r + bu + 1); ++c) acc -= B[(int64_t)r * ns + c] * v[c * st];
+        v[r * st] = acc / B[(int64_t)r * ns + r];
+    }
+}
+
+// Partially evaluated coefficients: contract directions 2 (3-D) and 1 at every
+// box index, keeping the coefficient index a0 of direction 0:
+//   3-D: partial[u][j2][j1][a0] = sum_{b,c} coef[u][a0, s1(j1)+b, s2(j2)+c] E1[j1][b] E2[j2][c]
+//   2-D: partial[u][j1][a0]     = sum_b     coef[u][a0, s1(j1)+b]          E1[j1][b]
+__global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* samples)
+{
+    const int n0 = sp.ns[0], n1 = sp.ns[1];
+    const int L1 = sp.L[1], L2 = (sp.dim == 3) ? sp.L[2] : 1;
+    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t total = S_up * L2 * L1 * n0;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int a0 = (int)(idx % n0);
+    const int j1 = (int)((idx / n0) % L1);
+    const int j2 = (int)((idx / ((int64_t)n0 * L1)) % L2);
+    const int64_t u = idx / ((int64_t)n0 * L1 * L2);
+    const double* coef = samples + (sp.c + 1 + u) * sp.n_samples;
+    const int q1 = sp.qe[1];
+    const int s1 = sb.espan[1][j1];
+    const double* E1 = sb.eval[1] + (int64_t)j1 * (q1 + 1);
+    double acc = 0.0;
+    if (sp.dim == 3) {
+        const int q2 = sp.qe[2];
+        const int s2 = sb.espan[2][j2];
+        const double* E2 = sb.eval[2] + (int64_t)j2 * (q2 + 1);
+        for (int c = 0; c <= q2; ++c) {
+            double inner = 0.0;
+            for (int b = 0; b <= q1; ++b)
+                inner += coef[a0 + (int64_t)n0 * ((s1 + b) + (int64_t)n1 * (s2 + c))] * E1[b];
+            acc += inner * E2[c];
+        }
+    } else {
+        for (int b = 0; b <= q1; ++b) acc += coef[a0 + (int64_t)n0 * (s1 + b)] * E1[b];
+    }
+    sb.partial[idx] = acc;
+}
+
+cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* samples,
+                          const SplineBufs& sb, cudaStream_t s)
+{
+    int nsmax = 0;
+    for (int d = 0; d < sp.dim; ++d) nsmax = max(nsmax, sp.ns[d] + sp.qe[d] + 1);
+    launch_begin(K_SPLINE_SETUP, s);
+    k_spline_setup<<<sp.dim, 256, (size_t)nsmax * sizeof(double), s>>>(sp, M, sb);
+    launch_end(K_SPLINE_SETUP, s);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int64_t S_up = sp.S - 1 - sp.c;
+    for (int d = 0; d < sp.dim; ++d) {
+        const int64_t n = S_up * (sp.n_samples / sp.ns[d]);
+        launch_begin(K_SPLINE_SOLVE, s);
+        k_spline_solve<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, d, sb, samples);
+        launch_end(K_SPLINE_SOLVE, s);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    const int64_t total = S_up * (sp.dim == 3 ? sp.L[2] : 1) * (int64_t)sp.L[1] * sp.ns[0];
+    launch_begin(K_SPLINE_PARTIAL, s);
+    k_spline_partial<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(sp, sb, samples);
+    launch_end(K_SPLINE_PARTIAL, s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K5: one thread per row.
+//  - rows outside Omega~ (written exactly by K3): diagonal := -(off-diagonal sum);
+//  - rows inside: for each slot with column j = i + delta,
+//      j in Omega~, j > i : Phi~_delta(x~_i)                      (interpolated)
+//      j in Omega~, j < i : Phi~_{-delta}(x~_j)  (= A~_ji, the copied entry)
+//      j outside Omega~   : A_ji from the exact frame row j (= A_ij)
+//    then the diagonal := -(off-diagonal sum), accumulated in FP64.
+// ---------------------------------------------------------------------------
+template <int P, int DIM, typename T>
+__global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, int empty_box, SplineBufs sb, T* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    const int m0 = g.m[0], m1 = g.m[1], m2 = (DIM == 3) ? g.m[2] : 1;
+    const int64_t N = (int64_t)m0 * m1 * m2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
+    const int k0 = sp.k0[0];
+    bool inbox = !empty_box;
+    if (inbox) {
+        inbox = (i0 >= k0 && i0 < k0 + sp.L[0]) && (i1 >= sp.k0[1] && i1 < sp.k0[1] + sp.L[1]);
+        if (DIM == 3) inbox = inbox && (i2 >= sp.k0[2] && i2 < sp.k0[2] + sp.L[2]);
+    }
+    double sum = 0.0;
+    if (!inbox) {
+#pragma unroll 8
+        for (int s = 0; s < S; ++s)
+            if (s != C) sum += (double)vals[(int64_t)s * N + i];
+        vals[(int64_t)C * N + i] = (T)(-sum);
+        return;
+    }
+    const int n0 = sp.ns[0], q0 = sp.qe[0];
+    const int L0 = sp.L[0], L1 = sp.L[1], L2 = (DIM == 3) ? sp.L[2] : 1;
+    const int kk0 = sp.k0[0], kk1 = sp.k0[1], kk2 = (DIM == 3) ? sp.k0[2] : 0;
+    for (int s = 0; s < S; ++s) {
+        if (s == C) continue;
+        const int d0 = s % W - P, d1 = (s / W) % W - P, d2 = (DIM == 3) ? s / (W * W) - P : 0;
+        const int j0 = i0 + d0, j1 = i1 + d1, j2 = i2 + d2;
+        const int l0 = j0 - kk0, l1 = j1 - kk1, l2 = j2 - kk2;
+        const bool jin = (l0 >= 0 && l0 < L0) && (l1 >= 0 && l1 < L1) && (l2 >= 0 && l2 < L2);
+        double v;
+        if (jin) {
+            // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
+            const bool upper = s > C;
+            const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
+            const int e0 = upper ? i0 - kk0 : l0;
+            const int e1 = upper ? i1 - kk1 : l1;
+            const int e2 = upper ? i2 - kk2 : l2;
+            const double* Pp = sb.partial + (((int64_t)u * L2 + e2) * L1 + e1) * n0 + sb.espan[0][e0];
+            const double* E = sb.eval[0] + (int64_t)e0 * (q0 + 1);
+            double a = 0.0;
+            for (int k = 0; k <= q0; ++k) a = fma(E[k], Pp[k], a);
+            v = a;
+        } else {
+            const int64_t jrow = j0 + (int64_t)m0 * (j1 + (int64_t)m1 * j2);
+            v = (double)vals[(int64_t)(S - 1 - s) * N + jrow];
+        }
+        vals[(int64_t)s * N + i] = (T)v;
+        sum += v;
+    }
+    vals[(int64_t)C * N + i] = (T)(-sum);
+}
+
+template <int P>
+static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const SplineBufs& sb, void* ell,
+                   int f32, unsigned grid, cudaStream_t s)
+{
+    if (g.dim == 3) {
+        if (f32) k_fill<P, 3, float><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (float*)ell);
+        else k_fill<P, 3, double><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (double*)ell);
+    } else {
+        if (f32) k_fill<P, 2, float><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (float*)ell);
+        else k_fill<P, 2, double><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (double*)ell);
+    }
+}
+
+cudaError_t launch_fill(const Geo& g, const SplinePlan& sp, int empty_box, const SplineBufs& sb,
+                        void* ell, int ell_f32, cudaStream_t s)
+{
+    const int64_t N = (int64_t)g.m[0] * g.m[1] * (g.dim == 3 ? g.m[2] : 1);
+    const unsigned grid = (unsigned)((N + kBlock - 1) / kBlock);
+    launch_begin(K_FILL, s);
+    switch (g.p) {
+    case 1: fill_p<1>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
+    case 2: fill_p<2>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
+    case 3: fill_p<3>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
+    case 4: fill_p<4>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
+    case 5: fill_p<5>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
+    default: break;
+    }
+    launch_end(K_FILL, s);
+    return cudaGetLastError();
+}
+
+}  // namespace iga

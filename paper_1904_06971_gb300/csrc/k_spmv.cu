@@ -1,0 +1,77 @@
+// K6: stencil SpMV y = A x on the index-free stencil-ELL layout
+// (eq. DiscreteVariationalProblems).  One thread per row; the value of slot s
+// of row i is vals[s * N + i] (coalesced across consecutive rows) and its
+// column is i + delta_0 + m_0 (delta_1 + m_1 delta_2).  Rows whose whole
+// stencil stays inside the index range skip the bounds tests.
+#include "iga_internal.cuh"
+
+namespace iga {
+
+template <int P, int DIM, typename T>
+__global__ void __launch_bounds__(kBlock) k_spmv(int m0, int m1, int m2, const T* __restrict__ vals,
+                                                 const T* __restrict__ x, T* __restrict__ y)
+{
+    constexpr int W = 2 * P + 1;
+    const int64_t N = (int64_t)m0 * m1 * m2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
+    const bool inner = i0 >= P && i0 < m0 - P && i1 >= P && i1 < m1 - P &&
+                       (DIM == 2 || (i2 >= P && i2 < m2 - P));
+    const int64_t s1 = m0, s2 = (int64_t)m0 * m1;
+    T acc = 0;
+    const int n2 = (DIM == 3) ? W : 1;
+    for (int d2 = 0; d2 < n2; ++d2) {
+        const int o2 = (DIM == 3) ? d2 - P : 0;
+        const bool ok2 = inner || (i2 + o2 >= 0 && i2 + o2 < m2);
+        for (int d1 = 0; d1 < W; ++d1) {
+            const int o1 = d1 - P;
+            const bool ok1 = ok2 && (inner || (i1 + o1 >= 0 && i1 + o1 < m1));
+            if (!ok1) continue;
+            const int sbase = W * (d1 + W * d2);
+            const int64_t jbase = i + o1 * s1 + o2 * s2;
+            const T* v = vals + (int64_t)sbase * N + i;
+#pragma unroll
+            for (int d0 = 0; d0 < W; ++d0) {
+                const int o0 = d0 - P;
+                if (inner || (i0 + o0 >= 0 && i0 + o0 < m0))
+                    acc = fma(v[(int64_t)d0 * N], __ldg(x + jbase + o0), acc);
+            }
+        }
+    }
+    y[i] = acc;
+}
+
+template <int P>
+static void spmv_p(int dim, const int m[3], const void* vals, int f32, const void* x, void* y,
+                   unsigned grid, cudaStream_t s)
+{
+    const int m2 = (dim == 3) ? m[2] : 1;
+    if (dim == 3) {
+        if (f32) k_spmv<P, 3, float><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const float*)vals, (const float*)x, (float*)y);
+        else k_spmv<P, 3, double><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const double*)vals, (const double*)x, (double*)y);
+    } else {
+        if (f32) k_spmv<P, 2, float><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const float*)vals, (const float*)x, (float*)y);
+        else k_spmv<P, 2, double><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const double*)vals, (const double*)x, (double*)y);
+    }
+}
+
+cudaError_t launch_spmv(int dim, int p, const int m[3], const void* values, int f32,
+                        const void* x, void* y, cudaStream_t s)
+{
+    const int64_t N = (int64_t)m[0] * m[1] * (dim == 3 ? m[2] : 1);
+    const unsigned grid = (unsigned)((N + kBlock - 1) / kBlock);
+    launch_begin(K_SPMV, s);
+    switch (p) {
+    case 1: spmv_p<1>(dim, m, values, f32, x, y, grid, s); break;
+    case 2: spmv_p<2>(dim, m, values, f32, x, y, grid, s); break;
+    case 3: spmv_p<3>(dim, m, values, f32, x, y, grid, s); break;
+    case 4: spmv_p<4>(dim, m, values, f32, x, y, grid, s); break;
+    case 5: spmv_p<5>(dim, m, values, f32, x, y, grid, s); break;
+    default: break;
+    }
+    launch_end(K_SPMV, s);
+    return cudaGetLastError();
+}
+
+}  // namespace iga

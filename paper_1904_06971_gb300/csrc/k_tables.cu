@@ -1,0 +1,324 @@
+// K1: Gauss rule, B-spline values/derivatives at the Gauss points and the 1-D
+//     pair-weight tables of the sum-factorised quadrature.
+// K2: the coefficient tensor K = kappa(phi) |det Dphi| Dphi^{-1} Dphi^{-T}
+//     (eq. BilinearFormPoissonTensor) at the Gauss points of each box.
+#include <math_constants.h>
+
+#include "iga_internal.cuh"
+
+namespace iga {
+
+// ---------------------------------------------------------------------------
+// (p+1)-point Gauss-Legendre rule on [0,1]: Newton's method on the Legendre
+// polynomial P_n evaluated by its three-term recurrence; node k of n on
+// [-1,1] starts from cos(pi (k + 3/4) / (n + 1/2)).
+// ---------------------------------------------------------------------------
+__device__ void legendre_eval(int n, double z, double& pn, double& dpn)
+{
+    double a = 1.0, b = z;                   // P_0, P_1
+    for (int j = 2; j <= n; ++j) {
+        double c = ((2 * j - 1) * z * b - (j - 1) * a) / j;
+        a = b;
+        b = c;
+    }
+    pn = (n == 0) ? 1.0 : b;
+    dpn = n * (z * b - a) / (z * z - 1.0);
+}
+
+__device__ void gauss_node(int n, int k, double& x01, double& w01)
+{
+    double z = cospi((k + 0.75) / (n + 0.5));
+    double pn, dpn;
+    for (int it = 0; it < 64; ++it) {
+        legendre_eval(n, z, pn, dpn);
+        double dz = pn / dpn;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+    }
+    legendre_eval(n, z, pn, dpn);
+    // ascending order on [0,1]: root k (descending in z) goes to slot n-1-k
+    x01 = 0.5 * (1.0 + z);
+    w01 = 1.0 / ((1.0 - z * z) * dpn * dpn);
+}
+
+// open uniform knot t_k of degree p with n_el elements (m = n_el + p functions)
+__device__ __forceinline__ double knot(int k, int p, int n_el)
+{
+    if (k <= p) return 0.0;
+    if (k >= n_el + p) return 1.0;
+    return (double)(k - p) / (double)n_el;
+}
+
+// Values N[a] and derivatives D[a], a = 0..p, of the p+1 B-splines e..e+p that
+// are nonzero on element e at xi, by the local triangular Cox-de Boor scheme
+// (span mu = e + p); derivatives from the degree p-1 values.
+__device__ void basis_on_element(int p, int n_el, int e, double xi, double* N, double* D)
+{
+    const int mu = e + p;
+    double left[kMaxP + 1], right[kMaxP + 1], prev[kMaxP + 1];
+    N[0] = 1.0;
+    prev[0] = 1.0;
+    for (int k = 1; k <= p; ++k) {
+        left[k] = xi - knot(mu + 1 - k, p, n_el);
+        right[k] = knot(mu + k, p, n_el) - xi;
+        double saved = 0.0;
+        for (int r = 0; r < k; ++r) {
+            double tmp = N[r] / (right[r + 1] + left[k - r]);
+            N[r] = saved + right[r + 1] * tmp;
+            saved = left[k - r] * tmp;
+        }
+        N[k] = saved;
+        if (k == p - 1)
+            for (int r = 0; r <= k; ++r) prev[r] = N[r];
+    }
+    // N'_{i,p} = p ( N_{i,p-1} / (t_{i+p} - t_i) - N_{i+1,p-1} / (t_{i+p+1} - t_{i+1}) ), i = e + a
+    for (int a = 0; a <= p; ++a) {
+        int i = e + a;
+        double d = 0.0;
+        if (a >= 1) d += prev[a - 1] / (knot(i + p, p, n_el) - knot(i, p, n_el));
+        if (a <= p - 1) d -= prev[a] / (knot(i + p + 1, p, n_el) - knot(i + 1, p, n_el));
+        D[a] = p * d;
+    }
+}
+
+struct BasisArgs {
+    double* gx[3];
+    double* sx[3];
+    double* cx[3];
+    double* bv[3];
+    double* bd[3];
+    double* wq[3];
+};
+
+__global__ void __launch_bounds__(kBlock) k_basis(Geo g, BasisArgs A)
+{
+    __shared__ double sgx[kMaxP + 1], sgw[kMaxP + 1];
+    const int d = blockIdx.y;
+    const int p = g.p, Q = p + 1;
+    if (threadIdx.x < Q) {
+        double x, w;
+        gauss_node(Q, threadIdx.x, x, w);
+        sgx[Q - 1 - threadIdx.x] = x;
+        sgw[Q - 1 - threadIdx.x] = w;
+    }
+    __syncthreads();
+    const int n_el = g.n_el[d];
+    const int G = n_el * Q;
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= G) return;
+    const int e = gi / Q, r = gi % Q;
+    const double h = 1.0 / n_el;
+    const double xi = (e + sgx[r]) * h;
+    A.gx[d][gi] = xi;
+    double s, c;
+    sincospi(xi, &s, &c);
+    A.sx[d][gi] = s;
+    A.cx[d][gi] = c;
+    A.wq[d][gi] = sgw[r] * h;
+    double N[kMaxP + 1], D[kMaxP + 1];
+    basis_on_element(p, n_el, e, xi, N, D);
+    for (int a = 0; a <= p; ++a) {
+        A.bv[d][gi * Q + a] = N[a];
+        A.bd[d][gi * Q + a] = D[a];
+    }
+}
+
+cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[3],
+                         double* bv[3], double* bd[3], double* wq[3], cudaStream_t s)
+{
+    BasisArgs A;
+    int Gmax = 0;
+    for (int d = 0; d < 3; ++d) {
+        A.gx[d] = gx[d]; A.sx[d] = sx[d]; A.cx[d] = cx[d];
+        A.bv[d] = bv[d]; A.bd[d] = bd[d]; A.wq[d] = wq[d];
+        if (d < g.dim && g.n_el[d] * (g.p + 1) > Gmax) Gmax = g.n_el[d] * (g.p + 1);
+    }
+    dim3 grid((Gmax + kBlock - 1) / kBlock, g.dim);
+    launch_begin(K_BASIS, s);
+    k_basis<<<grid, kBlock, 0, s>>>(g, A);
+    launch_end(K_BASIS, s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pair weights.  For direction d, row function i, offset delta (column
+// j = i + delta) and local point t = a (p+1) + r of supp(B_i) (element
+// e = i - p + a, Gauss point r), pattern pat = 2 alpha + beta:
+//   X[pat][i][delta + p][t] = w_r h  b_i^(alpha)(x_g)  b_j^(beta)(x_g),
+// zero when e is outside the mesh, j outside [0, m) or b_j vanishes on e.
+// The product over directions of these factors, summed over the Gauss
+// points, is the quadrature of d^alpha B_i d^beta B_j (Sec. 3.2, eq. ChangeOfVars).
+// ---------------------------------------------------------------------------
+struct PairArgs {
+    const double* bv[3];
+    const double* bd[3];
+    const double* wq[3];
+    double* X[3];
+};
+
+__global__ void __launch_bounds__(kBlock) k_pairs(Geo g, PairArgs A)
+{
+    const int d = blockIdx.y;
+    const int p = g.p, Q = p + 1, W = 2 * p + 1, TT = Q * Q;
+    const int m = g.m[d], n_el = g.n_el[d];
+    const int64_t total = (int64_t)4 * m * W * TT;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int t = (int)(idx % TT);
+    int64_t rest = idx / TT;
+    const int dd = (int)(rest % W);
+    rest /= W;
+    const int i = (int)(rest % m);
+    const int pat = (int)(rest / m);
+    const int alpha = pat >> 1, beta = pat & 1;
+    const int e = i - p + t / Q, r = t % Q;
+    const int j = i + dd - p;
+    double v = 0.0;
+    if (e >= 0 && e < n_el && j >= 0 && j < m && j - e >= 0 && j - e <= p) {
+        const int gi = e * Q + r;
+        const double bi = alpha ? A.bd[d][gi * Q + (i - e)] : A.bv[d][gi * Q + (i - e)];
+        const double bj = beta ? A.bd[d][gi * Q + (j - e)] : A.bv[d][gi * Q + (j - e)];
+        v = A.wq[d][gi] * bi * bj;
+    }
+    A.X[d][idx] = v;
+}
+
+cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
+                         double* const wq[3], double* X[3], cudaStream_t s)
+{
+    PairArgs A;
+    int64_t maxn = 0;
+    const int p = g.p;
+    for (int d = 0; d < 3; ++d) {
+        A.bv[d] = bv[d]; A.bd[d] = bd[d]; A.wq[d] = wq[d]; A.X[d] = X[d];
+        if (d < g.dim) {
+            int64_t n = (int64_t)4 * g.m[d] * (2 * p + 1) * (p + 1) * (p + 1);
+            if (n > maxn) maxn = n;
+        }
+    }
+    dim3 grid((unsigned)((maxn + kBlock - 1) / kBlock), g.dim);
+    launch_begin(K_PAIRS, s);
+    k_pairs<<<grid, kBlock, 0, s>>>(g, A);
+    launch_end(K_PAIRS, s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K2: coefficient fields of a box, SoA over the box's Gauss points
+// ([field][g2][g1][g0], g0 fastest).  Fields: 3-D C00 C01 C02 C11 C12 C22,
+// 2-D C00 C01 C11.
+// ---------------------------------------------------------------------------
+__device__ double kappa_at(const Geo& g, const double* x)
+{
+    switch (g.kappa_kind) {
+    case IGA_KAPPA_CONST:
+        return g.ka;
+    case IGA_KAPPA_SIN2D:
+        return g.ka + g.kb * sinpi(2.0 * x[0]) * sinpi(2.0 * x[1]);
+    case IGA_KAPPA_EXPSIN3D:
+        return exp(g.kb * sinpi(2.0 * x[0]) * cospi(2.0 * x[1]) * sinpi(2.0 * x[2]));
+    case IGA_KAPPA_POLY: {
+        const int D = g.kappa_deg + 1;
+        double v = 0.0;
+        const int cmax = (g.dim == 3) ? D : 1;
+        for (int c = cmax - 1; c >= 0; --c) {
+            double vb = 0.0;
+            for (int b = D - 1; b >= 0; --b) {
+                double va = 0.0;
+                for (int a = D - 1; a >= 0; --a) va = va * x[0] + g.poly[a + D * (b + D * c)];
+                vb = vb * x[1] + va;
+            }
+            v = (g.dim == 3) ? v * x[2] + vb : vb;
+        }
+        return v;
+    }
+    default:
+        return 0.0;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, double* scratch)
+{
+    Box b;
+    get_box(bs, DIM, g.p, 0, blockIdx.x, b);
+    const int Q = g.p + 1;
+    const int64_t G0 = (int64_t)b.E[0] * Q, G1 = (int64_t)b.E[1] * Q, G2 = (DIM == 3) ? (int64_t)b.E[2] * Q : 1;
+    const int64_t npts = G0 * G1 * G2;
+    const int64_t item = (int64_t)(blockIdx.x - b.blk[0]) * kBlock + threadIdx.x;
+    if (item >= npts) return;
+    int gl[3];
+    gl[0] = (int)(item % G0);
+    gl[1] = (int)((item / G0) % G1);
+    gl[2] = (int)(item / (G0 * G1));
+    double xi[3] = {0, 0, 0}, x[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    int gg[3];
+    for (int d = 0; d < DIM; ++d) {
+        gg[d] = b.elo[d] * Q + gl[d];
+        xi[d] = T.gx[d][gg[d]];
+    }
+    if (g.map_kind == IGA_MAP_SINPROD) {
+        double s[3], c[3], P = 1.0;
+        for (int d = 0; d < DIM; ++d) { s[d] = T.sx[d][gg[d]]; c[d] = T.cx[d][gg[d]]; P *= s[d]; }
+        for (int bdir = 0; bdir < DIM; ++bdir) {
+            double dP = CUDART_PI * c[bdir];
+            for (int j = 0; j < DIM; ++j) if (j != bdir) dP *= s[j];
+            for (int a = 0; a < DIM; ++a) J[a][bdir] = (a == bdir ? 1.0 : 0.0) + g.amp * dP;
+        }
+        for (int a = 0; a < DIM; ++a) x[a] = xi[a] + g.amp * P;
+    } else if (g.map_kind == IGA_MAP_AFFINE) {
+        for (int a = 0; a < DIM; ++a) {
+            x[a] = g.aff[9 + a];
+            for (int bdir = 0; bdir < DIM; ++bdir) {
+                J[a][bdir] = g.aff[a * 3 + bdir];
+                x[a] += J[a][bdir] * xi[bdir];
+            }
+        }
+    } else {
+        for (int a = 0; a < DIM; ++a) { x[a] = xi[a]; J[a][a] = 1.0; }
+    }
+    const double kap = kappa_at(g, x);
+    // K = kappa |det J| J^{-1} J^{-T} = kappa / |det J| adj(J) adj(J)^T
+    double* out = scratch + b.c_off;
+    if (DIM == 2) {
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double a00 = J[1][1], a01 = -J[0][1], a10 = -J[1][0], a11 = J[0][0];
+        const double f = kap / fabs(det);
+        out[0 * npts + item] = f * (a00 * a00 + a01 * a01);
+        out[1 * npts + item] = f * (a00 * a10 + a01 * a11);
+        out[2 * npts + item] = f * (a10 * a10 + a11 * a11);
+    } else {
+        double adj[3][3];
+        adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+        const double f = kap / fabs(det);
+        auto row = [&](int a, int c) { return adj[a][0] * adj[c][0] + adj[a][1] * adj[c][1] + adj[a][2] * adj[c][2]; };
+        out[0 * npts + item] = f * row(0, 0);
+        out[1 * npts + item] = f * row(0, 1);
+        out[2 * npts + item] = f * row(0, 2);
+        out[3 * npts + item] = f * row(1, 1);
+        out[4 * npts + item] = f * row(1, 2);
+        out[5 * npts + item] = f * row(2, 2);
+    }
+}
+
+cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t nblocks,
+                        double* scratch, cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    launch_begin(K_COEF, s);
+    if (g.dim == 3) k_coef<3><<<(unsigned)nblocks, kBlock, 0, s>>>(g, T, bs, scratch);
+    else k_coef<2><<<(unsigned)nblocks, kBlock, 0, s>>>(g, T, bs, scratch);
+    launch_end(K_COEF, s);
+    return cudaGetLastError();
+}
+
+}  // namespace iga

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative to the largest stored entry, max |X - ref| / max |ref|):
+FP64 values 1e-12, FP32 values 1e-5 (FP64 quadrature rounded to FP32 on store
+and FP32 SpMV).  Small cases compare every entry; the full-size workloads
+compare sampled rows the oracle computes one by one, plus properties that
+hold at any size (symmetry, zero row sums).
+"""
+import numpy as np
+import pytest
+
+import iga_workloads as W
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 1e-5
+
+
+@pytest.fixture(scope="module")
+def iga():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_06971_gb300 as m
+    m.load()
+    return m
+
+
+def rel(X, ref):
+    return oracle.relative_entry_error(X, ref)
+
+
+def gpu_exact(iga, prob, dtype="f64"):
+    A = iga.assemble_exact(prob, dtype=dtype)
+    v = A.values_host()
+    A.destroy()
+    return v
+
+
+def gpu_surr(iga, prob, M, q, dtype="f64"):
+    A = iga.assemble_surrogate(prob, M, q, dtype=dtype)
+    v = A.values_host()
+    A.destroy()
+    return v
+
+
+SMALL_EXACT = [
+    W.CFG_2D_P2.problem,
+    W.Problem(dim=2, p=1, n_el=(7, 9), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.5),
+    W.Problem(dim=2, p=4, n_el=(13, 11), map_kind="sinprod", map_amp=0.04, kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.3),
+    W.Problem(dim=2, p=5, n_el=(6, 17), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.5),
+    W.Problem(dim=3, p=1, n_el=(5, 6, 4), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=3, p=2, n_el=(9, 7, 8), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=3, p=3, n_el=(6, 7, 5), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=3, p=4, n_el=(5, 5, 6), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=3, p=2, n_el=(6, 6, 6), map_kind="affine",
+              affine=(1.1, 0.2, -0.1, 0.05, 0.9, 0.3, -0.2, 0.1, 1.2, 0.1, 0.2, 0.3), kappa_kind="const", kappa_a=2.0),
+]
+
+
+@pytest.mark.parametrize("prob", SMALL_EXACT, ids=lambda q: f"{q.dim}d_p{q.p}_{'x'.join(map(str, q.n_el))}")
+def test_exact_full_matrix(iga, prob):
+    ref = oracle.exact_matrix(prob)
+    assert rel(gpu_exact(iga, prob), ref) <= TOL64
+
+
+def test_exact_f32(iga):
+    prob = SMALL_EXACT[6]
+    ref = oracle.exact_matrix(prob)
+    v = gpu_exact(iga, prob, "f32")
+    assert v.dtype == np.float32
+    assert rel(v, ref) <= TOL32
+
+
+SMALL_SURR = [
+    (W.CFG_2D_P2.problem, 4, 3),
+    (W.CFG_2D_P2.problem, 3, 2),
+    (W.CFG_2D_P2.problem, 5, 0),
+    (W.CFG_2D_P2.problem, 1, 3),            # M = 1: every Omega~ point is a sample
+    (W.CFG_2D_P2.problem, 40, 3),           # M > L: two samples, degree lowered to 1
+    (W.Problem(dim=2, p=1, n_el=(21, 17), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d",
+               kappa_a=1.0, kappa_b=0.5), 3, 5),
+    (W.Problem(dim=2, p=3, n_el=(30, 26), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d",
+               kappa_a=1.0, kappa_b=0.5), 4, 4),
+    (W.Problem(dim=2, p=5, n_el=(40, 33), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d",
+               kappa_a=1.0, kappa_b=0.5), 6, 7),
+    (W.Problem(dim=2, p=3, n_el=(9, 10), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d",
+               kappa_a=1.0, kappa_b=0.5), 4, 3),    # Omega~ empty: all rows exact
+    (W.Problem(dim=3, p=2, n_el=(13, 12, 14), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+               kappa_b=0.5), 3, 3),
+    (W.Problem(dim=3, p=3, n_el=(17, 15, 16), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+               kappa_b=0.5), 2, 3),
+    (W.Problem(dim=3, p=1, n_el=(11, 9, 10), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+               kappa_b=0.5), 2, 2),
+    (W.Problem(dim=3, p=4, n_el=(19, 18, 17), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+               kappa_b=0.5), 2, 1),
+]
+
+
+@pytest.mark.parametrize("prob,M,q", SMALL_SURR,
+                         ids=lambda x: f"{x.dim}d_p{x.p}_{'x'.join(map(str, x.n_el))}" if hasattr(x, "dim") else str(x))
+def test_surrogate_full_matrix(iga, prob, M, q):
+    ref = oracle.surrogate_matrix(prob, M, q)
+    got = gpu_surr(iga, prob, M, q)
+    assert rel(got, ref) <= TOL64
+
+
+def test_surrogate_f32(iga):
+    prob, M, q = SMALL_SURR[9]
+    ref = oracle.surrogate_matrix(prob, M, q)
+    assert rel(gpu_surr(iga, prob, M, q, "f32"), ref) <= TOL32
+
+
+def test_polynomial_reproduction_on_gpu(iga):
+    """Identity map, kappa in Q_3, q = 3: GPU surrogate == GPU exact (prop:PolynomialReproduction)."""
+    rng = np.random.default_rng(4)
+    coef = np.zeros(64)
+    coef[:64] = rng.uniform(0.1, 1.0, 64) / 64
+    coef[0] += 1.0
+    prob = W.Problem(dim=3, p=2, n_el=(16, 15, 14), kappa_kind="poly", kappa_deg=3, kappa_poly=tuple(coef))
+    ex = gpu_exact(iga, prob)
+    su = gpu_surr(iga, prob, 3, 3)
+    assert rel(su, ex) <= 1e-12
+    assert rel(ex, oracle.exact_matrix(prob)) <= TOL64
+
+
+def test_handle_reuse_and_spmv(iga):
+    prob = SMALL_SURR[10][0]
+    A = iga.assemble_surrogate(prob, 2, 3)
+    v1 = A.values_host()
+    iga.assemble_surrogate(prob, 2, 3, out=A)
+    v2 = A.values_host()
+    assert np.array_equal(v1, v2)            # deterministic, storage reused
+    x = W.normal_vector(prob.N, seed=3)
+    yref = oracle.apply(v1, prob, x)
+    y = A.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    scale = np.abs(v1).max() * np.abs(x).max()
+    assert np.abs(y - yref).max() <= 1e-13 * scale * prob.S
+    yh = A.apply_host(x)
+    assert np.array_equal(yh, y)
+    ones = torch.ones(prob.N, dtype=torch.float64, device="cuda")
+    assert A.apply(ones).abs().max().item() <= 1e-13 * np.abs(v1).max() * prob.S
+    A.destroy()
+
+
+def test_spmv_f32(iga):
+    prob = SMALL_EXACT[7]
+    A = iga.assemble_exact(prob, dtype="f32")
+    v = A.values_host()
+    x = W.normal_vector(prob.N, seed=5).astype(np.float32)
+    yref = oracle.apply(v.astype(np.float64), prob, x.astype(np.float64))
+    y = A.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    scale = np.abs(v).max() * np.abs(x).max() * prob.S
+    assert np.abs(y - yref).max() <= 1e-6 * scale
+    A.destroy()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: sampled rows + properties
+# ---------------------------------------------------------------------------
+def _sampled_rows(prob, k, seed):
+    """k random rows plus rows near the Omega~ boundary and the patch corners."""
+    p, m = prob.p, np.array(prob.m)
+    rows = list(W.sample_rows(prob.N, k, seed))
+    stride = np.cumprod([1] + list(m[:-1]))
+    special = [np.zeros(prob.dim, dtype=int), m - 1, np.full(prob.dim, 2 * p), np.full(prob.dim, 2 * p - 1),
+               m - 2 * p - 1, m - 2 * p, np.full(prob.dim, 3 * p), m // 2]
+    rows += [int((np.array(s) * stride).sum()) for s in special]
+    return np.unique(np.array(rows, dtype=np.int64))
+
+
+@pytest.mark.parametrize("wl", [W.CFG_3D_P3, W.CFG_3D_P4], ids=lambda w: w.name)
+def test_full_size_surrogate_sampled_rows(iga, wl):
+    prob = wl.problem
+    tol = TOL64 if wl.dtype == "f64" else TOL32
+    A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype)
+    vals = A.values()                                           # device [S, N]
+    rows = _sampled_rows(prob, 48, seed=1)
+    got = vals[:, torch.from_numpy(rows).cuda()].double().cpu().numpy().T
+    setup = oracle.surrogate_setup(prob, wl.M, wl.q)
+    ref = oracle.surrogate_rows(prob, wl.M, wl.q, rows, setup)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= tol * scale
+    # zero row sums at full size (Sec. 5.3): A~ 1 = 0
+    ones = torch.ones(prob.N, dtype=A.torch_dtype, device="cuda")
+    rs = A.apply(ones).double().abs().max().item()
+    assert rs <= (1e-12 if wl.dtype == "f64" else 1e-4) * scale
+    # symmetry at full size: slot s of row i equals slot S-1-s of row i + delta_s
+    offs = oracle.offsets(prob.dim, prob.p)
+    m = np.array(prob.m)
+    mi = oracle.multi_index(np.arange(prob.N), m)
+    worst = 0.0
+    for s in range(prob.S // 2 + 1, prob.S, max(1, prob.S // 40)):
+        mj = mi + offs[s]
+        ok = np.all((mj >= 0) & (mj < m), axis=1)
+        i = torch.from_numpy(np.nonzero(ok)[0]).cuda()
+        j = torch.from_numpy(oracle.surrogate.flat_index(mj[ok], m)).cuda()
+        d = (vals[s, i] - vals[prob.S - 1 - s, j]).abs().max().item()
+        worst = max(worst, d)
+    assert worst <= (1e-14 if wl.dtype == "f64" else 1e-6) * scale
+    A.destroy()
+
+
+def test_full_size_exact_sampled_rows(iga):
+    wl = W.CFG_3D_P3
+    prob = wl.problem
+    A = iga.assemble_exact(prob, dtype="f64")
+    vals = A.values()
+    rows = _sampled_rows(prob, 32, seed=2)
+    got = vals[:, torch.from_numpy(rows).cuda()].cpu().numpy().T
+    ref = oracle.exact_rows(prob, rows)
+    assert np.abs(got - ref).max() <= TOL64 * np.abs(ref).max()
+    A.destroy()
