@@ -1,0 +1,498 @@
+"""Benchmark: stiffness nonzeros assembled per second, surrogate vs exact, on one GB300.
+
+One step = the whole hot path once: surrogate assembly of the stiffness
+matrix (basis and pair tables, coefficient field, sum-factorised quadrature of
+the frame and sample rows, per-offset spline interpolation, surrogate fill
+with the kernel-preserving diagonal) followed by one stencil SpMV with it.
+The exact Gauss-quadrature assembly of the same patch is timed the same way
+and reported beside it.  Default workload: 3-D patch, p = 3, 64^3 elements,
+M = 8, q = 3, FP64 values (x_i = xi_i + 0.03 prod sin(pi xi_j),
+kappa = exp(0.5 sin(2 pi x) cos(2 pi y) sin(2 pi z))), synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+Under torchrun (N > 1) every rank assembles its own replica of the workload
+(the benchmark is one patch; replicas only) and the time is the max over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import iga_workloads as W  # noqa: E402
+
+METRIC = "stiffness nonzeros assembled/s, surrogate vs exact on GB300 at stated entry error"
+UNIT = "nnz/s"
+FP64_FLOPS_PER_SM_CLK = 4          # 2 FP64 FMA per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (rank 0 prints; time is the max over ranks)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index]) if device.type == "cuda" else dist.barrier()
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: units all ranks processed / max time over ranks."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work model of the quadrature stages (what the kernels execute)
+# ---------------------------------------------------------------------------
+def _boxes(prob, M, surrogate):
+    """Row boxes of the assembly: whole patch (exact) or frame slabs + one-row sample boxes."""
+    p, m, dim = prob.p, list(prob.m), prob.dim
+    if not surrogate:
+        return [[(0, md) for md in m]], 0
+    k0 = 2 * p
+    k1 = [md - 2 * p - 1 for md in m]
+    if any(b < k0 for b in k1):
+        return [[(0, md) for md in m]], 0
+    boxes = []
+    full = [(0, md) for md in m]
+    inner = [(k0, b - k0 + 1) for b in k1]
+    for d in reversed(range(dim)):
+        for lo, R in ((0, k0), (k1[d] + 1, m[d] - 1 - k1[d])):
+            bx = []
+            for e in range(dim):
+                if e == d:
+                    bx.append((lo, R))
+                elif e > d:
+                    bx.append(inner[e])
+                else:
+                    bx.append(full[e])
+            boxes.append(bx)
+    ns = [ (b - k0) // M + 1 + (1 if (b - k0) % M else 0) for b in k1]
+    return boxes, int(np.prod(ns))
+
+
+def stage_fmas(prob, M, surrogate):
+    """FP64 FMAs executed by stage Z / Y / X (per launch), closed form over the boxes."""
+    p, dim = prob.p, prob.dim
+    Q, Wd = p + 1, 2 * p + 1
+    n_el = list(prob.n_el)
+
+    def nvalid(i, ne):        # elements of supp(B_i) inside the mesh
+        return sum(1 for a in range(p + 1) if 0 <= i - p + a < ne)
+
+    def G(lo, R, ne):         # Gauss points of the box in one direction
+        elo = max(0, lo - p)
+        ehi = min(ne - 1, lo + R - 1)
+        return (ehi - elo + 1) * Q
+
+    boxes, nsamp = _boxes(prob, M, surrogate)
+    samp_box = [(2 * p, 1)] * dim
+    tot = {"stage_z": 0, "stage_y": 0, "stage_x": 0}
+    for bx, mult in [(b, 1) for b in boxes] + ([(samp_box, nsamp)] if nsamp else []):
+        sv = [sum(nvalid(i, n_el[d]) for i in range(bx[d][0], bx[d][0] + bx[d][1])) for d in range(dim)]
+        g = [G(bx[d][0], bx[d][1], n_el[d]) for d in range(dim)]
+        R = [bx[d][1] for d in range(dim)]
+        if dim == 3:
+            tot["stage_z"] += mult * 8 * Q * Q * sv[2] * g[1] * g[0]
+            tot["stage_y"] += mult * 9 * Q * Q * sv[1] * (R[2] * Wd) * g[0]
+            tot["stage_x"] += mult * 4 * Q * Q * sv[0] * (R[2] * Wd) * (R[1] * Wd)
+        else:
+            tot["stage_y"] += mult * 4 * Q * Q * sv[1] * g[0]
+            tot["stage_x"] += mult * 4 * Q * Q * sv[0] * (R[1] * Wd)
+    return tot
+
+
+def kernel_work(prob, wl, surrogate=True):
+    """Per-launch algorithmic work: FP64 flops for the contraction stages, bytes for the SpMV."""
+    esz = 8 if wl.dtype == "f64" else 4
+    fm = stage_fmas(prob, wl.M, surrogate)
+    work = {k: {"bound": "alu", "flops": 2.0 * v} for k, v in fm.items() if v}
+    work["spmv"] = {"bound": "hbm", "bytes": float(prob.S * prob.N * esz + 2 * prob.N * esz)}
+    return work
+
+
+def source_hash(rel_path: str) -> str:
+    with open(os.path.join(ROOT, rel_path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+KERNEL_SOURCE = {"stage_z": "paper_1904_06971_gb300/csrc/k_quad.cu", "stage_y": "paper_1904_06971_gb300/csrc/k_quad.cu",
+                 "stage_x": "paper_1904_06971_gb300/csrc/k_quad.cu", "coef": "paper_1904_06971_gb300/csrc/k_tables.cu",
+                 "fill": "paper_1904_06971_gb300/csrc/k_spline.cu", "spmv": "paper_1904_06971_gb300/csrc/k_spmv.cu"}
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        rec = d.get(workload, {}).get(kernel)
+        if rec and rec.get("source_sha") == source_hash(KERNEL_SOURCE.get(kernel, "bench.py")):
+            return float(rec["dram_bytes_per_launch"])
+    except (ValueError, KeyError, OSError):
+        return None
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path)), "measured"
+        except ValueError:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_throughput(wl, rows_budget: int, seed: int):
+    """Oracle surrogate assembly on a bounded sample: the sample-row setup in full plus
+    `rows_budget` seeded random rows, extrapolated to every row."""
+    import oracle
+    prob = wl.problem
+    t0 = time.perf_counter()
+    setup = oracle.surrogate_setup(prob, wl.M, wl.q)
+    t1 = time.perf_counter()
+    rows = W.sample_rows(prob.N, rows_budget, seed=seed)
+    oracle.surrogate_rows(prob, wl.M, wl.q, rows, setup)
+    t2 = time.perf_counter()
+    t_full = (t1 - t0) + (t2 - t1) * prob.N / len(rows)
+    n_setup = int(np.prod([len(s) for s in setup.samples])) if not setup.empty else 0
+    return prob.nnz / t_full, t2 - t0, {
+        "t_setup": t1 - t0, "t_rows": t2 - t1,
+        "cores": oracle.num_threads(),
+        "sample": f"oracle surrogate assembly: all {n_setup} exact sample rows plus {len(rows)} of {prob.N} rows "
+                  f"(seeded uniform, seed {seed}), time extrapolated to all rows",
+    }
+
+
+def cpu_baseline(wl, target_s: float = 15.0):
+    # calibrate the row count so that the sample costs ~target_s seconds of CPU work
+    v, dt, info = oracle_throughput(wl, 64, seed=0)
+    per_row = info["t_rows"] / 64
+    k = int(min(wl.problem.N, max(64, (target_s - info["t_setup"]) / max(per_row, 1e-6))))
+    v, dt, info = oracle_throughput(wl, k, seed=1)
+    out = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
+           "seconds": dt}
+    return out
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, dt, info = oracle_throughput(wl, args.ref_rows, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.problem.nnz / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded); FP64 CPU oracle on the host cores",
+        "config": config_of(wl, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                         "sample": info["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(wl, world):
+    prob = wl.problem
+    return {"workload": wl.name, "dim": prob.dim, "p": prob.p, "n_el": list(prob.n_el), "M": wl.M, "q": wl.q,
+            "map": f"{prob.map_kind} amp {prob.map_amp}",
+            "kappa": f"{prob.kappa_kind} a {prob.kappa_a} b {prob.kappa_b}",
+            "N": prob.N, "nnz": prob.nnz, "slots": prob.S * prob.N, "values": wl.dtype,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "256 MiB L2 flush written between timed steps; each step writes > 1 GB"}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_gpu(args, wl):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    import paper_1904_06971_gb300 as iga
+    iga.load()
+    prob = wl.problem
+    stream = torch.cuda.current_stream()
+    A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype)
+    E = iga.assemble_exact(prob, dtype=wl.dtype)
+    tdt = A.torch_dtype
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dtype=tdt, device=dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)     # 256 MiB > L2
+
+    def step_surr():
+        iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A)
+        A.apply(x, y)
+
+    def step_exact():
+        iga.assemble_exact(prob, dtype=wl.dtype, out=E)
+        E.apply(x, y)
+
+    def timed(step, K, W_, profile=False, clocks=None):
+        for _ in range(W_):
+            step()
+        torch.cuda.synchronize()
+        barrier(dist, dev)
+        if profile:
+            iga.profile_read()
+            iga.profile_enable(True)
+        if clocks:
+            clocks.start()
+        l0 = iga.launch_count()
+        evs = []
+        t0 = time.perf_counter()
+        for _ in range(K):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier(dist, dev)
+        launches = iga.launch_count() - l0
+        clk = clocks.stop() if clocks else None
+        prof = None
+        if profile:
+            iga.profile_enable(False)
+            prof = iga.profile_read()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        return ms, launches, prof, clk, wall
+
+    clocks = Clocks(local) if rank == 0 else None
+    if args.mode == "exact":            # profiling helper: the exact step alone
+        ms_e, launches_e, prof_e, _, _ = timed(step_exact, args.steps, args.warmup, profile=True)
+        if rank == 0:
+            print(json.dumps({"mode": "exact", "ms_per_step": ms_e, "kernels": prof_e}))
+        return 0
+    ms_s, launches, prof, clk, _ = timed(step_surr, args.steps, args.warmup, profile=True, clocks=clocks)
+    if args.mode == "surrogate":        # profiling helper: the surrogate step alone
+        if rank == 0:
+            print(json.dumps({"mode": "surrogate", "ms_per_step": ms_s, "kernels": prof}))
+        return 0
+    ms_e, launches_e, prof_e, _, _ = timed(step_exact, max(3, args.steps // 2), args.warmup, profile=True)
+    ms_s_max = max_over_ranks(dist, ms_s, dev)
+    ms_e_max = max_over_ranks(dist, ms_e, dev)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    xh = torch.empty(prob.N, dtype=tdt, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty(prob.N, dtype=tdt, pin_memory=True)
+    xn, yn = xh.numpy(), yh.numpy()
+    esz = 8 if wl.dtype == "f64" else 4
+
+    def step_e2e():
+        iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A)
+        A.apply_host(xn, yn)
+
+    for _ in range(args.warmup):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier(dist, dev)
+    K2 = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        step_e2e()
+    t_e2e = (time.perf_counter() - t0) / K2
+    t_e2e = max_over_ranks(dist, t_e2e, dev)
+
+    # stated entry error of the surrogate: max |A~ - A| / max |A| over all stored entries (GPU copies)
+    vs, ve = A.values(), E.values()
+    entry_err = float((vs.double() - ve.double()).abs().max().item() / ve.double().abs().max().item())
+    del vs, ve
+    rowsum = float(A.apply(torch.ones_like(x)).double().abs().max().item())
+
+    if rank != 0:
+        return 0
+    peaks, peak_kind = measured_peaks()
+    work = kernel_work(prob, wl, surrogate=True)
+    per_kernel = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
+    dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dom = per_kernel[dominant]
+    avg_ms = dom["ms"] / dom["launches"]
+    sm_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if dominant in work and work[dominant]["bound"] == "alu":
+        achieved = work[dominant]["flops"] / (avg_ms * 1e-3) / 1e12
+        peak = 152 * FP64_FLOPS_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": dominant, "pipe": "fp64",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x max SM clock (nominal 1.25 TFLOP/s)"}
+    elif dominant in work:
+        achieved = work[dominant]["bytes"] / (avg_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "kernel": dominant, "peak_source": f"{peak_kind} hbm_gbs"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "kernel": dominant}
+    roof["traffic"] = ncu_traffic(dominant, wl.name)
+    roof["avg_launch_ms"] = avg_ms
+    # SpMV against HBM, from the same timed region
+    if "spmv" in per_kernel:
+        sp = per_kernel["spmv"]
+        gbs = work["spmv"]["bytes"] / (sp["ms"] / sp["launches"] * 1e-3) / 1e9
+        spmv_roof = {"achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": gbs / float(peaks["hbm_gbs"]), "ms": sp["ms"] / sp["launches"]}
+    else:
+        spmv_roof = None
+
+    value = aggregate_value(prob.nnz, world, ms_s_max * 1e-3)
+    exact_value = aggregate_value(prob.nnz, world, ms_e_max * 1e-3)
+    base = None
+    if world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(wl, target_s=args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_s_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic (seeded map/coefficient family, x ~ N(0,1))",
+        "config": config_of(wl, world),
+        "exact": {"value": exact_value, "unit": UNIT, "ms_per_step": ms_e_max,
+                  "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof_e.items() if v[0]}},
+        "speedup_surrogate_vs_exact": ms_e_max / ms_s_max,
+        "entry_error": {"surrogate_vs_exact_max_rel": entry_err, "row_sum_max_abs": rowsum},
+        "kernels": per_kernel,
+        "roofline": roof,
+        "spmv_roofline": spmv_roof,
+        "cpu_baseline": base,
+        "e2e": {"value": aggregate_value(prob.nnz, world, t_e2e), "unit": UNIT,
+                "h2d_bytes_per_step": prob.N * esz, "d2h_bytes_per_step": prob.N * esz},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default=W.CFG_3D_P3.name, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the oracle baseline")
+    ap.add_argument("--ref-rows", type=int, default=48, help="rows per step of the reference (oracle) arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["both", "surrogate", "exact"], default="both",
+                    help="profiling helper: time only one of the two steps and print a short line")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = W.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

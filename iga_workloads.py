@@ -86,7 +86,14 @@ CFG_3D_P4 = Workload(
             kappa_kind="expsin3d", kappa_b=0.5),
     M=8, q=3, dtype="f32")
 
-WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4)}
+# Smaller member of the p = 3 family for profiler captures (values 218 MB > L2).
+CFG_3D_P3_40 = Workload(
+    "3d_p3_40cube_M8_q3",
+    Problem(dim=3, p=3, n_el=(40, 40, 40), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="expsin3d", kappa_b=0.5),
+    M=8, q=3, dtype="f64")
+
+WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4, CFG_3D_P3_40)}
 
 
 def scaled(w: Workload, n_el: Tuple[int, ...], M: Optional[int] = None, p: Optional[int] = None) -> Workload:

@@ -1,0 +1,122 @@
+"""Host-side logic of bench.py (no GPU): the max-over-ranks timing and whole-job
+aggregation across 2 gloo ranks, the closed-form FMA model of the quadrature
+stages against brute-force loop counting, and the oracle reference arm."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import iga_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank))
+    dist = bench.init_dist(world, "gloo")
+    t = bench.max_over_ranks(dist, 1.0 + rank, torch.device("cpu"))
+    bench.barrier(dist)
+    q.put((rank, t, bench.aggregate_value(100.0, world, t)))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [2.0, 2.0]          # max over ranks
+    assert [o[2] for o in out] == [100.0, 100.0]      # 100 units x 2 ranks / 2 s
+
+
+def _brute_stage_fmas(prob, M, surrogate):
+    """Count the FMAs of the three stage loops literally (tiny problems)."""
+    p, dim = prob.p, prob.dim
+    Q, Wd = p + 1, 2 * p + 1
+    boxes, ns = bench._boxes(prob, M, surrogate)
+    if ns:
+        k0 = 2 * p
+        samples = []
+        for d in range(dim):
+            k1 = prob.m[d] - 2 * p - 1
+            s = list(range(k0, k1 + 1, M))
+            if s[-1] != k1:
+                s.append(k1)
+            samples.append(s)
+        import itertools
+        for c in itertools.product(*samples):
+            boxes = boxes + [[(ci, 1) for ci in c]]
+    tot = {"stage_z": 0, "stage_y": 0, "stage_x": 0}
+    for bx in boxes:
+        G = []
+        for d in range(dim):
+            lo, R = bx[d]
+            elo, ehi = max(0, lo - p), min(prob.n_el[d] - 1, lo + R - 1)
+            G.append((ehi - elo + 1) * Q)
+
+        def per_row(i, d):
+            n = 0
+            for t in range(Q * Q):
+                e = i - p + t // Q
+                if not (0 <= e < prob.n_el[d]):
+                    continue
+                for dd in range(Wd):
+                    dl = dd - p
+                    if max(0, dl) <= t // Q <= p + min(0, dl):
+                        n += 1
+            return n
+        rows = [range(bx[d][0], bx[d][0] + bx[d][1]) for d in range(dim)]
+        if dim == 3:
+            tot["stage_z"] += 8 * sum(per_row(i, 2) for i in rows[2]) * G[1] * G[0]
+            tot["stage_y"] += 9 * sum(per_row(i, 1) for i in rows[1]) * bx[2][1] * Wd * G[0]
+            tot["stage_x"] += 4 * sum(per_row(i, 0) for i in rows[0]) * bx[2][1] * Wd * bx[1][1] * Wd
+        else:
+            tot["stage_y"] += 4 * sum(per_row(i, 1) for i in rows[1]) * G[0]
+            tot["stage_x"] += 4 * sum(per_row(i, 0) for i in rows[0]) * bx[1][1] * Wd
+    return tot
+
+
+@pytest.mark.parametrize("prob,M,surr", [
+    (W.Problem(dim=3, p=2, n_el=(13, 12, 14)), 3, True),
+    (W.Problem(dim=3, p=3, n_el=(9, 8, 10)), 2, False),
+    (W.Problem(dim=2, p=2, n_el=(20, 23)), 4, True),
+])
+def test_stage_fma_model_matches_loop_count(prob, M, surr):
+    got = bench.stage_fmas(prob, M, surr)
+    ref = _brute_stage_fmas(prob, M, surr)
+    assert got == ref
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--workload", W.CFG_2D_P2.name, "--ref-rows", "64"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "nnz/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["workload"] == W.CFG_2D_P2.name
