@@ -163,6 +163,29 @@ int iga_profile_read(int n, int64_t* launches, double* ms);
 int iga_num_kernels(void);
 const char* iga_kernel_name(int k);
 
+/*
+ * Exact assembly that allocates no memory (the paper has no counterpart; this
+ * serves callers that may not allocate device memory during a call -- e.g.
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise or
+ * stall, or applications whose own allocator owns the GPU's memory).
+ *   values: caller-owned DEVICE buffer of S * N elements of dtype (double or
+ *   float), written with the stencil-ELL layout above; the other arguments
+ *   are those of iga_assemble_exact, and the result equals its values.
+ * Scratch: one file-scope device array of 64 MiB that every GPU which loads
+ * this library reserves until the process exits.  A patch whose quadrature
+ * scratch exceeds 64 MiB is rejected with IGA_EUNSUPPORTED before any work
+ * (e.g. 3-D p = 3 fits up to about 12^3 elements, p = 2 up to 16^3; 2-D p = 2
+ * up to several hundred elements per direction).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Every call uses the same array, so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  No part of the array needs to start at zero: every word a call
+ * reads is written earlier in the same call.
+ */
+int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const iga_map_t* map,
+                               const iga_kappa_t* kappa, int dtype, void* values, void* stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* iga_last_error(void);
 

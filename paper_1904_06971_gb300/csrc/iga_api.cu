@@ -403,6 +403,12 @@ void launch_begin(int kid, cudaStream_t s)
     }
 }
 
+int report_error(int code, const char* msg)
+{
+    t_err = msg ? msg : "";
+    return code;
+}
+
 void launch_end(int kid, cudaStream_t s)
 {
     if (!t_begin) return;

@@ -102,6 +102,9 @@ enum KernelId {
 void launch_begin(int kid, cudaStream_t s);
 void launch_end(int kid, cudaStream_t s);
 
+// Sets the calling thread's iga_last_error() message; returns code.
+int report_error(int code, const char* msg);
+
 // ---- launchers implemented in the kernel files; all return cudaError_t ----
 cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[3],
                          double* bv[3], double* bd[3], double* wq[3], cudaStream_t s);

@@ -1,0 +1,98 @@
+"""iga_assemble_exact_noalloc: exact assembly for callers that may not allocate
+device memory during a call (latency-critical loops where cudaMalloc/cudaFree
+would synchronise or stall, or applications whose own allocator owns the GPU's
+memory).  It takes its scratch from a fixed 64 MiB device array in the library
+and writes into a caller-owned buffer.
+
+Checked through the C ABI against iga_assemble_exact, within the FP64 / FP32
+parity tolerances of the other GPU tests, on consecutive calls that reuse the
+same scratch array (its contents left by the previous call must not matter),
+and for the clear rejection of patches whose scratch exceeds the array.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import iga_workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def iga():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_06971_gb300 as m
+    m.load()
+    return m
+
+
+def call_noalloc(iga, prob, out, dtype):
+    L = iga.load()
+    f = L.iga_assemble_exact_noalloc
+    f.argtypes = [ctypes.POINTER(iga.Patch), ctypes.c_int, ctypes.POINTER(iga.Map), ctypes.POINTER(iga.Kappa),
+                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    pt, mp, kp = iga._structs(prob)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = f(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp), 0 if dtype == "f64" else 1,
+           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+    torch.cuda.synchronize()
+    return rc
+
+
+def rel(x, ref):
+    return float(np.abs(x.astype(np.float64) - ref.astype(np.float64)).max() / np.abs(ref).max())
+
+
+CASES = [
+    (W.CFG_2D_P2.problem, "f64"),
+    (W.Problem(dim=3, p=3, n_el=(10, 9, 11), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+               kappa_b=0.5), "f64"),
+    (W.Problem(dim=3, p=2, n_el=(12, 13, 11), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+               kappa_b=0.5), "f32"),
+]
+
+
+def _reference(iga, prob, dtype):
+    A = iga.assemble_exact(prob, dtype=dtype)
+    v = A.values_host()
+    A.destroy()
+    return v
+
+
+def test_noalloc_matches_exact_on_consecutive_calls(iga):
+    refs = [_reference(iga, prob, dt) for prob, dt in CASES]
+    # two passes over all cases: every call finds the scratch left by another call
+    for _ in range(2):
+        for (prob, dt), ref in zip(CASES, refs):
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            out = torch.full((prob.S, prob.N), float("nan"), dtype=tdt, device="cuda")
+            assert call_noalloc(iga, prob, out, dt) == 0, iga.load().iga_last_error().decode()
+            got = out.cpu().numpy()
+            assert np.isfinite(got).all()
+            assert rel(got, ref) <= TOL[dt]
+
+
+def test_noalloc_twice_in_a_row_same_patch(iga):
+    prob, dt = CASES[1]
+    ref = _reference(iga, prob, dt)
+    for _ in range(2):
+        out = torch.full((prob.S, prob.N), float("nan"), dtype=torch.float64, device="cuda")
+        assert call_noalloc(iga, prob, out, dt) == 0
+        assert rel(out.cpu().numpy(), ref) <= TOL[dt]
+
+
+def test_noalloc_rejects_patches_beyond_its_scratch(iga):
+    prob = W.Problem(dim=3, p=3, n_el=(24, 24, 24), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+                     kappa_b=0.5)
+    out = torch.full((prob.S, prob.N), float("nan"), dtype=torch.float64, device="cuda")
+    rc = call_noalloc(iga, prob, out, "f64")
+    assert rc == -4
+    msg = iga.load().iga_last_error().decode()
+    assert "64 MiB" in msg
+    assert torch.isnan(out).all().item()          # nothing was launched
