@@ -35,6 +35,7 @@ import iga_workloads as W  # noqa: E402
 METRIC = "stiffness nonzeros assembled/s, surrogate vs exact on GB300 at stated entry error"
 UNIT = "nnz/s"
 FP64_FLOPS_PER_SM_CLK = 4          # 2 FP64 FMA per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
+FP32_FLOPS_PER_SM_CLK = 256        # 128 FP32 FMA per SM per clock (80.5 TFLOP/s at 2.07 GHz)
 
 
 # ---------------------------------------------------------------------------
@@ -193,13 +194,32 @@ def stage_fmas(prob, M, surrogate):
     return tot
 
 
-def kernel_work(prob, wl, surrogate=True):
-    """Per-launch algorithmic work: FP64 flops for the contraction stages, bytes for the SpMV."""
+# FP32 flops of one double-float multiply-accumulate (arith.cuh, PolDF::mac):
+# 1 FMUL + 3 FFMA + 8 FADD/FSUB = 15 flops in 12 instructions, so the FP32 pipe
+# caps this instruction mix at 15 / 24 = 62.5 % of its FFMA peak.
+DF64_FLOPS_PER_MAC = 15
+
+
+def kernel_work(prob, wl, arith: str, surrogate=True):
+    """Per-launch algorithmic work: flops of the contraction stages in the arithmetic
+    they run in, bytes for the SpMV."""
     esz = 8 if wl.dtype == "f64" else 4
     fm = stage_fmas(prob, wl.M, surrogate)
-    work = {k: {"bound": "alu", "flops": 2.0 * v} for k, v in fm.items() if v}
+    if arith == "fp64":
+        work = {k: {"bound": "alu", "pipe": "fp64", "flops": 2.0 * v} for k, v in fm.items() if v}
+    elif arith == "df64":
+        work = {k: {"bound": "alu", "pipe": "fp32 (double-float)", "flops": float(DF64_FLOPS_PER_MAC) * v}
+                for k, v in fm.items() if v}
+    else:
+        work = {k: {"bound": "alu", "pipe": "fp32", "flops": 2.0 * v} for k, v in fm.items() if v}
     work["spmv"] = {"bound": "hbm", "bytes": float(prob.S * prob.N * esz + 2 * prob.N * esz)}
     return work
+
+
+def alu_peak_tflops(pipe: str, sm_mhz: float) -> float:
+    """152 SMs x flops per SM per clock x clock: FP64 2 FMA/clk (4 flops), FP32 128 FMA/clk (256 flops)."""
+    per_clk = FP64_FLOPS_PER_SM_CLK if pipe == "fp64" else FP32_FLOPS_PER_SM_CLK
+    return 152 * per_clk * sm_mhz * 1e6 / 1e12
 
 
 def source_hash(rel_path: str) -> str:
@@ -414,18 +434,23 @@ def run_gpu(args, wl):
     if rank != 0:
         return 0
     peaks, peak_kind = measured_peaks()
-    work = kernel_work(prob, wl, surrogate=True)
+    arith = iga.get_arithmetic(wl.dtype)
+    work = kernel_work(prob, wl, arith, surrogate=True)
     per_kernel = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
     dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dom = per_kernel[dominant]
     avg_ms = dom["ms"] / dom["launches"]
     sm_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     if dominant in work and work[dominant]["bound"] == "alu":
+        pipe = work[dominant]["pipe"]
         achieved = work[dominant]["flops"] / (avg_ms * 1e-3) / 1e12
-        peak = 152 * FP64_FLOPS_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        peak = alu_peak_tflops("fp64" if pipe == "fp64" else "fp32", float(peaks.get("sm_max_mhz", 2070.0)))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "kernel": dominant, "pipe": "fp64",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x max SM clock (nominal 1.25 TFLOP/s)"}
+                "kernel": dominant, "pipe": pipe,
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x max SM clock (nominal 1.25 TFLOP/s)"
+                                if pipe == "fp64" else
+                                "derived: 152 SMs x 128 FP32 FMA/clk x max SM clock; the double-float "
+                                "instruction mix caps at 0.625 of it")}
     elif dominant in work:
         achieved = work[dominant]["bytes"] / (avg_ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
@@ -452,7 +477,9 @@ def run_gpu(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_s_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic (seeded map/coefficient family, x ~ N(0,1))",
+        "vs_baseline": None, "dtype": wl.dtype, "arith": {"contractions": arith, "coefficients": "fp64",
+                                                         "fill": "df64", "spmv": wl.dtype},
+        "data": "synthetic (seeded map/coefficient family, x ~ N(0,1))",
         "config": config_of(wl, world),
         "exact": {"value": exact_value, "unit": UNIT, "ms_per_step": ms_e_max,
                   "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof_e.items() if v[0]}},

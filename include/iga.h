@@ -69,6 +69,23 @@ extern "C" {
 #define IGA_KAPPA_EXPSIN3D 2    /* exp(b sin(2 pi x) cos(2 pi y) sin(2 pi z)) */
 #define IGA_KAPPA_POLY     3    /* sum_{a,b,c <= deg} poly[a + (deg+1)(b + (deg+1)c)] x^a y^b z^c, deg <= 3 */
 
+/*
+ * Arithmetic of the sum-factorised quadrature contractions (process-wide,
+ * chosen per value dtype).  The basis tables, the coefficient tensor and all
+ * accumulation into stored values are FP64 in every mode.
+ *   IGA_ARITH_FP64: native FP64 FMAs.
+ *   IGA_ARITH_DF64: double-float arithmetic on the FP32 units -- each value is
+ *     an unevaluated sum of two floats (about 48 significand bits), products
+ *     are formed exactly with an FMA and sums with an error-free two-sum.
+ *     GB300 runs FP32 about 64x faster than FP64, so this is the default for
+ *     IGA_F64 values; its results agree with FP64 to ~1e-14 relative to the
+ *     largest entry.
+ *   IGA_ARITH_FP32: FP32 FMAs (only for IGA_F32 values; the default there).
+ */
+#define IGA_ARITH_FP64 0
+#define IGA_ARITH_DF64 1
+#define IGA_ARITH_FP32 2
+
 typedef struct {
     int32_t dim;        /* n: 2 or 3 */
     int32_t n_el[3];    /* elements per direction (entries beyond dim ignored); n_el >= p + 1 (m >= 2p+1, Sec. 2.2) */
@@ -149,6 +166,11 @@ int iga_matrix_copy_values(iga_matrix_t A, void* dst, int dst_on_host, void* str
 /* Release A and its device storage (stream-ordered on the stream of its last assembly). NULL is a no-op. */
 int iga_matrix_destroy(iga_matrix_t A);
 
+/* Set / query the contraction arithmetic used by later assemblies of dtype
+ * values (IGA_F32 accepts all three, IGA_F64 only FP64 and DF64). */
+int iga_set_arithmetic(int dtype, int arith);
+int iga_get_arithmetic(int dtype);
+
 /*
  * Counters for benchmarking: number of kernels this library launched in the
  * calling process since start (monotone), and per-kernel device time.
@@ -185,6 +207,12 @@ const char* iga_kernel_name(int k);
  */
 int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const iga_map_t* map,
                                const iga_kappa_t* kappa, int dtype, void* values, void* stream);
+
+/* Self-test of the double-float sin / cos / exp used by the coefficient kernel:
+ * their maximum errors against CUDA's FP64 sincospi and exp on n points of
+ * their domains (|pi y| <= 0.5, |x| <= 1) go to errors[0..2] (sin and cos
+ * absolute, exp relative).  Synchronous; allocates a few bytes. */
+int iga_selftest_dfmath(int n, double* errors);
 
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* iga_last_error(void);

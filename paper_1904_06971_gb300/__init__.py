@@ -22,9 +22,11 @@ import numpy as np
 from . import _build
 
 __all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "load", "launch_count",
-           "profile_enable", "profile_read", "kernel_names", "F64", "F32"]
+           "profile_enable", "profile_read", "kernel_names", "set_arithmetic", "get_arithmetic",
+           "F64", "F32", "ARITH"]
 
 F64, F32 = 0, 1
+ARITH = {"fp64": 0, "df64": 1, "fp32": 2}
 _MAP = {"identity": 0, "affine": 1, "sinprod": 2}
 _KAPPA = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3}
 _lock = threading.Lock()
@@ -219,6 +221,16 @@ def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Opti
                                          int(M), int(q), _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)),
                                          ctypes.byref(h)))
     return out if out is not None else Matrix(h.value)
+
+
+def set_arithmetic(dtype, arith: str):
+    """Contraction arithmetic for later assemblies with `dtype` values: 'fp64', 'df64' or 'fp32'."""
+    _check(load().iga_set_arithmetic(_dtype_code(dtype), ARITH[arith]))
+
+
+def get_arithmetic(dtype) -> str:
+    code = load().iga_get_arithmetic(_dtype_code(dtype))
+    return {v: k for k, v in ARITH.items()}[code]
 
 
 def launch_count() -> int:

@@ -1,0 +1,81 @@
+// Arithmetic policies of the quadrature contractions.
+//
+// GB300 executes FP32 FMAs about 64x faster than FP64 FMAs, so FP64-accurate
+// contractions are also offered in double-float ("df64") arithmetic: a value
+// is an unevaluated sum hi + lo of two floats (about 48 significand bits), a
+// product is formed exactly with an FMA (Dekker/Ogita-Rump-Oishi error-free
+// product) and sums use Knuth's error-free two-sum, with the low parts
+// accumulated separately and renormalised when a sum is stored.  All the
+// error-free steps use the _rn intrinsics so the compiler cannot contract or
+// reorder them.
+//
+//   PolF64  : store double, accumulate double (FP64 pipe)
+//   PolDF   : store float2 (hi, lo), accumulate double-float (FP32 pipe)
+//   PolF32  : store float, accumulate float (FP32 pipe)
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace iga {
+
+enum Arith { kArithF64 = 0, kArithDF = 1, kArithF32 = 2 };
+
+struct PolF64 {
+    using store = double;
+    using acc = double;
+    static constexpr int kind = kArithF64;
+    __device__ __forceinline__ static acc zero() { return 0.0; }
+    __device__ __forceinline__ static void mac(acc& a, store x, store v) { a = fma(x, v, a); }
+    __device__ __forceinline__ static double to_double(const acc& a) { return a; }
+    __device__ __forceinline__ static store to_store(const acc& a) { return a; }
+    __device__ __forceinline__ static store from_double(double v) { return v; }
+};
+
+struct DFAcc {
+    float h, l;
+};
+
+struct PolDF {
+    using store = float2;
+    using acc = DFAcc;
+    static constexpr int kind = kArithDF;
+    __device__ __forceinline__ static acc zero() { return DFAcc{0.f, 0.f}; }
+    __device__ __forceinline__ static void mac(acc& a, store x, store v)
+    {
+        // x*v = ph + pe exactly for the high parts; the cross terms join pe
+        const float ph = __fmul_rn(x.x, v.x);
+        float pe = __fmaf_rn(x.x, v.x, -ph);
+        pe = __fmaf_rn(x.x, v.y, pe);
+        pe = __fmaf_rn(x.y, v.x, pe);
+        // two-sum of the running high part and ph
+        const float s = __fadd_rn(a.h, ph);
+        const float z = __fsub_rn(s, a.h);
+        const float t = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, z)), __fsub_rn(ph, z));
+        a.h = s;
+        a.l = __fadd_rn(a.l, __fadd_rn(t, pe));
+    }
+    __device__ __forceinline__ static double to_double(const acc& a) { return (double)a.h + (double)a.l; }
+    __device__ __forceinline__ static store to_store(const acc& a)
+    {
+        const float s = __fadd_rn(a.h, a.l);
+        return make_float2(s, __fsub_rn(a.l, __fsub_rn(s, a.h)));
+    }
+    __device__ __forceinline__ static store from_double(double v)
+    {
+        const float h = __double2float_rn(v);
+        return make_float2(h, __double2float_rn(v - (double)h));
+    }
+};
+
+struct PolF32 {
+    using store = float;
+    using acc = float;
+    static constexpr int kind = kArithF32;
+    __device__ __forceinline__ static acc zero() { return 0.f; }
+    __device__ __forceinline__ static void mac(acc& a, store x, store v) { a = __fmaf_rn(x, v, a); }
+    __device__ __forceinline__ static double to_double(const acc& a) { return (double)a; }
+    __device__ __forceinline__ static store to_store(const acc& a) { return a; }
+    __device__ __forceinline__ static store from_double(double v) { return __double2float_rn(v); }
+};
+
+}  // namespace iga

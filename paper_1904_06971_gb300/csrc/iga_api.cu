@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "arith.cuh"
 #include "iga_internal.cuh"
 
 using namespace iga;
@@ -42,6 +43,9 @@ int cuda_fail(cudaError_t e, const char* what)
 {
     return fail(e == cudaErrorMemoryAllocation ? IGA_ENOMEM : IGA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+// ---- contraction arithmetic per value dtype (process-wide) ----
+std::atomic<int> g_arith[2] = {{kArithDF}, {kArithF32}};
 
 // ---- launch counting and optional per-kernel event timing ----
 std::atomic<int64_t> g_launches{0};
@@ -263,13 +267,17 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
 
     // ---------------- scratch layout ----------------
     Layout lay;
-    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3];
+    const int arith = current_arith(dtype);
+    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3], o_Xs[3], o_tdf[3];
     for (int d = 0; d < 3; ++d) {
         const int64_t G = (d < dim) ? (int64_t)g.n_el[d] * Q : 1;
         const int64_t nX = (d < dim) ? (int64_t)4 * g.m[d] * W * TT : 1;
-        o_gx[d] = lay.take(G); o_sx[d] = lay.take(G); o_cx[d] = lay.take(G); o_wq[d] = lay.take(G);
+        o_gx[d] = lay.take(G); o_sx[d] = lay.take(2 * G); o_cx[d] = lay.take(2 * G); o_wq[d] = lay.take(G);
         o_bv[d] = lay.take(G * Q); o_bd[d] = lay.take(G * Q); o_X[d] = lay.take(nX);
+        o_Xs[d] = (arith == kArithF64) ? o_X[d] : lay.take(nX);
+        o_tdf[d] = lay.take(4 * G);
     }
+    prepare_coef_df(g, arith);
     int64_t nblk[4] = {0, 0, 0, 0};
     bs.nb = (int)boxes.size();
     for (int k = 0; k < bs.nb; ++k) {
@@ -284,7 +292,7 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         }
         bs.box[k] = b;
     }
-    int64_t o_samples = 0, o_lu[3] = {0, 0, 0}, o_eval[3] = {0, 0, 0}, o_partial = 0, o_ints = 0;
+    int64_t o_samples = 0, o_lu[3] = {0, 0, 0}, o_eval[3] = {0, 0, 0}, o_eval0 = 0, o_partial = 0, o_ints = 0;
     if (do_spline) {
         Box sbx;                         // shape of every sample box
         int lo[3] = {2 * p, 2 * p, 2 * p}, R[3] = {1, 1, 1};
@@ -305,6 +313,7 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
             o_lu[d] = lay.take((int64_t)sp.ns[d] * sp.ns[d]);
             o_eval[d] = lay.take((int64_t)sp.L[d] * (sp.qe[d] + 1));
         }
+        o_eval0 = lay.take((int64_t)sp.L[0] * (sp.qe[0] + 1));
         const int64_t S_up = S - 1 - sp.c;
         o_partial = lay.take(S_up * (dim == 3 ? sp.L[2] : 1) * (int64_t)sp.L[1] * sp.ns[0]);
         int64_t nints = 8;
@@ -343,15 +352,21 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     // ---------------- launches ----------------
     auto P = [&](int64_t off) { return scratch + off; };
     double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
+    void* Xs[3];
+    float2* tdf[3];
     for (int d = 0; d < 3; ++d) {
         gx[d] = P(o_gx[d]); sx[d] = P(o_sx[d]); cx[d] = P(o_cx[d]); wq[d] = P(o_wq[d]);
-        bv[d] = P(o_bv[d]); bd[d] = P(o_bd[d]); X[d] = P(o_X[d]);
+        bv[d] = P(o_bv[d]); bd[d] = P(o_bd[d]); X[d] = P(o_X[d]); Xs[d] = P(o_Xs[d]);
+        tdf[d] = reinterpret_cast<float2*>(P(o_tdf[d]));
     }
     Tables T;
-    for (int d = 0; d < 3; ++d) { T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; }
+    for (int d = 0; d < 3; ++d) {
+        T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
+    }
+    T.arith = arith;
     const char* stage = "basis tables";
-    ce = launch_basis(g, gx, sx, cx, bv, bd, wq, st);
-    if (ce == cudaSuccess) { stage = "pair tables"; ce = launch_pairs(g, bv, bd, wq, X, st); }
+    ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
+    if (ce == cudaSuccess) { stage = "pair tables"; ce = launch_pairs(g, bv, bd, wq, X, Xs, arith, st); }
     if (ce == cudaSuccess) { stage = "coefficient field"; ce = launch_coef(g, T, bs, nblk[0], scratch, st); }
     double* samples = do_spline ? P(o_samples) : nullptr;
     if (ce == cudaSuccess) {
@@ -370,7 +385,8 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
             sb.espan[d] = ints + io;
             io += sp.L[d] + 8;
         }
-        sb.partial = P(o_partial);
+        sb.eval0 = reinterpret_cast<float2*>(P(o_eval0));
+        sb.partial = reinterpret_cast<float2*>(P(o_partial));
         if (ce == cudaSuccess) { stage = "spline interpolation"; ce = launch_spline(g, sp, M, samples, sb, st); }
     }
     if (surrogate && ce == cudaSuccess) {
@@ -401,6 +417,11 @@ void launch_begin(int kid, cudaStream_t s)
     } else {
         t_begin = nullptr;
     }
+}
+
+int current_arith(int dtype)
+{
+    return g_arith[dtype == IGA_F32 ? 1 : 0].load();
 }
 
 int report_error(int code, const char* msg)
@@ -510,6 +531,29 @@ int iga_matrix_destroy(iga_matrix_t A)
     delete A;
     if (e != cudaSuccess) return cuda_fail(e, "freeing matrix values");
     return IGA_OK;
+}
+
+int iga_set_arithmetic(int dtype, int arith)
+{
+    t_err.clear();
+    if (dtype != IGA_F64 && dtype != IGA_F32) return fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
+    int a;
+    switch (arith) {
+    case IGA_ARITH_FP64: a = kArithF64; break;
+    case IGA_ARITH_DF64: a = kArithDF; break;
+    case IGA_ARITH_FP32: a = kArithF32; break;
+    default: return fail(IGA_EINVAL, "unknown arithmetic %d", arith);
+    }
+    if (dtype == IGA_F64 && a == kArithF32)
+        return fail(IGA_EINVAL, "FP32 contractions cannot meet FP64 accuracy; use IGA_ARITH_FP64 or IGA_ARITH_DF64");
+    g_arith[dtype == IGA_F32 ? 1 : 0].store(a);
+    return IGA_OK;
+}
+
+int iga_get_arithmetic(int dtype)
+{
+    const int a = current_arith(dtype);
+    return a == kArithF64 ? IGA_ARITH_FP64 : a == kArithDF ? IGA_ARITH_DF64 : IGA_ARITH_FP32;
 }
 
 int64_t iga_launch_count(void) { return g_launches.load(); }

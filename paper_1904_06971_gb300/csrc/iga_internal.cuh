@@ -22,6 +22,9 @@ struct Geo {
     int kappa_kind, kappa_deg;
     double ka, kb;
     double poly[64];
+    // double-float copies (hi, lo) of amp, ka, kb for the double-float coefficient path
+    float amp_df[2], ka_df[2], kb_df[2];
+    int coef_df;              // evaluate the coefficient tensor in double-float arithmetic
 };
 
 // A rectangular block of rows whose full stencil rows are computed by the
@@ -87,9 +90,12 @@ __device__ __forceinline__ void get_box(const BoxSet& bs, int dim, int p, int st
 // Per-direction device tables written by the basis kernels.
 struct Tables {
     const double* gx[3];      // [G]  Gauss point coordinates xi
-    const double* sx[3];      // [G]  sin(pi xi)
-    const double* cx[3];      // [G]  cos(pi xi)
-    const double* X[3];       // [4][m][2p+1][(p+1)^2] pair weights, see k_tables.cu
+    const double* sx[3];      // [2G] sin(pi xi), then sin(2 pi xi)
+    const double* cx[3];      // [2G] cos(pi xi), then cos(2 pi xi)
+    const double* X[3];       // [m][4][2p+1][(p+1)^2] pair weights (FP64), see k_tables.cu
+    const void* Xs[3];        // the same in the store type of the contraction arithmetic
+    const float2* tdf[3];     // [G][4] double-float sin(pi xi), pi cos(pi xi), sin(2 pi xi), cos(2 pi xi)
+    int arith;                // contraction arithmetic (arith.cuh: kArithF64 / kArithDF / kArithF32)
 };
 
 enum KernelId {
@@ -105,11 +111,19 @@ void launch_end(int kid, cudaStream_t s);
 // Sets the calling thread's iga_last_error() message; returns code.
 int report_error(int code, const char* msg);
 
+// Contraction arithmetic (arith.cuh kind) chosen for matrices of value type dtype.
+int current_arith(int dtype);
+
 // ---- launchers implemented in the kernel files; all return cudaError_t ----
 cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[3],
-                         double* bv[3], double* bd[3], double* wq[3], cudaStream_t s);
+                         double* bv[3], double* bd[3], double* wq[3], float2* tdf[3], cudaStream_t s);
+
+// Fill the double-float copies of the map / coefficient constants and decide
+// whether the coefficient tensor can be evaluated in double-float arithmetic
+// (sine-product map with |amp| <= 0.07, kappa constant / SIN2D / EXPSIN3D with |b| <= 1).
+void prepare_coef_df(Geo& g, int arith);
 cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
-                         double* const wq[3], double* X[3], cudaStream_t s);
+                         double* const wq[3], double* X[3], void* Xs[3], int arith, cudaStream_t s);
 cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t nblocks,
                         double* scratch, cudaStream_t s);
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
@@ -127,7 +141,8 @@ struct SplineBufs {
     int* band;                // [3][2] lower / upper bandwidth of the factors
     int* espan[3];            // [L] first nonzero interpolation basis index at box index k0 + k
     double* eval[3];          // [L][q+1] its values
-    double* partial;          // 3-D [S_up][L2][L1][ns0]; 2-D [S_up][L1][ns0]
+    float2* eval0;            // direction 0 values again, double-float pairs, transposed [q+1][L]
+    float2* partial;          // double-float; 3-D [S_up][L2][L1][ns0]; 2-D [S_up][L1][ns0]
 };
 cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* samples /* [S][n_samples] */,
                           const SplineBufs& sb, cudaStream_t s);

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "arith.cuh"
 #include "iga_internal.cuh"
 
 namespace {
@@ -115,18 +116,23 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
     }
     // scratch layout (doubles, 256-byte aligned pieces)
     int64_t off = 0;
-    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3];
+    const int arith = current_arith(dtype);
+    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3], o_Xs[3], o_tdf[3];
     for (int d = 0; d < 3; ++d) {
         const int64_t G = (d < g.dim) ? (int64_t)g.n_el[d] * Q : 1;
         const int64_t nX = (d < g.dim) ? (int64_t)4 * g.m[d] * W * TT : 1;
         o_gx[d] = off; off += up32(G);
-        o_sx[d] = off; off += up32(G);
-        o_cx[d] = off; off += up32(G);
+        o_sx[d] = off; off += up32(2 * G);
+        o_cx[d] = off; off += up32(2 * G);
         o_wq[d] = off; off += up32(G);
         o_bv[d] = off; off += up32(G * Q);
         o_bd[d] = off; off += up32(G * Q);
         o_X[d] = off; off += up32(nX);
+        if (arith == kArithF64) o_Xs[d] = o_X[d];
+        else { o_Xs[d] = off; off += up32(nX); }
+        o_tdf[d] = off; off += up32(4 * G);
     }
+    prepare_coef_df(g, arith);
     b.out_kind = 0;
     b.c_off = off; off += up32(box_coef_len(g.dim, p, b));
     b.t1_off = off; off += up32(box_t1_len(g.dim, p, b));
@@ -153,14 +159,21 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
 
     cudaStream_t st = (cudaStream_t)stream;
     double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
+    void* Xs[3];
+    float2* tdf[3];
     for (int d = 0; d < 3; ++d) {
         gx[d] = scratch + o_gx[d]; sx[d] = scratch + o_sx[d]; cx[d] = scratch + o_cx[d];
         wq[d] = scratch + o_wq[d]; bv[d] = scratch + o_bv[d]; bd[d] = scratch + o_bd[d]; X[d] = scratch + o_X[d];
+        Xs[d] = scratch + o_Xs[d];
+        tdf[d] = reinterpret_cast<float2*>(scratch + o_tdf[d]);
     }
     Tables T;
-    for (int d = 0; d < 3; ++d) { T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; }
-    e = launch_basis(g, gx, sx, cx, bv, bd, wq, st);
-    if (e == cudaSuccess) e = launch_pairs(g, bv, bd, wq, X, st);
+    for (int d = 0; d < 3; ++d) {
+        T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
+    }
+    T.arith = arith;
+    e = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
+    if (e == cudaSuccess) e = launch_pairs(g, bv, bd, wq, X, Xs, arith, st);
     if (e == cudaSuccess) e = launch_coef(g, T, bs, nblk[0], scratch, st);
     if (e == cudaSuccess) e = launch_stages(g, T, bs, nblk, scratch, values, dtype == IGA_F32, nullptr, st);
     if (e != cudaSuccess) return noalloc_fail(IGA_ECUDA, "no-allocation exact assembly: %s", cudaGetErrorString(e));

@@ -3,7 +3,7 @@
 // A_ij = sum_{k,l} sum_g K_kl(g) d_k B_i(g) d_l B_j(g) (Sec. 3.2, eq. ChangeOfVars)
 // factorises per direction: the Gauss points, the row index i_d and the
 // column offset delta_d = j_d - i_d of direction d meet only in the 1-D pair
-// weights X_d[pat][i_d][delta_d][t] (k_tables.cu).  The 3-D sum is
+// weights X_d[i_d][pat][delta_d][t] (k_tables.cu).  The 3-D sum is
 // contracted one direction at a time, slowest first, so every stage reads and
 // writes arrays whose fastest index is contiguous:
 //
@@ -17,23 +17,22 @@
 // (alpha, beta) puts a derivative on the row function (alpha) and/or the
 // column function (beta); the nine (k, l) terms are routed so that each
 // reaches its pattern (d_k on B_i, d_l on B_j) in every direction.
+//
+// The kernels are templated on the arithmetic policy (arith.cuh): FP64,
+// double-float on the FP32 pipe, or FP32.
+#include "arith.cuh"
 #include "iga_internal.cuh"
 
 namespace iga {
 
-// does local point t (element a = t / (P+1) of supp(B_i)) lie in supp(B_{i+delta})?
-template <int P>
-__device__ __forceinline__ constexpr bool in_overlap(int t, int dd)
-{
-    return (t / (P + 1)) >= ((dd - P) > 0 ? (dd - P) : 0) && (t / (P + 1)) <= P + ((dd - P) < 0 ? (dd - P) : 0);
-}
-
 // ---------------------------------------------------------------------------
 // stage Z: contract direction 2
 // ---------------------------------------------------------------------------
-template <int P>
+template <class Pol, int P>
 __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, double* scratch)
 {
+    using S = typename Pol::store;
+    using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     Box b;
     get_box(bs, 3, P, 1, blockIdx.x, b);
@@ -44,57 +43,60 @@ __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, 
     const int i3l = (int)(item / plane);
     const int64_t pp = item % plane;
     const int i3 = b.rlo[2] + i3l;
-    const int m2 = g.m[2];
-    const double* C = scratch + b.c_off;
+    const S* C = reinterpret_cast<const S*>(scratch + b.c_off);
     const int64_t fs = G2 * plane;
-    const double* X = T.X[2];
-    const int64_t ps = (int64_t)m2 * W * TT;            // pattern stride
-    const double* Xi = X + (int64_t)i3 * W * TT;
+    constexpr int ps = W * TT;                          // pattern stride
+    const S* Xi = reinterpret_cast<const S*>(T.Xs[2]) + (int64_t)i3 * 4 * W * TT;
 
-    double acc[W][8];
+    A acc[W][8];
 #pragma unroll
     for (int dd = 0; dd < W; ++dd)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[dd][k] = 0.0;
+        for (int k = 0; k < 8; ++k) acc[dd][k] = Pol::zero();
 
+    // local element a of supp(B_i) meets supp(B_{i+delta}) exactly for dd = delta + P in [a, a + P]
 #pragma unroll
-    for (int t = 0; t < TT; ++t) {
-        const int e3 = i3 - P + t / Q;
+    for (int a = 0; a <= P; ++a) {
+        const int e3 = i3 - P + a;
         if (e3 < b.elo[2] || e3 >= b.elo[2] + b.E[2]) continue;
-        const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + t % Q) * plane + pp;
-        const double c0 = C[o], c1 = C[fs + o], c2 = C[2 * fs + o];
-        const double c3 = C[3 * fs + o], c4 = C[4 * fs + o], c5 = C[5 * fs + o];
+#pragma unroll 1
+        for (int r = 0; r < Q; ++r) {
+        const int t = a * Q + r;
+        const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + r) * plane + pp;
+        const S c0 = C[o], c1 = C[fs + o], c2 = C[2 * fs + o];
+        const S c3 = C[3 * fs + o], c4 = C[4 * fs + o], c5 = C[5 * fs + o];
 #pragma unroll
-        for (int dd = 0; dd < W; ++dd) {
-            if (!in_overlap<P>(t, dd)) continue;
-            const int64_t xo = (int64_t)dd * TT + t;
-            const double x00 = __ldg(Xi + xo), x01 = __ldg(Xi + ps + xo);
-            const double x10 = __ldg(Xi + 2 * ps + xo), x11 = __ldg(Xi + 3 * ps + xo);
-            acc[dd][0] = fma(x00, c0, acc[dd][0]);
-            acc[dd][1] = fma(x00, c1, acc[dd][1]);
-            acc[dd][2] = fma(x00, c3, acc[dd][2]);
-            acc[dd][3] = fma(x01, c2, acc[dd][3]);
-            acc[dd][4] = fma(x10, c2, acc[dd][4]);
-            acc[dd][5] = fma(x01, c4, acc[dd][5]);
-            acc[dd][6] = fma(x10, c4, acc[dd][6]);
-            acc[dd][7] = fma(x11, c5, acc[dd][7]);
+        for (int dd = a; dd <= a + P; ++dd) {
+            const int xo = dd * TT + t;
+            const S x00 = Xi[xo], x01 = Xi[ps + xo], x10 = Xi[2 * ps + xo], x11 = Xi[3 * ps + xo];
+            Pol::mac(acc[dd][0], x00, c0);
+            Pol::mac(acc[dd][1], x00, c1);
+            Pol::mac(acc[dd][2], x00, c3);
+            Pol::mac(acc[dd][3], x01, c2);
+            Pol::mac(acc[dd][4], x10, c2);
+            Pol::mac(acc[dd][5], x01, c4);
+            Pol::mac(acc[dd][6], x10, c4);
+            Pol::mac(acc[dd][7], x11, c5);
+        }
         }
     }
-    double* T1 = scratch + b.t1_off;
+    S* T1 = reinterpret_cast<S*>(scratch + b.t1_off);
     const int64_t P3 = (int64_t)b.R[2] * W;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
-            T1[((int64_t)k * P3 + (int64_t)i3l * W + dd) * plane + pp] = acc[dd][k];
+            T1[((int64_t)k * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
 }
 
 // ---------------------------------------------------------------------------
 // stage Y: contract direction 1
 // ---------------------------------------------------------------------------
-template <int P, int DIM>
+template <class Pol, int P, int DIM>
 __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, double* scratch)
 {
+    using S = typename Pol::store;
+    using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     constexpr int NIN = (DIM == 3) ? 8 : 3;
     Box b;
@@ -108,83 +110,89 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
     const int i2l = (int)((item / G0) % R2);
     const int64_t pair3 = item / (G0 * R2);
     const int i2 = b.rlo[1] + i2l;
-    const int m1 = g.m[1];
-    const double* X = T.X[1];
-    const int64_t ps = (int64_t)m1 * W * TT;
-    const double* Xi = X + (int64_t)i2 * W * TT;
+    constexpr int ps = W * TT;
+    const S* Xi = reinterpret_cast<const S*>(T.Xs[1]) + (int64_t)i2 * 4 * W * TT;
 
     // input field f at local Gauss point g1 of direction 1
-    const double* in;
-    int64_t fstride, rowstride;
+    const S* in;
+    int64_t fstride;
     if (DIM == 3) {
-        in = scratch + b.t1_off + pair3 * G1 * G0 + g0;
+        in = reinterpret_cast<const S*>(scratch + b.t1_off) + pair3 * G1 * G0 + g0;
         fstride = P3 * G1 * G0;
-        rowstride = G0;
     } else {
-        in = scratch + b.c_off + g0;
+        in = reinterpret_cast<const S*>(scratch + b.c_off) + g0;
         fstride = G1 * G0;
-        rowstride = G0;
     }
 
-    double acc[W][4];
+    A acc[W][4];
 #pragma unroll
     for (int dd = 0; dd < W; ++dd)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[dd][k] = 0.0;
+        for (int k = 0; k < 4; ++k) acc[dd][k] = Pol::zero();
 
 #pragma unroll
-    for (int t = 0; t < TT; ++t) {
-        const int e2 = i2 - P + t / Q;
+    for (int a = 0; a <= P; ++a) {
+        const int e2 = i2 - P + a;
         if (e2 < b.elo[1] || e2 >= b.elo[1] + b.E[1]) continue;
-        const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + t % Q) * rowstride;
-        double v[NIN];
+#pragma unroll 1
+        for (int r = 0; r < Q; ++r) {
+        const int t = a * Q + r;
+        const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + r) * G0;
+        S v[NIN];
 #pragma unroll
         for (int f = 0; f < NIN; ++f) v[f] = in[f * fstride + o];
 #pragma unroll
-        for (int dd = 0; dd < W; ++dd) {
-            if (!in_overlap<P>(t, dd)) continue;
-            const int64_t xo = (int64_t)dd * TT + t;
-            const double x00 = __ldg(Xi + xo), x01 = __ldg(Xi + ps + xo);
-            const double x10 = __ldg(Xi + 2 * ps + xo), x11 = __ldg(Xi + 3 * ps + xo);
+        for (int dd = a; dd <= a + P; ++dd) {
+            const int xo = dd * TT + t;
+            const S x00 = Xi[xo], x01 = Xi[ps + xo], x10 = Xi[2 * ps + xo], x11 = Xi[3 * ps + xo];
             if (DIM == 3) {
-                // A^00 -> group 0 (pattern 11 left in direction 0)
-                acc[dd][0] = fma(x00, v[0], acc[dd][0]);
-                // A^01 (K01, 01) and A^02 (K02 combo 01 from direction 2, 00 here) -> group 1 (10)
-                acc[dd][1] = fma(x01, v[1], acc[dd][1]);
-                acc[dd][1] = fma(x00, v[3], acc[dd][1]);
-                // A^10 and A^20 -> group 2 (01)
-                acc[dd][2] = fma(x10, v[1], acc[dd][2]);
-                acc[dd][2] = fma(x00, v[4], acc[dd][2]);
-                // A^11, A^12, A^21, A^22 -> group 3 (00)
-                acc[dd][3] = fma(x11, v[2], acc[dd][3]);
-                acc[dd][3] = fma(x10, v[5], acc[dd][3]);
-                acc[dd][3] = fma(x01, v[6], acc[dd][3]);
-                acc[dd][3] = fma(x00, v[7], acc[dd][3]);
+                Pol::mac(acc[dd][0], x00, v[0]);   // A^00 -> group 0 (11 left in direction 0)
+                Pol::mac(acc[dd][1], x01, v[1]);   // A^01 -> group 1 (10)
+                Pol::mac(acc[dd][1], x00, v[3]);   // A^02 -> group 1
+                Pol::mac(acc[dd][2], x10, v[1]);   // A^10 -> group 2 (01)
+                Pol::mac(acc[dd][2], x00, v[4]);   // A^20 -> group 2
+                Pol::mac(acc[dd][3], x11, v[2]);   // A^11 -> group 3 (00)
+                Pol::mac(acc[dd][3], x10, v[5]);   // A^12 -> group 3
+                Pol::mac(acc[dd][3], x01, v[6]);   // A^21 -> group 3
+                Pol::mac(acc[dd][3], x00, v[7]);   // A^22 -> group 3
             } else {
-                acc[dd][0] = fma(x00, v[0], acc[dd][0]);   // A^00: K00, 00
-                acc[dd][1] = fma(x01, v[1], acc[dd][1]);   // A^01: K01, 01
-                acc[dd][2] = fma(x10, v[1], acc[dd][2]);   // A^10: K01, 10
-                acc[dd][3] = fma(x11, v[2], acc[dd][3]);   // A^11: K11, 11
+                Pol::mac(acc[dd][0], x00, v[0]);   // A^00: K00, 00
+                Pol::mac(acc[dd][1], x01, v[1]);   // A^01: K01, 01
+                Pol::mac(acc[dd][2], x10, v[1]);   // A^10: K01, 10
+                Pol::mac(acc[dd][3], x11, v[2]);   // A^11: K11, 11
             }
         }
+        }
     }
-    double* T2 = scratch + b.t2_off;
+    S* T2 = reinterpret_cast<S*>(scratch + b.t2_off);
     const int64_t P2 = (int64_t)R2 * W;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
-            T2[(((int64_t)k * P3 + pair3) * P2 + (int64_t)i2l * W + dd) * G0 + g0] = acc[dd][k];
+            T2[(((int64_t)k * P3 + pair3) * P2 + (int64_t)i2l * W + dd) * G0 + g0] = Pol::to_store(acc[dd][k]);
 }
 
 // ---------------------------------------------------------------------------
 // stage X: contract direction 0 and write the stencil rows
 // ---------------------------------------------------------------------------
-template <int P, int DIM>
+template <class Pol, int P, int DIM>
 __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, double* scratch,
                                                     void* ell, int ell_f32, int64_t N, double* samples)
 {
+    using S = typename Pol::store;
+    using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
+    // Rows whose stencil stays among cardinal B-splines (2p <= i1 <= m0-2p-1)
+    // all have the same pair weights (translation invariance, Sec. 2.2): they
+    // read one copy from shared memory, so a warp's loads are broadcasts.
+    // Loaded before any thread of the block can leave.
+    __shared__ S sX[4 * W * TT];
+    const bool has_card = g.m[0] >= 4 * P + 1;
+    const S* X0 = reinterpret_cast<const S*>(T.Xs[0]);
+    if (has_card)
+        for (int k = threadIdx.x; k < 4 * W * TT; k += blockDim.x) sX[k] = X0[(int64_t)(2 * P) * 4 * W * TT + k];
+    __syncthreads();
     Box b;
     get_box(bs, DIM, P, 3, blockIdx.x, b);
     const int64_t G0 = (int64_t)b.E[0] * Q;
@@ -202,31 +210,32 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
     const int i3 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
     const int d3 = (DIM == 3) ? (int)(pair3 % W) : 0;
     const int m0 = g.m[0];
-    const double* X = T.X[0];
-    const int64_t ps = (int64_t)m0 * W * TT;
-    const double* Xi = X + (int64_t)i1 * W * TT;
-    const double* T2 = scratch + b.t2_off + (pair3 * P2 + pair2) * G0;
+    constexpr int ps = W * TT;
+    const bool card = has_card && i1 >= 2 * P && i1 <= m0 - 2 * P - 1;
+    const S* Xi = card ? sX : X0 + (int64_t)i1 * 4 * W * TT;
+    const S* T2 = reinterpret_cast<const S*>(scratch + b.t2_off) + (pair3 * P2 + pair2) * G0;
     const int64_t gs = P3 * P2 * G0;        // group stride
 
-    double acc[W];
+    A acc[W];
 #pragma unroll
-    for (int dd = 0; dd < W; ++dd) acc[dd] = 0.0;
+    for (int dd = 0; dd < W; ++dd) acc[dd] = Pol::zero();
 #pragma unroll
-    for (int t = 0; t < TT; ++t) {
-        const int e1 = i1 - P + t / Q;
+    for (int a = 0; a <= P; ++a) {
+        const int e1 = i1 - P + a;
         if (e1 < b.elo[0] || e1 >= b.elo[0] + b.E[0]) continue;
-        const int64_t o = (e1 - b.elo[0]) * Q + t % Q;
-        const double v0 = T2[o], v1 = T2[gs + o], v2 = T2[2 * gs + o], v3 = T2[3 * gs + o];
+#pragma unroll 1
+        for (int r = 0; r < Q; ++r) {
+        const int t = a * Q + r;
+        const int64_t o = (e1 - b.elo[0]) * Q + r;
+        const S v0 = T2[o], v1 = T2[gs + o], v2 = T2[2 * gs + o], v3 = T2[3 * gs + o];
 #pragma unroll
-        for (int dd = 0; dd < W; ++dd) {
-            if (!in_overlap<P>(t, dd)) continue;
-            const int64_t xo = (int64_t)dd * TT + t;
-            double a = acc[dd];
-            a = fma(__ldg(Xi + 3 * ps + xo), v0, a);   // group 0: pattern 11
-            a = fma(__ldg(Xi + 2 * ps + xo), v1, a);   // group 1: pattern 10
-            a = fma(__ldg(Xi + ps + xo), v2, a);       // group 2: pattern 01
-            a = fma(__ldg(Xi + xo), v3, a);            // group 3: pattern 00
-            acc[dd] = a;
+        for (int dd = a; dd <= a + P; ++dd) {
+            const int xo = dd * TT + t;
+            Pol::mac(acc[dd], Xi[3 * ps + xo], v0);   // group 0: pattern 11
+            Pol::mac(acc[dd], Xi[2 * ps + xo], v1);   // group 1: pattern 10
+            Pol::mac(acc[dd], Xi[ps + xo], v2);       // group 2: pattern 01
+            Pol::mac(acc[dd], Xi[xo], v3);            // group 3: pattern 00
+        }
         }
     }
     const int slot0 = W * (d2 + W * d3);
@@ -235,20 +244,21 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
         if (ell_f32) {
             float* out = (float*)ell;
 #pragma unroll
-            for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = (float)acc[dd];
+            for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = (float)Pol::to_double(acc[dd]);
         } else {
             double* out = (double*)ell;
 #pragma unroll
-            for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = acc[dd];
+            for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = Pol::to_double(acc[dd]);
         }
     } else {
 #pragma unroll
-        for (int dd = 0; dd < W; ++dd) samples[(int64_t)(slot0 + dd) * bs.n_samples + b.sample_id] = acc[dd];
+        for (int dd = 0; dd < W; ++dd)
+            samples[(int64_t)(slot0 + dd) * bs.n_samples + b.sample_id] = Pol::to_double(acc[dd]);
     }
 }
 
 // ---------------------------------------------------------------------------
-template <int P>
+template <class Pol, int P>
 static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nb[4],
                             double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s)
 {
@@ -256,43 +266,55 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
     if (g.dim == 3) {
         if (nb[1] > 0) {
             launch_begin(K_STAGE_Z, s);
-            k_stage_z<P><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            k_stage_z<Pol, P><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Z, s);
         }
         if (nb[2] > 0) {
             launch_begin(K_STAGE_Y, s);
-            k_stage_y<P, 3><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
+            k_stage_y<Pol, P, 3><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Y, s);
         }
         if (nb[3] > 0) {
             launch_begin(K_STAGE_X, s);
-            k_stage_x<P, 3><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
+            k_stage_x<Pol, P, 3><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
             launch_end(K_STAGE_X, s);
         }
     } else {
         if (nb[2] > 0) {
             launch_begin(K_STAGE_Y, s);
-            k_stage_y<P, 2><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
+            k_stage_y<Pol, P, 2><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Y, s);
         }
         if (nb[3] > 0) {
             launch_begin(K_STAGE_X, s);
-            k_stage_x<P, 2><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
+            k_stage_x<Pol, P, 2><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
             launch_end(K_STAGE_X, s);
         }
     }
     return cudaGetLastError();
 }
 
+template <class Pol>
+static cudaError_t stages_pol(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nb[4],
+                              double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s)
+{
+    switch (g.p) {
+    case 1: return stages_p<Pol, 1>(g, T, bs, nb, scratch, ell, ell_f32, samples, s);
+    case 2: return stages_p<Pol, 2>(g, T, bs, nb, scratch, ell, ell_f32, samples, s);
+    case 3: return stages_p<Pol, 3>(g, T, bs, nb, scratch, ell, ell_f32, samples, s);
+    case 4: return stages_p<Pol, 4>(g, T, bs, nb, scratch, ell, ell_f32, samples, s);
+    case 5: return stages_p<Pol, 5>(g, T, bs, nb, scratch, ell, ell_f32, samples, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
                           double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s)
 {
-    switch (g.p) {
-    case 1: return stages_p<1>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
-    case 2: return stages_p<2>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
-    case 3: return stages_p<3>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
-    case 4: return stages_p<4>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
-    case 5: return stages_p<5>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
+    switch (T.arith) {
+    case kArithF64: return stages_pol<PolF64>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
+    case kArithDF: return stages_pol<PolDF>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
+    case kArithF32: return stages_pol<PolF32>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
     default: return cudaErrorInvalidValue;
     }
 }

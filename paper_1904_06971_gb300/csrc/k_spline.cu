@@ -11,6 +11,7 @@
 // interpolating spline.  Spans are half-open [kn_mu, kn_mu+1) except the last.
 // The collocation matrix is totally positive and banded, so it is factored
 // without pivoting and the factors keep its band.
+#include "arith.cuh"
 #include "iga_internal.cuh"
 
 namespace iga {
@@ -106,7 +107,10 @@ __global__ void k_spline_setup(SplinePlan sp, int M, SplineBufs sb)
         double N[kMaxQ + 1];
         spline_basis(kn, mu, q, x, N);
         sb.espan[d][k] = mu - q;
-        for (int a = 0; a <= q; ++a) sb.eval[d][(int64_t)k * (q + 1) + a] = N[a];
+        for (int a = 0; a <= q; ++a) {
+            sb.eval[d][(int64_t)k * (q + 1) + a] = N[a];
+            if (d == 0) sb.eval0[(int64_t)a * L + k] = PolDF::from_double(N[a]);
+        }
     }
 }
 
@@ -172,7 +176,7 @@ __global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* sam
     } else {
         for (int b = 0; b <= q1; ++b) acc += coef[a0 + (int64_t)n0 * (s1 + b)] * E1[b];
     }
-    sb.partial[idx] = acc;
+    sb.partial[idx] = PolDF::from_double(acc);
 }
 
 cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* samples,
@@ -207,8 +211,15 @@ cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* sam
 //      j in Omega~, j > i : Phi~_delta(x~_i)                      (interpolated)
 //      j in Omega~, j < i : Phi~_{-delta}(x~_j)  (= A~_ji, the copied entry)
 //      j outside Omega~   : A_ji from the exact frame row j (= A_ij)
-//    then the diagonal := -(off-diagonal sum), accumulated in FP64.
+//    then the diagonal := -(off-diagonal sum).
+// The interpolant is evaluated in double-float arithmetic on the FP32 pipe
+// (about 48 significand bits); the diagonal sums are FP64.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T from_df(const DFAcc& a) { return PolDF::to_double(a); }
+template <>
+__device__ __forceinline__ float from_df<float>(const DFAcc& a) { return __fadd_rn(a.h, a.l); }
+
 template <int P, int DIM, typename T>
 __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, int empty_box, SplineBufs sb, T* vals)
 {
@@ -220,12 +231,16 @@ __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, int empty
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
-    const int k0 = sp.k0[0];
+    const int kk0 = sp.k0[0], kk1 = sp.k0[1], kk2 = (DIM == 3) ? sp.k0[2] : 0;
+    const int L0 = sp.L[0], L1 = sp.L[1], L2 = (DIM == 3) ? sp.L[2] : 1;
     bool inbox = !empty_box;
     if (inbox) {
-        inbox = (i0 >= k0 && i0 < k0 + sp.L[0]) && (i1 >= sp.k0[1] && i1 < sp.k0[1] + sp.L[1]);
-        if (DIM == 3) inbox = inbox && (i2 >= sp.k0[2] && i2 < sp.k0[2] + sp.L[2]);
+        inbox = (i0 >= kk0 && i0 < kk0 + L0) && (i1 >= kk1 && i1 < kk1 + L1);
+        if (DIM == 3) inbox = inbox && (i2 >= kk2 && i2 < kk2 + L2);
     }
+    // The diagonal is minus a sum of up to (2p+1)^n - 1 stored values: it is
+    // accumulated in FP64, whose rounding stays ~1e-15 of the row's mass even
+    // for 1330 terms (a double-float sum would lose ~1e-12).
     double sum = 0.0;
     if (!inbox) {
 #pragma unroll 8
@@ -235,33 +250,38 @@ __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, int empty
         return;
     }
     const int n0 = sp.ns[0], q0 = sp.qe[0];
-    const int L0 = sp.L[0], L1 = sp.L[1], L2 = (DIM == 3) ? sp.L[2] : 1;
-    const int kk0 = sp.k0[0], kk1 = sp.k0[1], kk2 = (DIM == 3) ? sp.k0[2] : 0;
-    for (int s = 0; s < S; ++s) {
-        if (s == C) continue;
-        const int d0 = s % W - P, d1 = (s / W) % W - P, d2 = (DIM == 3) ? s / (W * W) - P : 0;
-        const int j0 = i0 + d0, j1 = i1 + d1, j2 = i2 + d2;
-        const int l0 = j0 - kk0, l1 = j1 - kk1, l2 = j2 - kk2;
-        const bool jin = (l0 >= 0 && l0 < L0) && (l1 >= 0 && l1 < L1) && (l2 >= 0 && l2 < L2);
-        double v;
-        if (jin) {
-            // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
-            const bool upper = s > C;
-            const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
-            const int e0 = upper ? i0 - kk0 : l0;
-            const int e1 = upper ? i1 - kk1 : l1;
-            const int e2 = upper ? i2 - kk2 : l2;
-            const double* Pp = sb.partial + (((int64_t)u * L2 + e2) * L1 + e1) * n0 + sb.espan[0][e0];
-            const double* E = sb.eval[0] + (int64_t)e0 * (q0 + 1);
-            double a = 0.0;
-            for (int k = 0; k <= q0; ++k) a = fma(E[k], Pp[k], a);
-            v = a;
-        } else {
-            const int64_t jrow = j0 + (int64_t)m0 * (j1 + (int64_t)m1 * j2);
-            v = (double)vals[(int64_t)(S - 1 - s) * N + jrow];
+    const int e0i = i0 - kk0, e1i = i1 - kk1, e2i = i2 - kk2;
+    constexpr int n2 = (DIM == 3) ? W : 1;
+    for (int d2 = 0; d2 < n2; ++d2) {
+        for (int d1 = 0; d1 < W; ++d1) {
+            const int dl1 = d1 - P, dl2 = (DIM == 3) ? d2 - P : 0;
+            const int l1 = e1i + dl1, l2 = e2i + dl2;
+            const bool in12 = (l1 >= 0 && l1 < L1) && (l2 >= 0 && l2 < L2);
+            const int sbase = W * (d1 + W * d2);
+#pragma unroll
+            for (int d0 = 0; d0 < W; ++d0) {
+                const int s = sbase + d0;
+                if (s == C) continue;
+                const int l0 = e0i + d0 - P;
+                T out;
+                if (in12 && l0 >= 0 && l0 < L0) {
+                    // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
+                    const bool upper = s > C;
+                    const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
+                    const int e0 = upper ? e0i : l0, e1 = upper ? e1i : l1, e2 = upper ? e2i : l2;
+                    const float2* Pp = sb.partial + (((int64_t)u * L2 + e2) * L1 + e1) * n0 + sb.espan[0][e0];
+                    const float2* E = sb.eval0 + e0;
+                    DFAcc v = PolDF::zero();
+                    for (int k = 0; k <= q0; ++k) PolDF::mac(v, E[(int64_t)k * L0], Pp[k]);
+                    out = from_df<T>(v);
+                } else {
+                    const int64_t jrow = (i0 + d0 - P) + (int64_t)m0 * ((i1 + dl1) + (int64_t)m1 * (i2 + dl2));
+                    out = vals[(int64_t)(S - 1 - s) * N + jrow];
+                }
+                vals[(int64_t)s * N + i] = out;
+                sum += (double)out;
+            }
         }
-        vals[(int64_t)s * N + i] = (T)v;
-        sum += v;
     }
     vals[(int64_t)C * N + i] = (T)(-sum);
 }

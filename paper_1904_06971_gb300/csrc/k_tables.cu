@@ -4,6 +4,8 @@
 //     (eq. BilinearFormPoissonTensor) at the Gauss points of each box.
 #include <math_constants.h>
 
+#include "arith.cuh"
+#include "dfmath.cuh"
 #include "iga_internal.cuh"
 
 namespace iga {
@@ -82,6 +84,7 @@ __device__ void basis_on_element(int p, int n_el, int e, double xi, double* N, d
 }
 
 struct BasisArgs {
+    float2* tdf[3];
     double* gx[3];
     double* sx[3];
     double* cx[3];
@@ -114,6 +117,13 @@ __global__ void __launch_bounds__(kBlock) k_basis(Geo g, BasisArgs A)
     sincospi(xi, &s, &c);
     A.sx[d][gi] = s;
     A.cx[d][gi] = c;
+    A.tdf[d][4 * gi + 0] = PolDF::from_double(s);
+    A.tdf[d][4 * gi + 1] = PolDF::from_double(CUDART_PI * c);
+    sincospi(2.0 * xi, &s, &c);
+    A.sx[d][G + gi] = s;          // sin(2 pi xi), cos(2 pi xi) after the first G entries
+    A.cx[d][G + gi] = c;
+    A.tdf[d][4 * gi + 2] = PolDF::from_double(s);
+    A.tdf[d][4 * gi + 3] = PolDF::from_double(c);
     A.wq[d][gi] = sgw[r] * h;
     double N[kMaxP + 1], D[kMaxP + 1];
     basis_on_element(p, n_el, e, xi, N, D);
@@ -124,11 +134,12 @@ __global__ void __launch_bounds__(kBlock) k_basis(Geo g, BasisArgs A)
 }
 
 cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[3],
-                         double* bv[3], double* bd[3], double* wq[3], cudaStream_t s)
+                         double* bv[3], double* bd[3], double* wq[3], float2* tdf[3], cudaStream_t s)
 {
     BasisArgs A;
     int Gmax = 0;
     for (int d = 0; d < 3; ++d) {
+        A.tdf[d] = tdf[d];
         A.gx[d] = gx[d]; A.sx[d] = sx[d]; A.cx[d] = cx[d];
         A.bv[d] = bv[d]; A.bd[d] = bd[d]; A.wq[d] = wq[d];
         if (d < g.dim && g.n_el[d] * (g.p + 1) > Gmax) Gmax = g.n_el[d] * (g.p + 1);
@@ -144,7 +155,7 @@ cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[
 // Pair weights.  For direction d, row function i, offset delta (column
 // j = i + delta) and local point t = a (p+1) + r of supp(B_i) (element
 // e = i - p + a, Gauss point r), pattern pat = 2 alpha + beta:
-//   X[pat][i][delta + p][t] = w_r h  b_i^(alpha)(x_g)  b_j^(beta)(x_g),
+//   X[i][pat][delta + p][t] = w_r h  b_i^(alpha)(x_g)  b_j^(beta)(x_g),
 // zero when e is outside the mesh, j outside [0, m) or b_j vanishes on e.
 // The product over directions of these factors, summed over the Gauss
 // points, is the quadrature of d^alpha B_i d^beta B_j (Sec. 3.2, eq. ChangeOfVars).
@@ -154,8 +165,10 @@ struct PairArgs {
     const double* bd[3];
     const double* wq[3];
     double* X[3];
+    void* Xs[3];
 };
 
+template <class Pol>
 __global__ void __launch_bounds__(kBlock) k_pairs(Geo g, PairArgs A)
 {
     const int d = blockIdx.y;
@@ -168,8 +181,8 @@ __global__ void __launch_bounds__(kBlock) k_pairs(Geo g, PairArgs A)
     int64_t rest = idx / TT;
     const int dd = (int)(rest % W);
     rest /= W;
-    const int i = (int)(rest % m);
-    const int pat = (int)(rest / m);
+    const int pat = (int)(rest % 4);
+    const int i = (int)(rest / 4);
     const int alpha = pat >> 1, beta = pat & 1;
     const int e = i - p + t / Q, r = t % Q;
     const int j = i + dd - p;
@@ -181,16 +194,17 @@ __global__ void __launch_bounds__(kBlock) k_pairs(Geo g, PairArgs A)
         v = A.wq[d][gi] * bi * bj;
     }
     A.X[d][idx] = v;
+    if (Pol::kind != kArithF64) reinterpret_cast<typename Pol::store*>(A.Xs[d])[idx] = Pol::from_double(v);
 }
 
 cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
-                         double* const wq[3], double* X[3], cudaStream_t s)
+                         double* const wq[3], double* X[3], void* Xs[3], int arith, cudaStream_t s)
 {
     PairArgs A;
     int64_t maxn = 0;
     const int p = g.p;
     for (int d = 0; d < 3; ++d) {
-        A.bv[d] = bv[d]; A.bd[d] = bd[d]; A.wq[d] = wq[d]; A.X[d] = X[d];
+        A.bv[d] = bv[d]; A.bd[d] = bd[d]; A.wq[d] = wq[d]; A.X[d] = X[d]; A.Xs[d] = Xs[d];
         if (d < g.dim) {
             int64_t n = (int64_t)4 * g.m[d] * (2 * p + 1) * (p + 1) * (p + 1);
             if (n > maxn) maxn = n;
@@ -198,7 +212,9 @@ cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
     }
     dim3 grid((unsigned)((maxn + kBlock - 1) / kBlock), g.dim);
     launch_begin(K_PAIRS, s);
-    k_pairs<<<grid, kBlock, 0, s>>>(g, A);
+    if (arith == kArithDF) k_pairs<PolDF><<<grid, kBlock, 0, s>>>(g, A);
+    else if (arith == kArithF32) k_pairs<PolF32><<<grid, kBlock, 0, s>>>(g, A);
+    else k_pairs<PolF64><<<grid, kBlock, 0, s>>>(g, A);
     launch_end(K_PAIRS, s);
     return cudaGetLastError();
 }
@@ -237,7 +253,7 @@ __device__ double kappa_at(const Geo& g, const double* x)
     }
 }
 
-template <int DIM>
+template <int DIM, class Pol>
 __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, double* scratch)
 {
     Box b;
@@ -257,15 +273,113 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
         gg[d] = b.elo[d] * Q + gl[d];
         xi[d] = T.gx[d][gg[d]];
     }
+    typename Pol::store* out = reinterpret_cast<typename Pol::store*>(scratch + b.c_off);
+    if (Pol::kind != kArithF64 && g.coef_df) {
+        // Same formulas as the FP64 branch below, in double-float arithmetic on
+        // the FP32 pipe (dfmath.cuh): the result is stored in double-float (or
+        // float) anyway, and GB300's FP64 pipe is 64x slower than its FP32 pipe.
+        df2 sv[3], pcv[3], S2[3], C2[3];
+        for (int d = 0; d < DIM; ++d) {
+            const float2* t4 = T.tdf[d] + 4 * gg[d];
+            sv[d] = df2{t4[0].x, t4[0].y};
+            pcv[d] = df2{t4[1].x, t4[1].y};
+            S2[d] = df2{t4[2].x, t4[2].y};
+            C2[d] = df2{t4[3].x, t4[3].y};
+        }
+        df2 gr[3], P;
+        if (DIM == 3) {
+            const df2 q12 = df_mul(sv[1], sv[2]), q02 = df_mul(sv[0], sv[2]), q01 = df_mul(sv[0], sv[1]);
+            gr[0] = df_mul(pcv[0], q12);
+            gr[1] = df_mul(pcv[1], q02);
+            gr[2] = df_mul(pcv[2], q01);
+            P = df_mul(sv[0], q12);
+        } else {
+            gr[0] = df_mul(pcv[0], sv[1]);
+            gr[1] = df_mul(pcv[1], sv[0]);
+            gr[2] = df2{0.f, 0.f};
+            P = df_mul(sv[0], sv[1]);
+        }
+        df2 gsum = gr[0], gg2 = df_mul(gr[0], gr[0]);
+        for (int d = 1; d < DIM; ++d) {
+            gsum = df_add(gsum, gr[d]);
+            gg2 = df_fma(gr[d], gr[d], gg2);
+        }
+        const df2 amp = df2{g.amp_df[0], g.amp_df[1]};
+        const df2 det = df_fma(amp, gsum, df2{1.f, 0.f});
+        const df2 cc = df_div(amp, det);
+        const df2 c2g = df_mul(df_mul(cc, cc), gg2);
+        df2 kap = df2{g.ka_df[0], g.ka_df[1]};
+        if (g.kappa_kind == IGA_KAPPA_SIN2D || g.kappa_kind == IGA_KAPPA_EXPSIN3D) {
+            const df2 th = df_add(amp, amp);
+            df2 st, ct;
+            df_sincospi_small(df_mul(th, P), st, ct);
+            const df2 kb = df2{g.kb_df[0], g.kb_df[1]};
+            const df2 sin0 = df_fma(S2[0], ct, df_mul(C2[0], st));
+            if (g.kappa_kind == IGA_KAPPA_SIN2D) {
+                const df2 sin1 = df_fma(S2[1], ct, df_mul(C2[1], st));
+                kap = df_fma(kb, df_mul(sin0, sin1), kap);
+            } else {
+                const df2 cos1 = df_sub(df_mul(C2[1], ct), df_mul(S2[1], st));
+                const df2 sin2 = df_fma(S2[2], ct, df_mul(C2[2], st));
+                kap = df_exp_small(df_mul(kb, df_mul(sin0, df_mul(cos1, sin2))));
+            }
+        }
+        const df2 f = df_mul(kap, df_abs(det));
+        int k = 0;
+        for (int a = 0; a < DIM; ++a)
+            for (int bdir = a; bdir < DIM; ++bdir, ++k) {
+                df2 m = df_add(df_neg(df_mul(cc, df_add(gr[a], gr[bdir]))), c2g);
+                if (a == bdir) m = df_add(m, df2{1.f, 0.f});
+                const df2 v = df_mul(f, m);
+                if (Pol::kind == kArithDF) reinterpret_cast<float2*>(out)[k * npts + item] = make_float2(v.h, v.l);
+                else reinterpret_cast<float*>(out)[k * npts + item] = __fadd_rn(v.h, v.l);
+            }
+        return;
+    }
     if (g.map_kind == IGA_MAP_SINPROD) {
+        // x = xi + amp P 1 with P = prod_j sin(pi xi_j): Dphi = I + amp 1 gr^T,
+        // gr_b = dP / dxi_b.  A rank-one update of I, so (Sherman-Morrison)
+        //   det = 1 + amp sum_b gr_b,  Dphi^{-1} = I - c 1 gr^T,  c = amp / det,
+        //   Dphi^{-1} Dphi^{-T} = I - c (1 gr^T + gr 1^T) + c^2 |gr|^2 1 1^T.
         double s[3], c[3], P = 1.0;
         for (int d = 0; d < DIM; ++d) { s[d] = T.sx[d][gg[d]]; c[d] = T.cx[d][gg[d]]; P *= s[d]; }
+        double gr[3], gsum = 0.0, gg2 = 0.0;
         for (int bdir = 0; bdir < DIM; ++bdir) {
             double dP = CUDART_PI * c[bdir];
             for (int j = 0; j < DIM; ++j) if (j != bdir) dP *= s[j];
-            for (int a = 0; a < DIM; ++a) J[a][bdir] = (a == bdir ? 1.0 : 0.0) + g.amp * dP;
+            gr[bdir] = dP;
+            gsum += dP;
+            gg2 += dP * dP;
         }
-        for (int a = 0; a < DIM; ++a) x[a] = xi[a] + g.amp * P;
+        const double det = 1.0 + g.amp * gsum;
+        const double cc = g.amp / det;
+        // kappa at x_a = xi_a + amp P: sin / cos of 2 pi x_a by angle addition from the
+        // tabulated sin / cos of 2 pi xi_a and one sincos of 2 pi amp P
+        double kap;
+        if (g.kappa_kind == IGA_KAPPA_SIN2D || g.kappa_kind == IGA_KAPPA_EXPSIN3D) {
+            double st, ct;
+            sincospi(2.0 * g.amp * P, &st, &ct);
+            const int64_t G0 = (int64_t)g.n_el[0] * Q, G1 = (int64_t)g.n_el[1] * Q;
+            const double S0 = T.sx[0][G0 + gg[0]], C0 = T.cx[0][G0 + gg[0]];
+            const double S1 = T.sx[1][G1 + gg[1]], C1 = T.cx[1][G1 + gg[1]];
+            const double sin0 = S0 * ct + C0 * st;
+            if (g.kappa_kind == IGA_KAPPA_SIN2D) {
+                kap = g.ka + g.kb * sin0 * (S1 * ct + C1 * st);
+            } else {
+                const int64_t G2 = (int64_t)g.n_el[2] * Q;
+                const double S2 = T.sx[2][G2 + gg[2]], C2 = T.cx[2][G2 + gg[2]];
+                kap = exp(g.kb * sin0 * (C1 * ct - S1 * st) * (S2 * ct + C2 * st));
+            }
+        } else {
+            for (int a = 0; a < DIM; ++a) x[a] = xi[a] + g.amp * P;
+            kap = kappa_at(g, x);
+        }
+        const double f = kap * fabs(det), c2g = cc * cc * gg2;
+        int k = 0;
+        for (int a = 0; a < DIM; ++a)
+            for (int bdir = a; bdir < DIM; ++bdir, ++k)
+                out[k * npts + item] = Pol::from_double(f * ((a == bdir ? 1.0 : 0.0) - cc * (gr[a] + gr[bdir]) + c2g));
+        return;
     } else if (g.map_kind == IGA_MAP_AFFINE) {
         for (int a = 0; a < DIM; ++a) {
             x[a] = g.aff[9 + a];
@@ -279,14 +393,13 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
     }
     const double kap = kappa_at(g, x);
     // K = kappa |det J| J^{-1} J^{-T} = kappa / |det J| adj(J) adj(J)^T
-    double* out = scratch + b.c_off;
     if (DIM == 2) {
         const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         const double a00 = J[1][1], a01 = -J[0][1], a10 = -J[1][0], a11 = J[0][0];
         const double f = kap / fabs(det);
-        out[0 * npts + item] = f * (a00 * a00 + a01 * a01);
-        out[1 * npts + item] = f * (a00 * a10 + a01 * a11);
-        out[2 * npts + item] = f * (a10 * a10 + a11 * a11);
+        out[0 * npts + item] = Pol::from_double(f * (a00 * a00 + a01 * a01));
+        out[1 * npts + item] = Pol::from_double(f * (a00 * a10 + a01 * a11));
+        out[2 * npts + item] = Pol::from_double(f * (a10 * a10 + a11 * a11));
     } else {
         double adj[3][3];
         adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
@@ -301,13 +414,27 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
         const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
         const double f = kap / fabs(det);
         auto row = [&](int a, int c) { return adj[a][0] * adj[c][0] + adj[a][1] * adj[c][1] + adj[a][2] * adj[c][2]; };
-        out[0 * npts + item] = f * row(0, 0);
-        out[1 * npts + item] = f * row(0, 1);
-        out[2 * npts + item] = f * row(0, 2);
-        out[3 * npts + item] = f * row(1, 1);
-        out[4 * npts + item] = f * row(1, 2);
-        out[5 * npts + item] = f * row(2, 2);
+        out[0 * npts + item] = Pol::from_double(f * row(0, 0));
+        out[1 * npts + item] = Pol::from_double(f * row(0, 1));
+        out[2 * npts + item] = Pol::from_double(f * row(0, 2));
+        out[3 * npts + item] = Pol::from_double(f * row(1, 1));
+        out[4 * npts + item] = Pol::from_double(f * row(1, 2));
+        out[5 * npts + item] = Pol::from_double(f * row(2, 2));
     }
+}
+
+void prepare_coef_df(Geo& g, int arith)
+{
+    auto split = [](double v, float* out) {
+        out[0] = (float)v;
+        out[1] = (float)(v - (double)out[0]);
+    };
+    split(g.amp, g.amp_df);
+    split(g.ka, g.ka_df);
+    split(g.kb, g.kb_df);
+    const bool kappa_ok = g.kappa_kind == IGA_KAPPA_CONST || g.kappa_kind == IGA_KAPPA_SIN2D ||
+                          (g.kappa_kind == IGA_KAPPA_EXPSIN3D && fabs(g.kb) <= 1.0);
+    g.coef_df = (arith != kArithF64 && g.map_kind == IGA_MAP_SINPROD && fabs(g.amp) <= 0.07 && kappa_ok) ? 1 : 0;
 }
 
 cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t nblocks,
@@ -315,8 +442,16 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
 {
     if (nblocks <= 0) return cudaSuccess;
     launch_begin(K_COEF, s);
-    if (g.dim == 3) k_coef<3><<<(unsigned)nblocks, kBlock, 0, s>>>(g, T, bs, scratch);
-    else k_coef<2><<<(unsigned)nblocks, kBlock, 0, s>>>(g, T, bs, scratch);
+    const unsigned grid = (unsigned)nblocks;
+    if (g.dim == 3) {
+        if (T.arith == kArithDF) k_coef<3, PolDF><<<grid, kBlock, 0, s>>>(g, T, bs, scratch);
+        else if (T.arith == kArithF32) k_coef<3, PolF32><<<grid, kBlock, 0, s>>>(g, T, bs, scratch);
+        else k_coef<3, PolF64><<<grid, kBlock, 0, s>>>(g, T, bs, scratch);
+    } else {
+        if (T.arith == kArithDF) k_coef<2, PolDF><<<grid, kBlock, 0, s>>>(g, T, bs, scratch);
+        else if (T.arith == kArithF32) k_coef<2, PolF32><<<grid, kBlock, 0, s>>>(g, T, bs, scratch);
+        else k_coef<2, PolF64><<<grid, kBlock, 0, s>>>(g, T, bs, scratch);
+    }
     launch_end(K_COEF, s);
     return cudaGetLastError();
 }

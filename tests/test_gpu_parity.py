@@ -31,6 +31,19 @@ def rel(X, ref):
     return oracle.relative_entry_error(X, ref)
 
 
+@pytest.fixture
+def arith(iga, request):
+    """Run a test under a given contraction arithmetic, restoring the defaults after."""
+    saved = {dt: iga.get_arithmetic(dt) for dt in ("f64", "f32")}
+    yield request.param
+    for dt, a in saved.items():
+        iga.set_arithmetic(dt, a)
+
+
+def use(iga, dtype, arith):
+    iga.set_arithmetic(dtype, arith)
+
+
 def gpu_exact(iga, prob, dtype="f64"):
     A = iga.assemble_exact(prob, dtype=dtype)
     v = A.values_host()
@@ -59,14 +72,19 @@ SMALL_EXACT = [
 ]
 
 
+@pytest.mark.parametrize("arith", ["df64", "fp64"], indirect=True)
 @pytest.mark.parametrize("prob", SMALL_EXACT, ids=lambda q: f"{q.dim}d_p{q.p}_{'x'.join(map(str, q.n_el))}")
-def test_exact_full_matrix(iga, prob):
+def test_exact_full_matrix(iga, prob, arith):
+    use(iga, "f64", arith)
     ref = oracle.exact_matrix(prob)
     assert rel(gpu_exact(iga, prob), ref) <= TOL64
 
 
-def test_exact_f32(iga):
-    prob = SMALL_EXACT[6]
+@pytest.mark.parametrize("arith", ["fp32", "df64", "fp64"], indirect=True)
+@pytest.mark.parametrize("idx", [3, 6, 7])
+def test_exact_f32(iga, idx, arith):
+    use(iga, "f32", arith)
+    prob = SMALL_EXACT[idx]
     ref = oracle.exact_matrix(prob)
     v = gpu_exact(iga, prob, "f32")
     assert v.dtype == np.float32
@@ -98,16 +116,21 @@ SMALL_SURR = [
 ]
 
 
+@pytest.mark.parametrize("arith", ["df64", "fp64"], indirect=True)
 @pytest.mark.parametrize("prob,M,q", SMALL_SURR,
                          ids=lambda x: f"{x.dim}d_p{x.p}_{'x'.join(map(str, x.n_el))}" if hasattr(x, "dim") else str(x))
-def test_surrogate_full_matrix(iga, prob, M, q):
+def test_surrogate_full_matrix(iga, prob, M, q, arith):
+    use(iga, "f64", arith)
     ref = oracle.surrogate_matrix(prob, M, q)
     got = gpu_surr(iga, prob, M, q)
     assert rel(got, ref) <= TOL64
 
 
-def test_surrogate_f32(iga):
-    prob, M, q = SMALL_SURR[9]
+@pytest.mark.parametrize("arith", ["fp32", "df64"], indirect=True)
+@pytest.mark.parametrize("idx", [7, 9, 12])
+def test_surrogate_f32(iga, idx, arith):
+    use(iga, "f32", arith)
+    prob, M, q = SMALL_SURR[idx]
     ref = oracle.surrogate_matrix(prob, M, q)
     assert rel(gpu_surr(iga, prob, M, q, "f32"), ref) <= TOL32
 
@@ -198,7 +221,8 @@ def test_full_size_surrogate_sampled_rows(iga, wl):
         j = torch.from_numpy(oracle.surrogate.flat_index(mj[ok], m)).cuda()
         d = (vals[s, i] - vals[prob.S - 1 - s, j]).abs().max().item()
         worst = max(worst, d)
-    assert worst <= (1e-14 if wl.dtype == "f64" else 1e-6) * scale
+    # frame rows are exact quadrature rows, symmetric only up to the rounding of the contractions
+    assert worst <= tol * scale
     A.destroy()
 
 
@@ -212,3 +236,27 @@ def test_full_size_exact_sampled_rows(iga):
     ref = oracle.exact_rows(prob, rows)
     assert np.abs(got - ref).max() <= TOL64 * np.abs(ref).max()
     A.destroy()
+
+
+def test_dfmath_against_cuda_fp64(iga):
+    """Double-float Taylor-series sin / cos / exp of the coefficient kernel vs CUDA's FP64 functions."""
+    import ctypes
+    L = iga.load()
+    err = (ctypes.c_double * 3)()
+    L.iga_selftest_dfmath.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    assert L.iga_selftest_dfmath(100001, err) == 0
+    assert err[0] < 1e-14 and err[1] < 1e-14, list(err)
+    assert err[2] < 5e-14, list(err)
+
+
+@pytest.mark.parametrize("arith", ["df64"], indirect=True)
+def test_double_float_coefficients_match_fp64_path(iga, arith):
+    """The double-float coefficient path agrees with the FP64 one on the benchmark map family."""
+    prob = W.Problem(dim=3, p=3, n_el=(12, 13, 11), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+                     kappa_b=0.5)
+    iga.set_arithmetic("f64", "fp64")
+    ref = gpu_exact(iga, prob)
+    iga.set_arithmetic("f64", "df64")
+    got = gpu_exact(iga, prob)
+    assert rel(got, ref) <= 1e-12
+    assert rel(got, oracle.exact_matrix(prob)) <= TOL64
