@@ -35,6 +35,21 @@ struct DFAcc {
     float h, l;
 };
 
+// Exact float -> double conversion by integer operations (sign, rebiased
+// exponent, widened significand), so it stays off GB300's slow FP64 pipe where
+// the F2F conversion instruction runs.  Zero, subnormal, infinite and NaN
+// inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 struct PolDF {
     using store = float2;
     using acc = DFAcc;
@@ -54,7 +69,7 @@ struct PolDF {
         a.h = s;
         a.l = __fadd_rn(a.l, __fadd_rn(t, pe));
     }
-    __device__ __forceinline__ static double to_double(const acc& a) { return (double)a.h + (double)a.l; }
+    __device__ __forceinline__ static double to_double(const acc& a) { return f2d_exact(a.h) + f2d_exact(a.l); }
     __device__ __forceinline__ static store to_store(const acc& a)
     {
         const float s = __fadd_rn(a.h, a.l);

@@ -57,7 +57,7 @@ std::vector<cudaEvent_t> g_events;
 thread_local cudaEvent_t t_begin = nullptr;
 
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
-                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv"};
+                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag"};
 
 cudaEvent_t take_event()
 {

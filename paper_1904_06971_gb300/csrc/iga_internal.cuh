@@ -11,6 +11,7 @@ namespace iga {
 constexpr int kMaxP = 5;          // degrees 1..5 are instantiated
 constexpr int kMaxQ = 7;          // interpolation degree 0..7
 constexpr int kBlock = 256;       // threads per block of the item-parallel kernels
+constexpr int kLinesX = 2;        // output lines per thread in quadrature stage X
 
 // Geometry map + diffusion coefficient + mesh; passed by value to kernels.
 struct Geo {
@@ -92,7 +93,7 @@ struct Tables {
     const double* gx[3];      // [G]  Gauss point coordinates xi
     const double* sx[3];      // [2G] sin(pi xi), then sin(2 pi xi)
     const double* cx[3];      // [2G] cos(pi xi), then cos(2 pi xi)
-    const double* X[3];       // [m][4][2p+1][(p+1)^2] pair weights (FP64), see k_tables.cu
+    const double* X[3];       // [m][2p+1][(p+1)^2][4] pair weights (FP64), see k_tables.cu
     const void* Xs[3];        // the same in the store type of the contraction arithmetic
     const float2* tdf[3];     // [G][4] double-float sin(pi xi), pi cos(pi xi), sin(2 pi xi), cos(2 pi xi)
     int arith;                // contraction arithmetic (arith.cuh: kArithF64 / kArithDF / kArithF32)
@@ -100,7 +101,7 @@ struct Tables {
 
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
-    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_NUM
+    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
@@ -177,7 +178,7 @@ inline int64_t box_items(int dim, int p, const Box& b, int stage) {
         case 0: return G0 * G1 * G2;                         // coefficient points
         case 1: return (dim == 3) ? (int64_t)b.R[2] * G1 * G0 : 0;  // stage Z
         case 2: return P3 * b.R[1] * G0;                     // stage Y
-        default: return P3 * ((int64_t)b.R[1] * W) * b.R[0]; // stage X
+        default: return P3 * (((int64_t)b.R[1] * W + kLinesX - 1) / kLinesX) * b.R[0]; // stage X
     }
 }
 

@@ -3,11 +3,11 @@
 // A_ij = sum_{k,l} sum_g K_kl(g) d_k B_i(g) d_l B_j(g) (Sec. 3.2, eq. ChangeOfVars)
 // factorises per direction: the Gauss points, the row index i_d and the
 // column offset delta_d = j_d - i_d of direction d meet only in the 1-D pair
-// weights X_d[i_d][pat][delta_d][t] (k_tables.cu).  The 3-D sum is
+// weights X_d[i_d][delta_d][t][pat] (k_tables.cu).  The 3-D sum is
 // contracted one direction at a time, slowest first, so every stage reads and
 // writes arrays whose fastest index is contiguous:
 //
-//   stage Z (3-D): K fields [6][g2][g1][g0]            -> T1 [8][(i2,d2)][g1][g0]
+//   stage Z (3-D): K fields [6][g2][g1][g0]            -> T1 [8][(i2,d2)][g1][g0]  (two launches of 4 combos)
 //   stage Y      : T1 (3-D) or K fields (2-D)          -> T2 [4][(i2,d2)][(i1,d1)][g0]
 //   stage X      : T2                                  -> rows [slot][row]
 //
@@ -25,10 +25,54 @@
 
 namespace iga {
 
+// The four pattern weights (00, 01, 10, 11) of one (delta, t) are contiguous:
+// two 16-byte loads for double / float2 values, one for float.
+template <class S>
+__device__ __forceinline__ void load_pats(const S* p, S& x00, S& x01, S& x10, S& x11)
+{
+    x00 = p[0]; x01 = p[1]; x10 = p[2]; x11 = p[3];
+}
+template <>
+__device__ __forceinline__ void load_pats<float2>(const float2* p, float2& x00, float2& x01, float2& x10, float2& x11)
+{
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    x00 = make_float2(a.x, a.y); x01 = make_float2(a.z, a.w);
+    x10 = make_float2(b.x, b.y); x11 = make_float2(b.z, b.w);
+}
+template <>
+__device__ __forceinline__ void load_pats<double>(const double* p, double& x00, double& x01, double& x10, double& x11)
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    x00 = a.x; x01 = a.y; x10 = b.x; x11 = b.y;
+}
+template <>
+__device__ __forceinline__ void load_pats<float>(const float* p, float& x00, float& x01, float& x10, float& x11)
+{
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    x00 = a.x; x01 = a.y; x10 = a.z; x11 = a.w;
+}
+
+// Q consecutive values starting at an offset that is a multiple of Q; 16-byte
+// vector loads when Q values span whole 16-byte words (then they are aligned).
+template <class S, int Q>
+__device__ __forceinline__ void load_run(const S* p, S* v)
+{
+    if constexpr ((Q * sizeof(S)) % 16 == 0) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        float4* v4 = reinterpret_cast<float4*>(v);
+#pragma unroll
+        for (int k = 0; k < (int)(Q * sizeof(S) / 16); ++k) v4[k] = p4[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v[k] = p[k];
+    }
+}
+
 // ---------------------------------------------------------------------------
-// stage Z: contract direction 2
+// stage Z: contract direction 2.  HALF selects combos 0..3 or 4..7 (two launches
+// keep the accumulators of one thread small enough for two blocks per SM).
 // ---------------------------------------------------------------------------
-template <class Pol, int P>
+template <class Pol, int P, int HALF>
 __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, double* scratch)
 {
     using S = typename Pol::store;
@@ -45,14 +89,13 @@ __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, 
     const int i3 = b.rlo[2] + i3l;
     const S* C = reinterpret_cast<const S*>(scratch + b.c_off);
     const int64_t fs = G2 * plane;
-    constexpr int ps = W * TT;                          // pattern stride
-    const S* Xi = reinterpret_cast<const S*>(T.Xs[2]) + (int64_t)i3 * 4 * W * TT;
+    const S* Xi = reinterpret_cast<const S*>(T.Xs[2]) + (int64_t)i3 * W * TT * 4;
 
-    A acc[W][8];
+    A acc[W][4];
 #pragma unroll
     for (int dd = 0; dd < W; ++dd)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[dd][k] = Pol::zero();
+        for (int k = 0; k < 4; ++k) acc[dd][k] = Pol::zero();
 
     // local element a of supp(B_i) meets supp(B_{i+delta}) exactly for dd = delta + P in [a, a + P]
 #pragma unroll
@@ -61,32 +104,36 @@ __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, 
         if (e3 < b.elo[2] || e3 >= b.elo[2] + b.E[2]) continue;
 #pragma unroll 1
         for (int r = 0; r < Q; ++r) {
-        const int t = a * Q + r;
-        const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + r) * plane + pp;
-        const S c0 = C[o], c1 = C[fs + o], c2 = C[2 * fs + o];
-        const S c3 = C[3 * fs + o], c4 = C[4 * fs + o], c5 = C[5 * fs + o];
+            const int t = a * Q + r;
+            const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + r) * plane + pp;
+            S c0, c1, c2, c3;
+            if (HALF == 0) { c0 = C[o]; c1 = C[fs + o]; c2 = C[3 * fs + o]; c3 = C[2 * fs + o]; }
+            else { c0 = C[2 * fs + o]; c1 = C[4 * fs + o]; c2 = C[5 * fs + o]; c3 = c0; }
 #pragma unroll
-        for (int dd = a; dd <= a + P; ++dd) {
-            const int xo = dd * TT + t;
-            const S x00 = Xi[xo], x01 = Xi[ps + xo], x10 = Xi[2 * ps + xo], x11 = Xi[3 * ps + xo];
-            Pol::mac(acc[dd][0], x00, c0);
-            Pol::mac(acc[dd][1], x00, c1);
-            Pol::mac(acc[dd][2], x00, c3);
-            Pol::mac(acc[dd][3], x01, c2);
-            Pol::mac(acc[dd][4], x10, c2);
-            Pol::mac(acc[dd][5], x01, c4);
-            Pol::mac(acc[dd][6], x10, c4);
-            Pol::mac(acc[dd][7], x11, c5);
-        }
+            for (int dd = a; dd <= a + P; ++dd) {
+                S x00, x01, x10, x11;
+                load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+                if (HALF == 0) {
+                    Pol::mac(acc[dd][0], x00, c0);   // (K00, 00)
+                    Pol::mac(acc[dd][1], x00, c1);   // (K01, 00)
+                    Pol::mac(acc[dd][2], x00, c2);   // (K11, 00)
+                    Pol::mac(acc[dd][3], x01, c3);   // (K02, 01)
+                } else {
+                    Pol::mac(acc[dd][0], x10, c0);   // (K02, 10)
+                    Pol::mac(acc[dd][1], x01, c1);   // (K12, 01)
+                    Pol::mac(acc[dd][2], x10, c1);   // (K12, 10)
+                    Pol::mac(acc[dd][3], x11, c2);   // (K22, 11)
+                }
+            }
         }
     }
     S* T1 = reinterpret_cast<S*>(scratch + b.t1_off);
     const int64_t P3 = (int64_t)b.R[2] * W;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
-            T1[((int64_t)k * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
+            T1[((int64_t)(4 * HALF + k) * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -110,8 +157,7 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
     const int i2l = (int)((item / G0) % R2);
     const int64_t pair3 = item / (G0 * R2);
     const int i2 = b.rlo[1] + i2l;
-    constexpr int ps = W * TT;
-    const S* Xi = reinterpret_cast<const S*>(T.Xs[1]) + (int64_t)i2 * 4 * W * TT;
+    const S* Xi = reinterpret_cast<const S*>(T.Xs[1]) + (int64_t)i2 * W * TT * 4;
 
     // input field f at local Gauss point g1 of direction 1
     const S* in;
@@ -136,32 +182,32 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
         if (e2 < b.elo[1] || e2 >= b.elo[1] + b.E[1]) continue;
 #pragma unroll 1
         for (int r = 0; r < Q; ++r) {
-        const int t = a * Q + r;
-        const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + r) * G0;
-        S v[NIN];
+            const int t = a * Q + r;
+            const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + r) * G0;
+            S v[NIN];
 #pragma unroll
-        for (int f = 0; f < NIN; ++f) v[f] = in[f * fstride + o];
+            for (int f = 0; f < NIN; ++f) v[f] = in[f * fstride + o];
 #pragma unroll
-        for (int dd = a; dd <= a + P; ++dd) {
-            const int xo = dd * TT + t;
-            const S x00 = Xi[xo], x01 = Xi[ps + xo], x10 = Xi[2 * ps + xo], x11 = Xi[3 * ps + xo];
-            if (DIM == 3) {
-                Pol::mac(acc[dd][0], x00, v[0]);   // A^00 -> group 0 (11 left in direction 0)
-                Pol::mac(acc[dd][1], x01, v[1]);   // A^01 -> group 1 (10)
-                Pol::mac(acc[dd][1], x00, v[3]);   // A^02 -> group 1
-                Pol::mac(acc[dd][2], x10, v[1]);   // A^10 -> group 2 (01)
-                Pol::mac(acc[dd][2], x00, v[4]);   // A^20 -> group 2
-                Pol::mac(acc[dd][3], x11, v[2]);   // A^11 -> group 3 (00)
-                Pol::mac(acc[dd][3], x10, v[5]);   // A^12 -> group 3
-                Pol::mac(acc[dd][3], x01, v[6]);   // A^21 -> group 3
-                Pol::mac(acc[dd][3], x00, v[7]);   // A^22 -> group 3
-            } else {
-                Pol::mac(acc[dd][0], x00, v[0]);   // A^00: K00, 00
-                Pol::mac(acc[dd][1], x01, v[1]);   // A^01: K01, 01
-                Pol::mac(acc[dd][2], x10, v[1]);   // A^10: K01, 10
-                Pol::mac(acc[dd][3], x11, v[2]);   // A^11: K11, 11
+            for (int dd = a; dd <= a + P; ++dd) {
+                S x00, x01, x10, x11;
+                load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+                if (DIM == 3) {
+                    Pol::mac(acc[dd][0], x00, v[0]);   // A^00 -> group 0 (11 left in direction 0)
+                    Pol::mac(acc[dd][1], x01, v[1]);   // A^01 -> group 1 (10)
+                    Pol::mac(acc[dd][1], x00, v[3]);   // A^02 -> group 1
+                    Pol::mac(acc[dd][2], x10, v[1]);   // A^10 -> group 2 (01)
+                    Pol::mac(acc[dd][2], x00, v[4]);   // A^20 -> group 2
+                    Pol::mac(acc[dd][3], x11, v[2]);   // A^11 -> group 3 (00)
+                    Pol::mac(acc[dd][3], x10, v[5]);   // A^12 -> group 3
+                    Pol::mac(acc[dd][3], x01, v[6]);   // A^21 -> group 3
+                    Pol::mac(acc[dd][3], x00, v[7]);   // A^22 -> group 3
+                } else {
+                    Pol::mac(acc[dd][0], x00, v[0]);   // A^00: K00, 00
+                    Pol::mac(acc[dd][1], x01, v[1]);   // A^01: K01, 01
+                    Pol::mac(acc[dd][2], x10, v[1]);   // A^10: K01, 10
+                    Pol::mac(acc[dd][3], x11, v[2]);   // A^11: K11, 11
+                }
             }
-        }
         }
     }
     S* T2 = reinterpret_cast<S*>(scratch + b.t2_off);
@@ -174,9 +220,11 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
 }
 
 // ---------------------------------------------------------------------------
-// stage X: contract direction 0 and write the stencil rows
+// stage X: contract direction 0 and write the stencil rows.  A thread takes
+// LINES consecutive (i1, delta_1) lines of one row i0, so every pair weight it
+// loads serves LINES rows of output.
 // ---------------------------------------------------------------------------
-template <class Pol, int P, int DIM>
+template <class Pol, int P, int DIM, int LINES>
 __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, double* scratch,
                                                     void* ell, int ell_f32, int64_t N, double* samples)
 {
@@ -187,73 +235,93 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
     // all have the same pair weights (translation invariance, Sec. 2.2): they
     // read one copy from shared memory, so a warp's loads are broadcasts.
     // Loaded before any thread of the block can leave.
-    __shared__ S sX[4 * W * TT];
+    __shared__ __align__(16) S sX[W * TT * 4];
     const bool has_card = g.m[0] >= 4 * P + 1;
     const S* X0 = reinterpret_cast<const S*>(T.Xs[0]);
     if (has_card)
-        for (int k = threadIdx.x; k < 4 * W * TT; k += blockDim.x) sX[k] = X0[(int64_t)(2 * P) * 4 * W * TT + k];
+        for (int k = threadIdx.x; k < W * TT * 4; k += blockDim.x) sX[k] = X0[(int64_t)(2 * P) * W * TT * 4 + k];
     __syncthreads();
     Box b;
     get_box(bs, DIM, P, 3, blockIdx.x, b);
     const int64_t G0 = (int64_t)b.E[0] * Q;
     const int64_t P3 = (DIM == 3) ? (int64_t)b.R[2] * W : 1;
     const int64_t P2 = (int64_t)b.R[1] * W;
+    const int64_t NL = (P2 + LINES - 1) / LINES;       // line groups
     const int R1 = b.R[0];
     const int64_t item = (int64_t)(blockIdx.x - b.blk[3]) * kBlock + threadIdx.x;
-    if (item >= P3 * P2 * R1) return;
+    if (item >= P3 * NL * R1) return;
     const int i1l = (int)(item % R1);
-    const int64_t pair2 = (item / R1) % P2;
-    const int64_t pair3 = item / (R1 * P2);
+    const int64_t lg = (item / R1) % NL;
+    const int64_t pair3 = item / (R1 * NL);
     const int i1 = b.rlo[0] + i1l;
-    const int i2 = b.rlo[1] + (int)(pair2 / W);
-    const int d2 = (int)(pair2 % W);
     const int i3 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
     const int d3 = (DIM == 3) ? (int)(pair3 % W) : 0;
     const int m0 = g.m[0];
-    constexpr int ps = W * TT;
     const bool card = has_card && i1 >= 2 * P && i1 <= m0 - 2 * P - 1;
-    const S* Xi = card ? sX : X0 + (int64_t)i1 * 4 * W * TT;
-    const S* T2 = reinterpret_cast<const S*>(scratch + b.t2_off) + (pair3 * P2 + pair2) * G0;
+    const S* Xi = card ? sX : X0 + (int64_t)i1 * W * TT * 4;
     const int64_t gs = P3 * P2 * G0;        // group stride
-
-    A acc[W];
+    int nl = (int)(P2 - lg * LINES);
+    if (nl > LINES) nl = LINES;
+    const S* T2[LINES];
 #pragma unroll
-    for (int dd = 0; dd < W; ++dd) acc[dd] = Pol::zero();
+    for (int l = 0; l < LINES; ++l)
+        T2[l] = reinterpret_cast<const S*>(scratch + b.t2_off) + (pair3 * P2 + lg * LINES + (l < nl ? l : 0)) * G0;
+
+    A acc[LINES][W];
+#pragma unroll
+    for (int l = 0; l < LINES; ++l)
+#pragma unroll
+        for (int dd = 0; dd < W; ++dd) acc[l][dd] = Pol::zero();
 #pragma unroll
     for (int a = 0; a <= P; ++a) {
         const int e1 = i1 - P + a;
         if (e1 < b.elo[0] || e1 >= b.elo[0] + b.E[0]) continue;
-#pragma unroll 1
-        for (int r = 0; r < Q; ++r) {
-        const int t = a * Q + r;
-        const int64_t o = (e1 - b.elo[0]) * Q + r;
-        const S v0 = T2[o], v1 = T2[gs + o], v2 = T2[2 * gs + o], v3 = T2[3 * gs + o];
+        const int64_t o = (int64_t)(e1 - b.elo[0]) * Q;
+        __align__(16) S v[LINES][4][Q];
 #pragma unroll
-        for (int dd = a; dd <= a + P; ++dd) {
-            const int xo = dd * TT + t;
-            Pol::mac(acc[dd], Xi[3 * ps + xo], v0);   // group 0: pattern 11
-            Pol::mac(acc[dd], Xi[2 * ps + xo], v1);   // group 1: pattern 10
-            Pol::mac(acc[dd], Xi[ps + xo], v2);       // group 2: pattern 01
-            Pol::mac(acc[dd], Xi[xo], v3);            // group 3: pattern 00
-        }
+        for (int l = 0; l < LINES; ++l)
+#pragma unroll
+            for (int gr = 0; gr < 4; ++gr) load_run<S, Q>(T2[l] + gr * gs + o, v[l][gr]);
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            const int t = a * Q + r;
+#pragma unroll
+            for (int dd = a; dd <= a + P; ++dd) {
+                S x00, x01, x10, x11;
+                load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+#pragma unroll
+                for (int l = 0; l < LINES; ++l) {
+                    Pol::mac(acc[l][dd], x11, v[l][0][r]);   // group 0: pattern 11
+                    Pol::mac(acc[l][dd], x10, v[l][1][r]);   // group 1: pattern 10
+                    Pol::mac(acc[l][dd], x01, v[l][2][r]);   // group 2: pattern 01
+                    Pol::mac(acc[l][dd], x00, v[l][3][r]);   // group 3: pattern 00
+                }
+            }
         }
     }
-    const int slot0 = W * (d2 + W * d3);
-    if (b.out_kind == 0) {
-        const int64_t row = i1 + (int64_t)m0 * (i2 + (int64_t)g.m[1] * i3);
-        if (ell_f32) {
-            float* out = (float*)ell;
 #pragma unroll
-            for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = (float)Pol::to_double(acc[dd]);
+    for (int l = 0; l < LINES; ++l) {
+        if (l >= nl) break;
+        const int64_t pair2 = lg * LINES + l;
+        const int i2 = b.rlo[1] + (int)(pair2 / W);
+        const int d2 = (int)(pair2 % W);
+        const int slot0 = W * (d2 + W * d3);
+        if (b.out_kind == 0) {
+            const int64_t row = i1 + (int64_t)m0 * (i2 + (int64_t)g.m[1] * i3);
+            if (ell_f32) {
+                float* out = (float*)ell;
+#pragma unroll
+                for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = (float)Pol::to_double(acc[l][dd]);
+            } else {
+                double* out = (double*)ell;
+#pragma unroll
+                for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = Pol::to_double(acc[l][dd]);
+            }
         } else {
-            double* out = (double*)ell;
 #pragma unroll
-            for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = Pol::to_double(acc[dd]);
+            for (int dd = 0; dd < W; ++dd)
+                samples[(int64_t)(slot0 + dd) * bs.n_samples + b.sample_id] = Pol::to_double(acc[l][dd]);
         }
-    } else {
-#pragma unroll
-        for (int dd = 0; dd < W; ++dd)
-            samples[(int64_t)(slot0 + dd) * bs.n_samples + b.sample_id] = Pol::to_double(acc[dd]);
     }
 }
 
@@ -266,7 +334,10 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
     if (g.dim == 3) {
         if (nb[1] > 0) {
             launch_begin(K_STAGE_Z, s);
-            k_stage_z<Pol, P><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            k_stage_z<Pol, P, 0><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            launch_end(K_STAGE_Z, s);
+            launch_begin(K_STAGE_Z, s);
+            k_stage_z<Pol, P, 1><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Z, s);
         }
         if (nb[2] > 0) {
@@ -276,7 +347,7 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
         }
         if (nb[3] > 0) {
             launch_begin(K_STAGE_X, s);
-            k_stage_x<Pol, P, 3><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
+            k_stage_x<Pol, P, 3, kLinesX><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
             launch_end(K_STAGE_X, s);
         }
     } else {
@@ -287,7 +358,7 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
         }
         if (nb[3] > 0) {
             launch_begin(K_STAGE_X, s);
-            k_stage_x<Pol, P, 2><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
+            k_stage_x<Pol, P, 2, kLinesX><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
             launch_end(K_STAGE_X, s);
         }
     }

@@ -1,8 +1,8 @@
 // K4: per-offset tensor-product B-spline interpolation of the stencil
 //     functions through their samples (Sec. 4.1, Sec. 6).
 // K5: surrogate rows of eq. DefinitionOfSurrogateMatrixSymmetricKernel
-//     (Sec. 5.3) written into the stencil-ELL values, with the
-//     kernel-preserving diagonal.
+//     (Sec. 5.3) written into the stencil-ELL values (pass 1, rows of
+//     Omega~), then the kernel-preserving diagonal of every row (pass 2).
 //
 // Interpolation reading: abscissae are the sample indices t_a = min(k0 + a M, k1);
 // the knot vector of degree q has (q+1)-fold end knots at t_0 and t_{ns-1}
@@ -205,13 +205,11 @@ cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* sam
 }
 
 // ---------------------------------------------------------------------------
-// K5: one thread per row.
-//  - rows outside Omega~ (written exactly by K3): diagonal := -(off-diagonal sum);
-//  - rows inside: for each slot with column j = i + delta,
+// K5, rows of Omega~: for each slot with column j = i + delta,
 //      j in Omega~, j > i : Phi~_delta(x~_i)                      (interpolated)
 //      j in Omega~, j < i : Phi~_{-delta}(x~_j)  (= A~_ji, the copied entry)
 //      j outside Omega~   : A_ji from the exact frame row j (= A_ij)
-//    then the diagonal := -(off-diagonal sum).
+// then, for every row, diagonal := -(off-diagonal sum).
 // The interpolant is evaluated in double-float arithmetic on the FP32 pipe
 // (about 48 significand bits); the diagonal sums are FP64.
 // ---------------------------------------------------------------------------
@@ -220,100 +218,122 @@ __device__ __forceinline__ T from_df(const DFAcc& a) { return PolDF::to_double(a
 template <>
 __device__ __forceinline__ float from_df<float>(const DFAcc& a) { return __fadd_rn(a.h, a.l); }
 
+// Pass 1 (rows of Omega~ only): one thread per (row, delta_1, delta_2) writes the
+// 2p+1 slots delta_0 = -p..p of that row.
 template <int P, int DIM, typename T>
-__global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, int empty_box, SplineBufs sb, T* vals)
+__global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, SplineBufs sb, T* vals)
 {
     constexpr int W = 2 * P + 1;
     constexpr int S = (DIM == 3) ? W * W * W : W * W;
     constexpr int C = (S - 1) / 2;
-    const int m0 = g.m[0], m1 = g.m[1], m2 = (DIM == 3) ? g.m[2] : 1;
-    const int64_t N = (int64_t)m0 * m1 * m2;
+    constexpr int NPAIR = (DIM == 3) ? W * W : W;
+    const int L0 = sp.L[0], L1 = sp.L[1], L2 = (DIM == 3) ? sp.L[2] : 1;
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)L0 * L1 * L2 * NPAIR;
+    if (item >= total) return;
+    const int e0i = (int)(item % L0);
+    int64_t rest = item / L0;
+    const int pr = (int)(rest % NPAIR);
+    rest /= NPAIR;
+    const int e1i = (int)(rest % L1);
+    const int e2i = (int)(rest / L1);
+    const int d1 = pr % W, d2 = (DIM == 3) ? pr / W : 0;
+    const int m0 = g.m[0], m1 = g.m[1];
+    const int64_t N = (int64_t)m0 * m1 * ((DIM == 3) ? g.m[2] : 1);
+    const int kk0 = sp.k0[0], kk1 = sp.k0[1], kk2 = (DIM == 3) ? sp.k0[2] : 0;
+    const int i0 = kk0 + e0i, i1 = kk1 + e1i, i2 = kk2 + e2i;
+    const int64_t i = i0 + (int64_t)m0 * (i1 + (int64_t)m1 * i2);
+    const int dl1 = d1 - P, dl2 = (DIM == 3) ? d2 - P : 0;
+    const int l1 = e1i + dl1, l2 = e2i + dl2;
+    const bool in12 = (l1 >= 0 && l1 < L1) && (l2 >= 0 && l2 < L2);
+    const int n0 = sp.ns[0], q0 = sp.qe[0];
+    const int sbase = W * (d1 + W * d2);
+#pragma unroll
+    for (int d0 = 0; d0 < W; ++d0) {
+        const int s = sbase + d0;
+        if (s == C) continue;
+        const int l0 = e0i + d0 - P;
+        T out;
+        if (in12 && l0 >= 0 && l0 < L0) {
+            // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
+            const bool upper = s > C;
+            const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
+            const int e0 = upper ? e0i : l0, e1 = upper ? e1i : l1, e2 = upper ? e2i : l2;
+            const float2* Pp = sb.partial + (((int64_t)u * L2 + e2) * L1 + e1) * n0 + sb.espan[0][e0];
+            const float2* E = sb.eval0 + e0;
+            DFAcc v = PolDF::zero();
+            for (int k = 0; k <= q0; ++k) PolDF::mac(v, E[(int64_t)k * L0], Pp[k]);
+            out = from_df<T>(v);
+        } else {
+            const int64_t jrow = (i0 + d0 - P) + (int64_t)m0 * ((i1 + dl1) + (int64_t)m1 * (i2 + dl2));
+            out = vals[(int64_t)(S - 1 - s) * N + jrow];
+        }
+        vals[(int64_t)s * N + i] = out;
+    }
+}
+
+// Pass 2 (every row): the kernel-preserving diagonal, minus the sum of the
+// row's stored off-diagonal values.  The sum is FP64, whose rounding stays
+// ~1e-15 of the row's mass even for 1330 terms (a double-float sum would lose
+// ~1e-12).
+template <int P, int DIM, typename T>
+__global__ void __launch_bounds__(kBlock) k_diag(int64_t N, T* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
-    const int kk0 = sp.k0[0], kk1 = sp.k0[1], kk2 = (DIM == 3) ? sp.k0[2] : 0;
-    const int L0 = sp.L[0], L1 = sp.L[1], L2 = (DIM == 3) ? sp.L[2] : 1;
-    bool inbox = !empty_box;
-    if (inbox) {
-        inbox = (i0 >= kk0 && i0 < kk0 + L0) && (i1 >= kk1 && i1 < kk1 + L1);
-        if (DIM == 3) inbox = inbox && (i2 >= kk2 && i2 < kk2 + L2);
-    }
-    // The diagonal is minus a sum of up to (2p+1)^n - 1 stored values: it is
-    // accumulated in FP64, whose rounding stays ~1e-15 of the row's mass even
-    // for 1330 terms (a double-float sum would lose ~1e-12).
-    double sum = 0.0;
-    if (!inbox) {
-#pragma unroll 8
-        for (int s = 0; s < S; ++s)
-            if (s != C) sum += (double)vals[(int64_t)s * N + i];
-        vals[(int64_t)C * N + i] = (T)(-sum);
-        return;
-    }
-    const int n0 = sp.ns[0], q0 = sp.qe[0];
-    const int e0i = i0 - kk0, e1i = i1 - kk1, e2i = i2 - kk2;
-    constexpr int n2 = (DIM == 3) ? W : 1;
-    for (int d2 = 0; d2 < n2; ++d2) {
-        for (int d1 = 0; d1 < W; ++d1) {
-            const int dl1 = d1 - P, dl2 = (DIM == 3) ? d2 - P : 0;
-            const int l1 = e1i + dl1, l2 = e2i + dl2;
-            const bool in12 = (l1 >= 0 && l1 < L1) && (l2 >= 0 && l2 < L2);
-            const int sbase = W * (d1 + W * d2);
-#pragma unroll
-            for (int d0 = 0; d0 < W; ++d0) {
-                const int s = sbase + d0;
-                if (s == C) continue;
-                const int l0 = e0i + d0 - P;
-                T out;
-                if (in12 && l0 >= 0 && l0 < L0) {
-                    // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
-                    const bool upper = s > C;
-                    const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
-                    const int e0 = upper ? e0i : l0, e1 = upper ? e1i : l1, e2 = upper ? e2i : l2;
-                    const float2* Pp = sb.partial + (((int64_t)u * L2 + e2) * L1 + e1) * n0 + sb.espan[0][e0];
-                    const float2* E = sb.eval0 + e0;
-                    DFAcc v = PolDF::zero();
-                    for (int k = 0; k <= q0; ++k) PolDF::mac(v, E[(int64_t)k * L0], Pp[k]);
-                    out = from_df<T>(v);
-                } else {
-                    const int64_t jrow = (i0 + d0 - P) + (int64_t)m0 * ((i1 + dl1) + (int64_t)m1 * (i2 + dl2));
-                    out = vals[(int64_t)(S - 1 - s) * N + jrow];
-                }
-                vals[(int64_t)s * N + i] = out;
-                sum += (double)out;
-            }
-        }
-    }
-    vals[(int64_t)C * N + i] = (T)(-sum);
+    // four interleaved partial sums keep more loads in flight; combined in a fixed order
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int s = 0; s < S; ++s)
+        if (s != C) part[s & 3] += (double)vals[(int64_t)s * N + i];
+    vals[(int64_t)C * N + i] = (T)(-((part[0] + part[1]) + (part[2] + part[3])));
 }
 
 template <int P>
 static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const SplineBufs& sb, void* ell,
-                   int f32, unsigned grid, cudaStream_t s)
+                   int f32, cudaStream_t s)
 {
-    if (g.dim == 3) {
-        if (f32) k_fill<P, 3, float><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (float*)ell);
-        else k_fill<P, 3, double><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (double*)ell);
-    } else {
-        if (f32) k_fill<P, 2, float><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (float*)ell);
-        else k_fill<P, 2, double><<<grid, kBlock, 0, s>>>(g, sp, empty_box, sb, (double*)ell);
+    const int W = 2 * P + 1;
+    const int64_t N = (int64_t)g.m[0] * g.m[1] * (g.dim == 3 ? g.m[2] : 1);
+    const unsigned gdiag = (unsigned)((N + kBlock - 1) / kBlock);
+    if (!empty_box) {
+        const int64_t total = (int64_t)sp.L[0] * sp.L[1] * (g.dim == 3 ? (int64_t)sp.L[2] * W * W : W);
+        const unsigned gfill = (unsigned)((total + kBlock - 1) / kBlock);
+        launch_begin(K_FILL, s);
+        if (g.dim == 3) {
+            if (f32) k_fill<P, 3, float><<<gfill, kBlock, 0, s>>>(g, sp, sb, (float*)ell);
+            else k_fill<P, 3, double><<<gfill, kBlock, 0, s>>>(g, sp, sb, (double*)ell);
+        } else {
+            if (f32) k_fill<P, 2, float><<<gfill, kBlock, 0, s>>>(g, sp, sb, (float*)ell);
+            else k_fill<P, 2, double><<<gfill, kBlock, 0, s>>>(g, sp, sb, (double*)ell);
+        }
+        launch_end(K_FILL, s);
     }
+    launch_begin(K_DIAG, s);
+    if (g.dim == 3) {
+        if (f32) k_diag<P, 3, float><<<gdiag, kBlock, 0, s>>>(N, (float*)ell);
+        else k_diag<P, 3, double><<<gdiag, kBlock, 0, s>>>(N, (double*)ell);
+    } else {
+        if (f32) k_diag<P, 2, float><<<gdiag, kBlock, 0, s>>>(N, (float*)ell);
+        else k_diag<P, 2, double><<<gdiag, kBlock, 0, s>>>(N, (double*)ell);
+    }
+    launch_end(K_DIAG, s);
 }
 
 cudaError_t launch_fill(const Geo& g, const SplinePlan& sp, int empty_box, const SplineBufs& sb,
                         void* ell, int ell_f32, cudaStream_t s)
 {
-    const int64_t N = (int64_t)g.m[0] * g.m[1] * (g.dim == 3 ? g.m[2] : 1);
-    const unsigned grid = (unsigned)((N + kBlock - 1) / kBlock);
-    launch_begin(K_FILL, s);
     switch (g.p) {
-    case 1: fill_p<1>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
-    case 2: fill_p<2>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
-    case 3: fill_p<3>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
-    case 4: fill_p<4>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
-    case 5: fill_p<5>(g, sp, empty_box, sb, ell, ell_f32, grid, s); break;
-    default: break;
+    case 1: fill_p<1>(g, sp, empty_box, sb, ell, ell_f32, s); break;
+    case 2: fill_p<2>(g, sp, empty_box, sb, ell, ell_f32, s); break;
+    case 3: fill_p<3>(g, sp, empty_box, sb, ell, ell_f32, s); break;
+    case 4: fill_p<4>(g, sp, empty_box, sb, ell, ell_f32, s); break;
+    case 5: fill_p<5>(g, sp, empty_box, sb, ell, ell_f32, s); break;
+    default: return cudaErrorInvalidValue;
     }
-    launch_end(K_FILL, s);
     return cudaGetLastError();
 }
 

@@ -155,7 +155,7 @@ cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[
 // Pair weights.  For direction d, row function i, offset delta (column
 // j = i + delta) and local point t = a (p+1) + r of supp(B_i) (element
 // e = i - p + a, Gauss point r), pattern pat = 2 alpha + beta:
-//   X[i][pat][delta + p][t] = w_r h  b_i^(alpha)(x_g)  b_j^(beta)(x_g),
+//   X[i][delta + p][t][pat] = w_r h  b_i^(alpha)(x_g)  b_j^(beta)(x_g),
 // zero when e is outside the mesh, j outside [0, m) or b_j vanishes on e.
 // The product over directions of these factors, summed over the Gauss
 // points, is the quadrature of d^alpha B_i d^beta B_j (Sec. 3.2, eq. ChangeOfVars).
@@ -177,12 +177,12 @@ __global__ void __launch_bounds__(kBlock) k_pairs(Geo g, PairArgs A)
     const int64_t total = (int64_t)4 * m * W * TT;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int t = (int)(idx % TT);
-    int64_t rest = idx / TT;
+    const int pat = (int)(idx % 4);
+    int64_t rest = idx / 4;
+    const int t = (int)(rest % TT);
+    rest /= TT;
     const int dd = (int)(rest % W);
-    rest /= W;
-    const int pat = (int)(rest % 4);
-    const int i = (int)(rest / 4);
+    const int i = (int)(rest / W);
     const int alpha = pat >> 1, beta = pat & 1;
     const int e = i - p + t / Q, r = t % Q;
     const int j = i + dd - p;
