@@ -431,6 +431,20 @@ def run_gpu(args, wl):
     del vs, ve
     rowsum = float(A.apply(torch.ones_like(x)).double().abs().max().item())
 
+    # stated accuracy of the discrete solution: CG on both matrices, same load vector
+    solution = None
+    if not args.no_solve:
+        f = torch.from_numpy(W.rhs_vector(prob.N, seed=wl.seed)).to(dev)
+        u_e, it_e, res_e = E.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+        u_s, it_s, res_s = A.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+        err = u_s - u_e
+        Ee = E.apply(err.to(tdt)).double() if tdt == torch.float64 else E.apply(err.float()).double()
+        Eu = E.apply(u_e.to(tdt)).double()
+        solution = {"rel_l2": float(err.norm() / u_e.norm()),
+                    "rel_energy": float(torch.sqrt(torch.dot(err, Ee) / torch.dot(u_e, Eu))),
+                    "cg_iters": {"exact": it_e, "surrogate": it_s}, "cg_rel_residual": max(res_e, res_s),
+                    "load": "f_i ~ U[-1,1] (seeded), homogeneous Dirichlet"}
+
     if rank != 0:
         return 0
     peaks, peak_kind = measured_peaks()
@@ -485,6 +499,7 @@ def run_gpu(args, wl):
                   "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof_e.items() if v[0]}},
         "speedup_surrogate_vs_exact": ms_e_max / ms_s_max,
         "entry_error": {"surrogate_vs_exact_max_rel": entry_err, "row_sum_max_abs": rowsum},
+        "solution_error": solution,
         "kernels": per_kernel,
         "roofline": roof,
         "spmv_roofline": spmv_roof,
@@ -510,6 +525,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the oracle baseline")
     ap.add_argument("--ref-rows", type=int, default=48, help="rows per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the CG solution-error report")
+    ap.add_argument("--cg-tol", type=float, default=1e-10)
+    ap.add_argument("--cg-maxit", type=int, default=20000)
     ap.add_argument("--mode", choices=["both", "surrogate", "exact"], default="both",
                     help="profiling helper: time only one of the two steps and print a short line")
     args = ap.parse_args(argv)

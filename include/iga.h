@@ -154,6 +154,22 @@ int iga_apply(iga_matrix_t A, const void* x, void* y, void* stream);
  */
 int iga_apply_host(iga_matrix_t A, const void* x_host, void* y_host, void* stream);
 
+/*
+ * Conjugate gradients on the Dirichlet-reduced system A_II u_I = f_I (Sec. 6,
+ * Remark with eq. BlockSystem: the dofs of basis functions with an index 0 or
+ * m-1 in some direction carry homogeneous Dirichlet values and are
+ * eliminated).  f, u: caller-owned DEVICE arrays of N doubles; f's Dirichlet
+ * entries are ignored, u returns the solution with zeros on Dirichlet dofs
+ * (the start vector is zero).  Stops when ||f_I - A_II u_I|| <= tol ||f_I|| or
+ * after maxit CG iterations.  IGA_F64 matrices: CG in FP64.  IGA_F32
+ * matrices: iterative refinement -- the residual is computed in FP64 (the
+ * FP32 values promoted), an FP32 CG solves for the correction to 1e-4, and
+ * the correction is added in FP64.  iters / relres return the total CG
+ * iterations and the final relative residual (FP64).  Synchronises `stream`.
+ */
+int iga_cg(iga_matrix_t A, const double* f, double* u, double tol, int maxit, void* stream,
+           int* iters, double* relres);
+
 /* Sizes: N dofs, S slots, structural nonzeros prod_d(m_d(2p+1) - p(p+1)), dtype. Any out pointer may be NULL. */
 int iga_matrix_info(iga_matrix_t A, int64_t* N, int32_t* S, int64_t* nnz, int32_t* dtype);
 

@@ -187,6 +187,24 @@ class Matrix:
                                              ctypes.c_void_p(_stream_ptr(stream))))
         return out
 
+    def cg(self, f, tol: float = 1e-10, maxit: int = 100000, stream=None):
+        """Solve the Dirichlet-reduced system A_II u_I = f_I on the GPU (iga_cg).
+
+        f: CUDA float64 tensor of N entries.  Returns (u, iterations, relative residual)."""
+        import torch
+        if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == torch.float64 and f.numel() == self.N
+                and f.is_contiguous()):
+            raise ValueError("f must be a contiguous CUDA float64 tensor of N elements")
+        u = torch.empty_like(f)
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        L = load()
+        L.iga_cg.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        _check(L.iga_cg(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()), float(tol), int(maxit),
+                        ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(it), ctypes.byref(rel)))
+        return u, it.value, rel.value
+
     def device_ptr(self) -> int:
         p = ctypes.c_void_p()
         _check(load().iga_matrix_values(self._h, ctypes.byref(p)))

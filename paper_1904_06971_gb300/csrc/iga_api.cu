@@ -57,7 +57,7 @@ std::vector<cudaEvent_t> g_events;
 thread_local cudaEvent_t t_begin = nullptr;
 
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
-                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag"};
+                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg"};
 
 cudaEvent_t take_event()
 {
@@ -417,6 +417,28 @@ void launch_begin(int kid, cudaStream_t s)
     } else {
         t_begin = nullptr;
     }
+}
+
+int matrix_fields(iga_matrix_t A, int* dim, int* p, int m[3], int64_t* N, const void** vals, int* f32)
+{
+    if (!A) return fail(IGA_EINVAL, "null matrix");
+    *dim = A->dim;
+    *p = A->p;
+    for (int d = 0; d < 3; ++d) m[d] = A->m[d];
+    *N = A->N;
+    *vals = A->values;
+    *f32 = A->dtype == IGA_F32;
+    return IGA_OK;
+}
+
+cudaError_t pool_alloc(size_t bytes, cudaStream_t s, void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool;
+    if ((e = device_pool(dev, &pool)) != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(out, bytes, pool, s);
 }
 
 int current_arith(int dtype)

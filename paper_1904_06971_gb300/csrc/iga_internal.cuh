@@ -101,7 +101,7 @@ struct Tables {
 
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
-    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_NUM
+    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,

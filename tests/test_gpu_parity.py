@@ -260,3 +260,34 @@ def test_double_float_coefficients_match_fp64_path(iga, arith):
     got = gpu_exact(iga, prob)
     assert rel(got, ref) <= 1e-12
     assert rel(got, oracle.exact_matrix(prob)) <= TOL64
+
+
+@pytest.mark.parametrize("kind", ["exact", "surrogate"])
+def test_cg_matches_oracle(iga, kind):
+    """GPU CG on the Dirichlet-reduced system vs the oracle's CG (same matrix values)."""
+    wl = W.CFG_2D_P2
+    prob = wl.problem
+    A = iga.assemble_exact(prob) if kind == "exact" else iga.assemble_surrogate(prob, wl.M, wl.q)
+    vals = A.values_host()
+    f = W.rhs_vector(prob.N)
+    u, it, rel_res = A.cg(torch.from_numpy(f).cuda(), tol=1e-12)
+    A.destroy()
+    uref, _, _ = oracle.cg(vals, prob, f, tol=1e-13)
+    u = u.cpu().numpy()
+    assert rel_res <= 1e-12 and it > 10
+    assert np.abs(u - uref).max() <= 1e-9 * np.abs(uref).max()
+    assert np.all(u[np.setdiff1d(np.arange(prob.N), oracle.interior_dofs(prob))] == 0.0)
+
+
+def test_cg_fp32_iterative_refinement(iga):
+    """FP32 matrix: FP64-residual refinement reaches an FP64-level residual on the stored system."""
+    prob = W.Problem(dim=3, p=2, n_el=(14, 12, 13), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d",
+                     kappa_b=0.5)
+    A = iga.assemble_surrogate(prob, 3, 3, dtype="f32")
+    v32 = A.values_host()
+    f = W.rhs_vector(prob.N, seed=2)
+    u, it, rel_res = A.cg(torch.from_numpy(f).cuda(), tol=1e-11)
+    A.destroy()
+    assert rel_res <= 1e-11
+    uref, _, _ = oracle.cg(v32.astype(np.float64), prob, f, tol=1e-13)
+    assert np.abs(u.cpu().numpy() - uref).max() <= 1e-8 * np.abs(uref).max()
