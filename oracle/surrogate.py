@@ -203,13 +203,19 @@ def bspline_basis(knots: np.ndarray, q: int, x: np.ndarray) -> np.ndarray:
     """[len(x), nb] values of all degree-q B-splines on `knots` at points x.
 
     Cox-de Boor recursion, N_{i,0} = 1 on [t_i, t_{i+1}); x equal to the last
-    knot belongs to the last non-empty interval; 0/0 read as 0.
+    knot belongs to the last non-empty interval; 0/0 read as 0.  A knot vector
+    with no non-empty interval (one sample, q = 0) has the single basis
+    function 1: the interpolant through one sample is that constant.
     """
     knots = np.asarray(knots, dtype=np.float64)
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     nt = len(knots)
     nb = nt - q - 1
     nonempty = np.nonzero(knots[1:] > knots[:-1])[0]
+    if len(nonempty) == 0:
+        # a single abscissa: degree 0 with one basis function, the constant 1
+        assert q == 0 and nb == 1
+        return np.ones((len(x), 1))
     last = nonempty[-1]
     N = np.zeros((len(x), nt - 1))
     for i in range(nt - 1):

@@ -147,6 +147,16 @@ def test_empty_omega_is_exact():
     assert oracle.relative_entry_error(oracle.surrogate_matrix(prob, 4, 3), A) < 1e-13
 
 
+def test_single_index_omega_is_exact():
+    """One index of Omega~ per direction: one sample, a constant interpolant equal to it."""
+    prob = W.Problem(dim=2, p=2, n_el=(7, 7), map_kind="sinprod", map_amp=0.05,
+                     kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.5)   # m = 9: box [4, 4]
+    setup = oracle.surrogate_setup(prob, 4, 3)
+    assert setup.samples == [[4], [4]] and setup.q_eff == [0, 0]
+    A = oracle.exact_matrix(prob)
+    assert oracle.relative_entry_error(oracle.surrogate_matrix(prob, 4, 3), A) < 1e-13
+
+
 def _offdiag_max(X, prob):
     c = oracle.center_slot(prob.dim, prob.p)
     Y = X.copy()
