@@ -141,6 +141,36 @@ int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map
                            void* stream, iga_matrix_t* A);
 
 /*
+ * Choice of the interpolation domains of the surrogate.
+ *   IGA_DOMAINS_COMMON: every stencil function is interpolated on the common
+ *     set Omega~ of Sec. 4 (the index box [2p, m-2p-1]); rows outside it are
+ *     exact (iga_assemble_surrogate).
+ *   IGA_DOMAINS_PER_OFFSET: each stencil function Phi_delta is interpolated on
+ *     its own domain Omega~_delta (Sec. 3.2, and Sec. 4 on reformulating with
+ *     one interpolation operator per delta): the indices k with k and k + delta
+ *     both cardinal, i.e. in [p, m-p-1] in every direction.  Only entries with a
+ *     non-cardinal basis function are exact, so exact rows are the frame of
+ *     width p.  Samples per direction: every M-th index from p, and the p + 1
+ *     first and last cardinal indices (the ends of every Omega~_delta); each
+ *     offset interpolates through the samples inside its own domain.
+ */
+#define IGA_DOMAINS_COMMON 0
+#define IGA_DOMAINS_PER_OFFSET 1
+
+/*
+ * Surrogate assembly (eq. DefinitionOfSurrogateMatrixSymmetricKernel) with the
+ * interpolation domains chosen by `domains` (IGA_DOMAINS_*): for i < j with
+ * x~_i in the domain of delta = x~_j - x~_i, A~_ij = Phi~_delta(x~_i); for i > j
+ * the copy A~_ji; every other off-diagonal entry exact; every diagonal entry
+ * minus its row's off-diagonal sum.  IGA_DOMAINS_COMMON is iga_assemble_surrogate.
+ * An unknown `domains` value returns IGA_EINVAL.  Other arguments as for
+ * iga_assemble_surrogate.
+ */
+int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_map_t* map,
+                                   const iga_kappa_t* kappa, int M, int q, int domains,
+                                   int dtype, void* stream, iga_matrix_t* A);
+
+/*
  * y = A x (eq. DiscreteVariationalProblems), stencil SpMV.  x and y are
  * caller-owned DEVICE arrays of N elements of the matrix dtype (double for
  * IGA_F64, float for IGA_F32); x and y must not overlap.

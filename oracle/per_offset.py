@@ -14,11 +14,14 @@ DefinitionOfSurrogateMatrixSymmetricKernel (Sec. 5.3), in the paper's order:
 2. Omega~_delta in indices: the k with k and k + delta_d both cardinal in
    every direction d (``offset_domain``).  The union of all of them is the
    cardinal box, their intersection the box [2p, m-2p-1] of Sec. 4.
-3. Sec. 6 sampling, applied to every Omega~_delta: every M-th index of one
-   lattice anchored at the first cardinal index p, plus both end indices of
-   Omega~_delta (``offset_samples``).  Anchoring every offset on the same
-   lattice makes the sample rows of different offsets coincide, so the union
-   of the sample grids of all offsets stays small.
+3. Sec. 6 sampling, applied to every Omega~_delta on one shared lattice,
+   every M-th index from the first cardinal index p: an offset samples the two
+   ends k0, k1 of its own domain and the lattice points at least M/2 away from
+   both ends (``offset_samples``), so its knot spacing stays between M/2 and
+   3M/2 -- quasi-uniform as Sec. 4.1 asks of the knot vector.  All offsets
+   together sample the lattice and the p + 1 first and last cardinal indices
+   (the ends of every Omega~_delta, ``union_samples``): those are the rows
+   assembled by quadrature.
 4. Sec. 4.1: per upper offset, the tensor-product not-a-knot B-spline
    interpolant of degree q through its own sample grid (same knot reading as
    ``surrogate.interp_knots``; degree lowered to n_s - 1 with fewer than
@@ -55,16 +58,23 @@ def offset_domain(p: int, m: int, dd: int):
     return c0 + max(0, -dd), c1 - max(0, dd)
 
 
-def offset_samples(p: int, m: int, M: int, dd: int) -> List[int]:
-    """Sample indices of Omega~_delta in one direction (Sec. 6 applied per offset).
+def union_samples(p: int, m: int, M: int) -> List[int]:
+    """Sample indices of one direction shared by all offsets: the lattice p + aM
+    in the cardinal range, and the p + 1 first and last cardinal indices."""
+    c0, c1 = cardinal_range(p, m)
+    lattice = set(range(c0, c1 + 1, M))
+    ends = set(range(c0, min(c0 + p, c1) + 1)) | set(range(max(c1 - p, c0), c1 + 1))
+    return sorted(lattice | ends)
 
-    Lattice points p + aM strictly inside (k0, k1), plus k0 and k1.
-    """
+
+def offset_samples(p: int, m: int, M: int, dd: int) -> List[int]:
+    """Sample indices of Omega~_delta in one direction: its ends k0, k1 and the
+    lattice points p + aM with distance >= M/2 from both ends."""
     k0, k1 = offset_domain(p, m, dd)
     if k1 < k0:
         return []
     c0 = cardinal_range(p, m)[0]
-    inner = [k for k in range(c0, k1, M) if k > k0]
+    inner = [k for k in range(c0, k1 + 1, M) if 2 * (k - k0) >= M and 2 * (k1 - k) >= M]
     return sorted(set([k0] + inner + [k1]))
 
 
@@ -94,9 +104,9 @@ def per_offset_setup(prob, M: int, q: int) -> PerOffsetSetup:
     c0 = [cardinal_range(p, md)[0] for md in m]
     c1 = [cardinal_range(p, md)[1] for md in m]
 
-    # sample indices of every offset component, and their union per direction
+    # sample indices per direction, and those of every offset component
+    union = [union_samples(p, md, M) for md in m]
     samp = [{dd: offset_samples(p, m[d], M, dd) for dd in range(-p, p + 1)} for d in range(dim)]
-    union = [sorted(set(k for dd in range(-p, p + 1) for k in samp[d][dd])) for d in range(dim)]
 
     # exact stencil rows at every point of the union grid
     grids = np.meshgrid(*[np.array(u) for u in union], indexing="ij")

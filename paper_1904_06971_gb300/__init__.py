@@ -69,6 +69,9 @@ def load():
         L.iga_assemble_surrogate.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                              ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              vp, ctypes.POINTER(H)]
+        L.iga_assemble_surrogate_domains.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                                     ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, vp, ctypes.POINTER(H)]
         L.iga_apply.argtypes = [H, vp, vp, vp]
         L.iga_apply_host.argtypes = [H, vp, vp, vp]
         L.iga_matrix_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -231,13 +234,25 @@ def assemble_exact(prob, dtype="f64", stream=None, out: Optional[Matrix] = None)
     return out if out is not None else Matrix(h.value)
 
 
-def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Optional[Matrix] = None) -> Matrix:
-    """Symmetric kernel-preserving surrogate stiffness matrix on the GPU (iga_assemble_surrogate)."""
+DOMAINS = {"common": 0, "per_offset": 1}       # IGA_DOMAINS_COMMON / IGA_DOMAINS_PER_OFFSET
+
+
+def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Optional[Matrix] = None,
+                       domains: str = "common") -> Matrix:
+    """Symmetric kernel-preserving surrogate stiffness matrix on the GPU.
+
+    domains='common' interpolates on Omega~ (iga_assemble_surrogate); 'per_offset'
+    on each Omega~_delta (iga_assemble_surrogate_domains)."""
     pt, mp, kp = _structs(prob)
     h = ctypes.c_void_p(out.handle.value if out is not None else None)
-    _check(load().iga_assemble_surrogate(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
-                                         int(M), int(q), _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)),
-                                         ctypes.byref(h)))
+    st = ctypes.c_void_p(_stream_ptr(stream))
+    if domains == "common":
+        _check(load().iga_assemble_surrogate(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
+                                             int(M), int(q), _dtype_code(dtype), st, ctypes.byref(h)))
+    else:
+        _check(load().iga_assemble_surrogate_domains(ctypes.byref(pt), int(prob.p), ctypes.byref(mp),
+                                                     ctypes.byref(kp), int(M), int(q), DOMAINS[domains],
+                                                     _dtype_code(dtype), st, ctypes.byref(h)))
     return out if out is not None else Matrix(h.value)
 
 

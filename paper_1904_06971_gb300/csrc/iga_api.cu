@@ -163,8 +163,42 @@ struct Layout {
     int64_t take(int64_t n_doubles) { int64_t o = total; total += align_up(std::max<int64_t>(n_doubles, 1), 32); return o; }
 };
 
+// Sample axis of one direction (SampleAxis in iga_internal.cuh).
+SampleAxis common_axis(int k0, int k1, int M)
+{
+    SampleAxis a;
+    memset(&a, 0, sizeof(a));
+    a.c0 = k0; a.M = M; a.n_lo = 0; a.j_first = 0;
+    a.n_mid = (k1 - k0) / M + 1;
+    a.hi0 = k1;
+    a.n_hi = ((k1 - k0) % M) ? 1 : 0;
+    a.n = a.n_mid + a.n_hi;
+    return a;
+}
+
+SampleAxis per_offset_axis(int p, int m, int M)
+{
+    SampleAxis a;
+    memset(&a, 0, sizeof(a));
+    const int c0 = p, c1 = m - p - 1;
+    a.c0 = c0; a.M = M;
+    if (c1 - c0 <= 2 * p + 1) {          // the two end runs meet: every cardinal index
+        a.n_lo = c1 - c0 + 1;
+        a.hi0 = c1 + 1;
+    } else {
+        a.n_lo = p + 1;
+        a.j_first = p / M + 1;                      // first lattice point past the low run
+        const int j_last = (c1 - p - 1 - c0) / M;   // last lattice point before the high run
+        a.n_mid = std::max(0, j_last - a.j_first + 1);
+        a.hi0 = c1 - p;
+        a.n_hi = p + 1;
+    }
+    a.n = a.n_lo + a.n_mid + a.n_hi;
+    return a;
+}
+
 int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
-             int M, int q, int dtype, void* stream_v, iga_matrix_t* out)
+             int M, int q, int domains, int dtype, void* stream_v, iga_matrix_t* out)
 {
     t_err.clear();
     Geo g;
@@ -175,6 +209,8 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     if (surrogate) {
         if (M < 1) return fail(IGA_EINVAL, "sampling parameter M must be >= 1 (got %d)", M);
         if (q < 0 || q > kMaxQ) return fail(IGA_EUNSUPPORTED, "interpolation degree q must be in 0..%d (got %d)", kMaxQ, q);
+        if (domains != IGA_DOMAINS_COMMON && domains != IGA_DOMAINS_PER_OFFSET)
+            return fail(IGA_EINVAL, "domains must be IGA_DOMAINS_COMMON or IGA_DOMAINS_PER_OFFSET (got %d)", domains);
     }
     const int dim = g.dim, W = 2 * p + 1, Q = p + 1, TT = Q * Q;
     const int S = (dim == 3) ? W * W * W : W * W;
@@ -201,38 +237,61 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     memset(&bs, 0, sizeof(bs));
     SplinePlan sp;
     memset(&sp, 0, sizeof(sp));
-    sp.dim = dim; sp.q = q; sp.S = S; sp.c = (S - 1) / 2;
+    sp.dim = dim; sp.q = q; sp.S = S; sp.c = (S - 1) / 2; sp.nv = W;
+    sp.all = (domains == IGA_DOMAINS_COMMON);
     int empty = 0;
     bool do_spline = false;
     std::vector<Box> boxes;
     if (surrogate) {
-        int k0 = 2 * p, k1[3] = {0, 0, 0};
+        // region of rows with interpolated entries, [r0, r1] per direction: the box
+        // Omega~ = [2p, m-2p-1] (Sec. 4), or the cardinal box [p, m-p-1] with
+        // per-offset domains (Sec. 3.2); the frame outside it is exact
+        const bool per_offset = (domains == IGA_DOMAINS_PER_OFFSET);
+        const int k0 = per_offset ? p : 2 * p;
+        int k1[3] = {0, 0, 0};
         for (int d = 0; d < dim; ++d) {
-            k1[d] = g.m[d] - 2 * p - 1;
+            k1[d] = g.m[d] - k0 - 1;
             if (k1[d] < k0) empty = 1;
         }
         if (!empty) {
-            for (int d = 0; d < dim; ++d) {
-                sp.k0[d] = k0;
-                sp.L[d] = k1[d] - k0 + 1;
-                const int span = k1[d] - k0;
-                sp.ns[d] = span / M + 1 + ((span % M) ? 1 : 0);
-                sp.qe[d] = std::min(q, sp.ns[d] - 1);
-                if (sp.ns[d] > 4096) return fail(IGA_EUNSUPPORTED, "more than 4096 samples per direction");
-                bs.ns[d] = sp.ns[d];
-                bs.k0[d] = k0;
-                bs.k1[d] = k1[d];
+            for (int d = 0; d < 3; ++d) {
+                if (d >= dim) {
+                    sp.ax[d] = common_axis(0, 0, 1);
+                    sp.nu[d] = 1;
+                    sp.r0[d] = sp.r1[d] = 0;
+                    sp.Lmax[d] = 1;
+                    for (int v = 0; v < W; ++v) { sp.L[d][v] = 1; sp.ns[d][v] = 1; }
+                    continue;
+                }
+                sp.ax[d] = per_offset ? per_offset_axis(p, g.m[d], M) : common_axis(k0, k1[d], M);
+                sp.nu[d] = sp.ax[d].n;
+                if (sp.nu[d] > kMaxSamplesPerDir)
+                    return fail(IGA_EUNSUPPORTED, "more than %d samples per direction", kMaxSamplesPerDir);
+                sp.r0[d] = k0;
+                sp.r1[d] = k1[d];
+                sp.Lmax[d] = 0;
+                for (int v = 0; v < W; ++v) {
+                    const int dd = v - p;
+                    // domain of the offset component dd: Omega~_delta (Sec. 3.2) or Omega~
+                    const int lo = per_offset ? k0 + std::max(0, -dd) : k0;
+                    const int hi = per_offset ? k1[d] - std::max(0, dd) : k1[d];
+                    if (hi < lo) { sp.L[d][v] = 0; sp.ns[d][v] = 0; sp.k0[d][v] = lo; continue; }
+                    sp.k0[d][v] = lo;
+                    sp.L[d][v] = hi - lo + 1;
+                    int ns = 0;
+                    for (int a = 0; a < sp.nu[d]; ++a) ns += variant_sample(sp.ax[d], sp.all, axis_sample(sp.ax[d], a), lo, hi);
+                    sp.ns[d][v] = ns;
+                    sp.qe[d][v] = std::min(q, ns - 1);
+                    sp.Lmax[d] = std::max(sp.Lmax[d], sp.L[d][v]);
+                }
             }
-            for (int d = dim; d < 3; ++d) { bs.ns[d] = 1; sp.ns[d] = 1; sp.L[d] = 1; }
-            bs.M = M;
             sp.n_samples = 1;
-            for (int d = 0; d < dim; ++d) sp.n_samples *= sp.ns[d];
+            for (int d = 0; d < dim; ++d) sp.n_samples *= sp.nu[d];
+            for (int d = 0; d < 3; ++d) bs.ax[d] = sp.ax[d];
             bs.n_samples = sp.n_samples;
             do_spline = true;
             // frame = rows with an index outside [k0, k1], as disjoint slabs
             Box b;
-            const int full = 0;
-            (void)full;
             if (dim == 3) {
                 int lo[3], R[3];
                 // slabs normal to direction 2
@@ -292,11 +351,14 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         }
         bs.box[k] = b;
     }
-    int64_t o_samples = 0, o_lu[3] = {0, 0, 0}, o_eval[3] = {0, 0, 0}, o_eval0 = 0, o_partial = 0, o_ints = 0;
+    int64_t o_samples = 0, o_lu[3][kMaxV], o_eval[3][kMaxV], o_eval0[kMaxV], o_partial = 0, o_ints = 0, o_mid = 0;
+    int64_t i_espan[3][kMaxV], i_pos[3][kMaxV], i_inv[3][kMaxV];
+    memset(o_lu, 0, sizeof(o_lu)); memset(o_eval, 0, sizeof(o_eval)); memset(o_eval0, 0, sizeof(o_eval0));
+    memset(i_espan, 0, sizeof(i_espan)); memset(i_pos, 0, sizeof(i_pos)); memset(i_inv, 0, sizeof(i_inv));
     if (do_spline) {
-        Box sbx;                         // shape of every sample box
-        int lo[3] = {2 * p, 2 * p, 2 * p}, R[3] = {1, 1, 1};
-        make_box(g, sbx, lo, R);
+        Box sbx;                         // shape of every sample box: one row, p + 1 elements per direction
+        memset(&sbx, 0, sizeof(sbx));
+        for (int d = 0; d < 3; ++d) { sbx.R[d] = 1; sbx.E[d] = (d < dim) ? p + 1 : 1; }
         bs.s_c_len = align_up(box_coef_len(dim, p, sbx), 32);
         bs.s_t1_len = align_up(box_t1_len(dim, p, sbx), 32);
         bs.s_t2_len = align_up(box_t2_len(dim, p, sbx), 32);
@@ -309,15 +371,23 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
             nblk[s] += bs.bper_s[s] * sp.n_samples;
         }
         o_samples = lay.take((int64_t)S * sp.n_samples);
-        for (int d = 0; d < dim; ++d) {
-            o_lu[d] = lay.take((int64_t)sp.ns[d] * sp.ns[d]);
-            o_eval[d] = lay.take((int64_t)sp.L[d] * (sp.qe[d] + 1));
-        }
-        o_eval0 = lay.take((int64_t)sp.L[0] * (sp.qe[0] + 1));
+        int64_t nints = 2 * 3 * kMaxV + 8;
+        for (int d = 0; d < dim; ++d)
+            for (int v = 0; v < W; ++v) {
+                const int64_t L = sp.L[d][v];
+                o_lu[d][v] = lay.take((int64_t)sp.ns[d][v] * sp.ns[d][v]);
+                o_eval[d][v] = lay.take(L * (sp.qe[d][v] + 1));
+                if (d == 0) o_eval0[v] = lay.take(L * (sp.qe[d][v] + 1));
+                i_espan[d][v] = nints;
+                nints += align_up(L + 1, 8);
+                i_pos[d][v] = nints;
+                nints += align_up(sp.ns[d][v] + 1, 8);
+                i_inv[d][v] = nints;
+                nints += align_up(sp.nu[d] + 1, 8);
+            }
         const int64_t S_up = S - 1 - sp.c;
-        o_partial = lay.take(S_up * (dim == 3 ? sp.L[2] : 1) * (int64_t)sp.L[1] * sp.ns[0]);
-        int64_t nints = 8;
-        for (int d = 0; d < dim; ++d) nints += sp.L[d] + 8;
+        o_mid = lay.take(dim == 3 ? S_up * sp.Lmax[2] * (int64_t)sp.nu[1] * sp.nu[0] : 1);
+        o_partial = lay.take(S_up * (dim == 3 ? sp.Lmax[2] : 1) * (int64_t)sp.Lmax[1] * sp.nu[0]);
         o_ints = lay.take(div_up(nints, 2));
     }
     for (int s = 0; s < 4; ++s)
@@ -378,16 +448,18 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     if (do_spline) {
         int* ints = (int*)P(o_ints);
         sb.band = ints;
-        int64_t io = 8;
-        for (int d = 0; d < dim; ++d) {
-            sb.lu[d] = P(o_lu[d]);
-            sb.eval[d] = P(o_eval[d]);
-            sb.espan[d] = ints + io;
-            io += sp.L[d] + 8;
-        }
-        sb.eval0 = reinterpret_cast<float2*>(P(o_eval0));
+        for (int d = 0; d < dim; ++d)
+            for (int v = 0; v < W; ++v) {
+                sb.lu[d][v] = P(o_lu[d][v]);
+                sb.eval[d][v] = P(o_eval[d][v]);
+                sb.espan[d][v] = ints + i_espan[d][v];
+                sb.pos[d][v] = ints + i_pos[d][v];
+                sb.inv[d][v] = ints + i_inv[d][v];
+                if (d == 0) sb.eval0[v] = reinterpret_cast<float2*>(P(o_eval0[v]));
+            }
         sb.partial = reinterpret_cast<float2*>(P(o_partial));
-        if (ce == cudaSuccess) { stage = "spline interpolation"; ce = launch_spline(g, sp, M, samples, sb, st); }
+        sb.mid = P(o_mid);
+        if (ce == cudaSuccess) { stage = "spline interpolation"; ce = launch_spline(g, sp, samples, sb, st); }
     }
     if (surrogate && ce == cudaSuccess) {
         stage = "surrogate fill";
@@ -470,13 +542,19 @@ extern "C" {
 int iga_assemble_exact(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
                        int dtype, void* stream, iga_matrix_t* A)
 {
-    return assemble(patch, p, map, kappa, false, 1, 0, dtype, stream, A);
+    return assemble(patch, p, map, kappa, false, 1, 0, IGA_DOMAINS_COMMON, dtype, stream, A);
 }
 
 int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
                            int M, int q, int dtype, void* stream, iga_matrix_t* A)
 {
-    return assemble(patch, p, map, kappa, true, M, q, dtype, stream, A);
+    return assemble(patch, p, map, kappa, true, M, q, IGA_DOMAINS_COMMON, dtype, stream, A);
+}
+
+int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+                                   int M, int q, int domains, int dtype, void* stream, iga_matrix_t* A)
+{
+    return assemble(patch, p, map, kappa, true, M, q, domains, dtype, stream, A);
 }
 
 int iga_apply(iga_matrix_t A, const void* x, void* y, void* stream)

@@ -41,15 +41,34 @@ struct Box {
 };
 
 constexpr int kMaxBoxes = 7;
+constexpr int kMaxV = 2 * kMaxP + 1;      // offset components delta_d = -p..p
+
+// The sample indices of one direction, in increasing order: a run of n_lo
+// consecutive indices from c0, n_mid lattice points c0 + (j_first + k) M, and a
+// run of n_hi consecutive indices from hi0 (n = n_lo + n_mid + n_hi).
+//   common domain Omega~ = [k0, k1]: no low run, the lattice k0 + jM <= k1, and k1
+//     as a one-index high run when the lattice misses it (Sec. 6);
+//   per-offset domains: the p + 1 first and last cardinal indices as the runs and
+//     the lattice p + jM between them (the ends of every Omega~_delta are samples).
+struct SampleAxis {
+    int c0, M, n_lo, j_first, n_mid, hi0, n_hi, n;
+};
+__host__ __device__ __forceinline__ int axis_sample(const SampleAxis& a, int k)
+{
+    if (k < a.n_lo) return a.c0 + k;
+    k -= a.n_lo;
+    if (k < a.n_mid) return a.c0 + (a.j_first + k) * a.M;
+    return a.hi0 + (k - a.n_mid);
+}
 
 // The boxes of one assembly: a few explicit boxes (the whole patch, or the
 // frame slabs) and an implicit batch of one-row boxes at the sample rows
-// s_d = min(k0_d + a_d M, k1_d), a_d = 0..ns_d-1 (sample id a_0 + ns_0 (a_1 + ns_1 a_2)).
+// s_d = axis_sample(ax_d, a_d), a_d = 0..n_d-1 (sample id a_0 + n_0 (a_1 + n_1 a_2)).
 struct BoxSet {
     int nb;
     Box box[kMaxBoxes];
     int64_t n_samples;
-    int ns[3], k0[3], k1[3], M;
+    SampleAxis ax[3];
     int64_t s_c_off, s_t1_off, s_t2_off;      // scratch offsets of sample box 0
     int64_t s_c_len, s_t1_len, s_t2_len;      // scratch per sample box
     int64_t blk_s[4];                         // first block of the batch in launch k
@@ -65,10 +84,9 @@ __device__ __forceinline__ void get_box(const BoxSet& bs, int dim, int p, int st
         for (int d = 0; d < 3; ++d) {
             int s = 0;
             if (d < dim) {
-                const int a = (int)(rem % bs.ns[d]);
-                rem /= bs.ns[d];
-                s = bs.k0[d] + a * bs.M;
-                if (s > bs.k1[d]) s = bs.k1[d];
+                const int a = (int)(rem % bs.ax[d].n);
+                rem /= bs.ax[d].n;
+                s = axis_sample(bs.ax[d], a);
             }
             b.rlo[d] = s;
             b.R[d] = 1;
@@ -130,22 +148,49 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
                           double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
 
+// Whether the sample index t of a direction is a sample of the variant with
+// domain [k0, k1]: every sample in the domain (all != 0, the common domain),
+// else the ends and the lattice points c0 + jM at least M/2 away from both
+// ends (per-offset domains; the knot spacing then stays within [M/2, 3M/2]).
+__host__ __device__ __forceinline__ bool variant_sample(const SampleAxis& ax, int all, int t, int k0, int k1)
+{
+    if (t < k0 || t > k1) return false;
+    if (all || t == k0 || t == k1) return true;
+    if ((t - ax.c0) % ax.M) return false;
+    return 2 * (t - k0) >= ax.M && 2 * (k1 - t) >= ax.M;
+}
+
+// Interpolation plan.  Every offset delta interpolates, in each direction d,
+// over the domain [k0, k0 + L - 1] of its component delta_d (variant v = delta_d + p)
+// through ns of the direction's samples (variant_sample).  With the common
+// domain Omega~ all variants coincide; with per-offset domains they are the
+// Omega~_delta of Sec. 3.2.  A variant with L = 0 has no domain.
+constexpr int kMaxSamplesPerDir = 2048;
 struct SplinePlan {
-    int dim, q, k0[3], L[3], ns[3], qe[3];
-    int64_t n_samples;        // prod ns
-    int S, c;                 // slots and centre slot
+    int dim, q, S, c, nv;     // nv = 2p + 1 variants per direction
+    int all;                  // every variant uses every sample (common domain)
+    int64_t n_samples;        // prod nu
+    SampleAxis ax[3];
+    int nu[3];                // samples per direction (= ax[d].n)
+    int r0[3], r1[3];         // rows with interpolated entries: r0 <= i_d <= r1 in every direction
+    int k0[3][kMaxV], L[3][kMaxV], ns[3][kMaxV], qe[3][kMaxV];
+    int Lmax[3];              // max over variants of L
 };
-// K4: collocation LU per direction, coefficient solves in place in the upper
-// slots of the sample table, evaluation tables and the partially evaluated field.
+// K4: collocation LU per direction and variant, coefficient solves in place in
+// the upper slots of the sample table, evaluation tables and the partially
+// evaluated field.
 struct SplineBufs {
-    double* lu[3];            // [ns][ns] LU factors (unit lower L below the diagonal)
-    int* band;                // [3][2] lower / upper bandwidth of the factors
-    int* espan[3];            // [L] first nonzero interpolation basis index at box index k0 + k
-    double* eval[3];          // [L][q+1] its values
-    float2* eval0;            // direction 0 values again, double-float pairs, transposed [q+1][L]
-    float2* partial;          // double-float; 3-D [S_up][L2][L1][ns0]; 2-D [S_up][L1][ns0]
+    int* pos[3][kMaxV];       // [ns] sample positions (axis_sample index) of the variant
+    int* inv[3][kMaxV];       // [nu] index into pos of each sample position, or -1
+    double* lu[3][kMaxV];     // [ns][ns] LU factors (unit lower L below the diagonal)
+    int* band;                // [3][kMaxV][2] lower / upper bandwidth of the factors
+    int* espan[3][kMaxV];     // [L] first nonzero basis index (into pos) at domain index k0 + k
+    double* eval[3][kMaxV];   // [L][q+1] its values
+    float2* eval0[kMaxV];     // direction 0 values again, double-float pairs, transposed [q+1][L]
+    float2* partial;          // double-float; 3-D [S_up][Lmax2][Lmax1][nu0]; 2-D [S_up][Lmax1][nu0]
+    double* mid;              // 3-D: direction-2 partial sums [S_up][Lmax2][nu1][nu0]
 };
-cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* samples /* [S][n_samples] */,
+cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, double* samples /* [S][n_samples] */,
                           const SplineBufs& sb, cudaStream_t s);
 cudaError_t launch_fill(const Geo& g, const SplinePlan& sp, int empty_box, const SplineBufs& sb,
                         void* ell, int ell_f32, cudaStream_t s);

@@ -1,12 +1,13 @@
 // K4: per-offset tensor-product B-spline interpolation of the stencil
 //     functions through their samples (Sec. 4.1, Sec. 6).
 // K5: surrogate rows of eq. DefinitionOfSurrogateMatrixSymmetricKernel
-//     (Sec. 5.3) written into the stencil-ELL values (pass 1, rows of
-//     Omega~), then the kernel-preserving diagonal of every row (pass 2).
+//     (Sec. 5.3) written into the stencil-ELL values (pass 1, rows with
+//     interpolated entries), then the kernel-preserving diagonal of every row
+//     (pass 2).
 //
-// Interpolation reading: abscissae are the sample indices t_a = min(k0 + a M, k1);
-// the knot vector of degree q has (q+1)-fold end knots at t_0 and t_{ns-1}
-// and interior knots at t_{(q+1)/2} .. t_{ns-1-(q+1)/2} (odd q) or at the
+// Each offset delta interpolates, per direction d, through the samples of the
+// variant v = delta_d + p (SplinePlan, variant_sample): abscissae t_a, a = 0..ns-1.  The knot vector of degree q has (q+1)-fold end knots at t_0 and
+// t_{ns-1} and interior knots at t_{(q+1)/2} .. t_{ns-1-(q+1)/2} (odd q) or at the
 // midpoints (t_r + t_{r+1})/2, r = q/2 .. ns-2-q/2 (even q) -- the not-a-knot
 // interpolating spline.  Spans are half-open [kn_mu, kn_mu+1) except the last.
 // The collocation matrix is totally positive and banded, so it is factored
@@ -15,12 +16,6 @@
 #include "iga_internal.cuh"
 
 namespace iga {
-
-__device__ __forceinline__ double sample_pos(int a, int k0, int k1, int M)
-{
-    int s = k0 + a * M;
-    return (double)(s > k1 ? k1 : s);
-}
 
 __device__ int find_span(const double* kn, int ns, int q, double x)
 {
@@ -52,33 +47,59 @@ __device__ void spline_basis(const double* kn, int mu, int q, double x, double* 
     }
 }
 
-// One block per direction: knots, collocation matrix, banded LU, evaluation tables.
-__global__ void k_spline_setup(SplinePlan sp, int M, SplineBufs sb)
+// variant (v_0, v_1, v_2) of upper slot u: v_d = delta_d + p of slot c + 1 + u
+__device__ __forceinline__ void slot_variants(const SplinePlan& sp, int64_t u, int v[3])
 {
-    extern __shared__ double kn[];
+    const int W = sp.nv;
+    int s = sp.c + 1 + (int)u;
+    for (int d = 0; d < 3; ++d) {
+        v[d] = (d < sp.dim) ? s % W : 0;
+        s /= W;
+    }
+}
+
+// One block per (variant, direction): sample list, knots, collocation matrix,
+// banded LU, evaluation tables.
+__global__ void k_spline_setup(SplinePlan sp, SplineBufs sb)
+{
+    extern __shared__ double smem[];
     __shared__ int sbl, sbu;
-    const int d = blockIdx.x;
-    const int ns = sp.ns[d], q = sp.qe[d], k0 = sp.k0[d], L = sp.L[d];
-    const int k1 = k0 + L - 1;
+    const int v = blockIdx.x, d = blockIdx.y;
+    const int ns = sp.ns[d][v], q = sp.qe[d][v], k0 = sp.k0[d][v], L = sp.L[d][v];
+    if (L <= 0 || ns <= 0) return;
+    const SampleAxis ax = sp.ax[d];
+    const int nu = sp.nu[d];
+    double* ts = smem;               // [ns] abscissae
+    double* kn = smem + ns;          // [ns + q + 1] knots
     const int nk = ns + q + 1;
-    if (threadIdx.x == 0) { sbl = 0; sbu = 0; }
+    if (threadIdx.x == 0) {
+        sbl = 0; sbu = 0;
+        int r = 0;
+        for (int a = 0; a < nu; ++a) {
+            const int t = axis_sample(ax, a);
+            const bool in = variant_sample(ax, sp.all, t, k0, k0 + L - 1) && r < ns;
+            sb.inv[d][v][a] = in ? r : -1;
+            if (in) { sb.pos[d][v][r] = a; ts[r] = (double)t; ++r; }
+        }
+    }
+    __syncthreads();
     for (int r = threadIdx.x; r < nk; r += blockDim.x) {
-        double v;
-        if (r <= q) v = sample_pos(0, k0, k1, M);
-        else if (r >= ns) v = sample_pos(ns - 1, k0, k1, M);
-        else if (q & 1) v = sample_pos((q + 1) / 2 + (r - q - 1), k0, k1, M);
+        double x;
+        if (r <= q) x = ts[0];
+        else if (r >= ns) x = ts[ns - 1];
+        else if (q & 1) x = ts[(q + 1) / 2 + (r - q - 1)];
         else {
             const int a = q / 2 + (r - q - 1);
-            v = 0.5 * (sample_pos(a, k0, k1, M) + sample_pos(a + 1, k0, k1, M));
+            x = 0.5 * (ts[a] + ts[a + 1]);
         }
-        kn[r] = v;
+        kn[r] = x;
     }
-    double* B = sb.lu[d];
+    double* B = sb.lu[d][v];
     for (int64_t k = threadIdx.x; k < (int64_t)ns * ns; k += blockDim.x) B[k] = 0.0;
     __syncthreads();
     // collocation rows: B[r][c] = N_c(t_r)
     for (int r = threadIdx.x; r < ns; r += blockDim.x) {
-        const double x = sample_pos(r, k0, k1, M);
+        const double x = ts[r];
         const int mu = find_span(kn, ns, q, x);
         double N[kMaxQ + 1];
         spline_basis(kn, mu, q, x, N);
@@ -99,116 +120,168 @@ __global__ void k_spline_setup(SplinePlan sp, int M, SplineBufs sb)
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { sb.band[2 * d] = bl; sb.band[2 * d + 1] = bu; }
-    // evaluation at every box index k0 + k
+    if (threadIdx.x == 0) {
+        sb.band[2 * (d * kMaxV + v)] = bl;
+        sb.band[2 * (d * kMaxV + v) + 1] = bu;
+    }
+    // evaluation at every domain index k0 + k
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const double x = (double)(k0 + k);
         const int mu = find_span(kn, ns, q, x);
         double N[kMaxQ + 1];
         spline_basis(kn, mu, q, x, N);
-        sb.espan[d][k] = mu - q;
+        sb.espan[d][v][k] = mu - q;
         for (int a = 0; a <= q; ++a) {
-            sb.eval[d][(int64_t)k * (q + 1) + a] = N[a];
-            if (d == 0) sb.eval0[(int64_t)a * L + k] = PolDF::from_double(N[a]);
+            sb.eval[d][v][(int64_t)k * (q + 1) + a] = N[a];
+            if (d == 0) sb.eval0[v][(int64_t)a * L + k] = PolDF::from_double(N[a]);
         }
     }
 }
 
-// Solve the collocation system along direction d for every upper offset and line,
-// in place in the sample table rows c+1 .. S-1.
+// Solve the collocation system along direction d for every upper offset and every
+// line of its sample grid, in place in the sample table rows c+1 .. S-1.  Thread
+// per (offset, line of the full sample grid); lines through positions that are
+// not samples of the offset return.
 __global__ void k_spline_solve(SplinePlan sp, int d, SplineBufs sb, double* samples)
 {
-    const int ns = sp.ns[d];
-    const int64_t lines = sp.n_samples / ns;
+    const int64_t lines = sp.n_samples / sp.nu[d];
     const int64_t S_up = sp.S - 1 - sp.c;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= S_up * lines) return;
-    const int64_t u = idx / lines, l = idx % lines;
-    int64_t st = 1;
-    for (int e = 0; e < d; ++e) st *= sp.ns[e];
-    const int64_t base = (l % st) + (l / st) * st * ns;
-    double* v = samples + (sp.c + 1 + u) * sp.n_samples + base;
-    const double* B = sb.lu[d];
-    const int bl = sb.band[2 * d], bu = sb.band[2 * d + 1];
+    const int64_t u = idx / lines;
+    int64_t l = idx % lines;
+    int v[3];
+    slot_variants(sp, u, v);
+    int64_t base = 0, st = 1, std_ = 1;
+    for (int e = 0; e < sp.dim; ++e) {
+        if (e == d) { std_ = st; st *= sp.nu[e]; continue; }
+        const int pos = (int)(l % sp.nu[e]);
+        l /= sp.nu[e];
+        if (sp.ns[e][v[e]] <= 0 || sb.inv[e][v[e]][pos] < 0) return;
+        base += pos * st;
+        st *= sp.nu[e];
+    }
+    const int ns = sp.ns[d][v[d]];
+    if (ns <= 0) return;
+    double* x = samples + (sp.c + 1 + u) * sp.n_samples + base;
+    const int* ps = sb.pos[d][v[d]];
+    const double* B = sb.lu[d][v[d]];
+    const int bl = sb.band[2 * (d * kMaxV + v[d])], bu = sb.band[2 * (d * kMaxV + v[d]) + 1];
     for (int r = 1; r < ns; ++r) {
-        double acc = v[r * st];
-        for (int c = max(0, r - bl); c < r; ++c) acc -= B[(int64_t)r * ns + c] * v[c * st];
-        v[r * st] = acc;
+        double acc = x[ps[r] * std_];
+        for (int c = max(0, r - bl); c < r; ++c) acc -= B[(int64_t)r * ns + c] * x[ps[c] * std_];
+        x[ps[r] * std_] = acc;
     }
     for (int r = ns - 1; r >= 0; --r) {
-        double acc = v[r * st];
-        for (int c = r + 1; c < min(ns, r + bu + 1); ++c) acc -= B[(int64_t)r * ns + c] * v[c * st];
-        v[r * st] = acc / B[(int64_t)r * ns + r];
+        double acc = x[ps[r] * std_];
+        for (int c = r + 1; c < min(ns, r + bu + 1); ++c) acc -= B[(int64_t)r * ns + c] * x[ps[c] * std_];
+        x[ps[r] * std_] = acc / B[(int64_t)r * ns + r];
     }
 }
 
 // Partially evaluated coefficients: contract directions 2 (3-D) and 1 at every
-// box index, keeping the coefficient index a0 of direction 0:
+// domain index, keeping the coefficient index a0 of direction 0 (all indices
+// relative to the offset's own samples and domain):
 //   3-D: partial[u][j2][j1][a0] = sum_{b,c} coef[u][a0, s1(j1)+b, s2(j2)+c] E1[j1][b] E2[j2][c]
 //   2-D: partial[u][j1][a0]     = sum_b     coef[u][a0, s1(j1)+b]          E1[j1][b]
-__global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* samples)
+// Sum-factorised: first direction 2 into mid[u][j2][b'][a0] (3-D only), then direction 1.
+__global__ void k_spline_mid(SplinePlan sp, SplineBufs sb, const double* samples, double* mid)
 {
-    const int n0 = sp.ns[0], n1 = sp.ns[1];
-    const int L1 = sp.L[1], L2 = (sp.dim == 3) ? sp.L[2] : 1;
+    const int nu0 = sp.nu[0], nu1 = sp.nu[1], L2 = sp.Lmax[2];
     const int64_t S_up = sp.S - 1 - sp.c;
-    const int64_t total = S_up * L2 * L1 * n0;
+    const int64_t total = S_up * L2 * nu1 * nu0;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int a0 = (int)(idx % n0);
-    const int j1 = (int)((idx / n0) % L1);
-    const int j2 = (int)((idx / ((int64_t)n0 * L1)) % L2);
-    const int64_t u = idx / ((int64_t)n0 * L1 * L2);
+    const int a0 = (int)(idx % nu0);
+    const int b1 = (int)((idx / nu0) % nu1);
+    const int j2 = (int)((idx / ((int64_t)nu0 * nu1)) % L2);
+    const int64_t u = idx / ((int64_t)nu0 * nu1 * L2);
+    int v[3];
+    slot_variants(sp, u, v);
+    if (a0 >= sp.ns[0][v[0]] || b1 >= sp.ns[1][v[1]] || j2 >= sp.L[2][v[2]]) return;
     const double* coef = samples + (sp.c + 1 + u) * sp.n_samples;
-    const int q1 = sp.qe[1];
-    const int s1 = sb.espan[1][j1];
-    const double* E1 = sb.eval[1] + (int64_t)j1 * (q1 + 1);
+    const int q2 = sp.qe[2][v[2]];
+    const int s2 = sb.espan[2][v[2]][j2];
+    const int* p2 = sb.pos[2][v[2]];
+    const double* E2 = sb.eval[2][v[2]] + (int64_t)j2 * (q2 + 1);
+    const int64_t o01 = sb.pos[0][v[0]][a0] + (int64_t)nu0 * sb.pos[1][v[1]][b1];
+    const int64_t plane = (int64_t)nu0 * nu1;
+    double acc = 0.0;
+    for (int c = 0; c <= q2; ++c) acc += coef[o01 + plane * p2[s2 + c]] * E2[c];
+    mid[idx] = acc;
+}
+
+__global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* samples, const double* mid)
+{
+    const int nu0 = sp.nu[0], nu1 = sp.nu[1];
+    const int L1 = sp.Lmax[1], L2 = (sp.dim == 3) ? sp.Lmax[2] : 1;
+    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t total = S_up * L2 * L1 * nu0;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int a0 = (int)(idx % nu0);
+    const int j1 = (int)((idx / nu0) % L1);
+    const int j2 = (int)((idx / ((int64_t)nu0 * L1)) % L2);
+    const int64_t u = idx / ((int64_t)nu0 * L1 * L2);
+    int v[3];
+    slot_variants(sp, u, v);
+    if (a0 >= sp.ns[0][v[0]] || j1 >= sp.L[1][v[1]] || (sp.dim == 3 && j2 >= sp.L[2][v[2]])) return;
+    const int q1 = sp.qe[1][v[1]];
+    const int s1 = sb.espan[1][v[1]][j1];
+    const double* E1 = sb.eval[1][v[1]] + (int64_t)j1 * (q1 + 1);
     double acc = 0.0;
     if (sp.dim == 3) {
-        const int q2 = sp.qe[2];
-        const int s2 = sb.espan[2][j2];
-        const double* E2 = sb.eval[2] + (int64_t)j2 * (q2 + 1);
-        for (int c = 0; c <= q2; ++c) {
-            double inner = 0.0;
-            for (int b = 0; b <= q1; ++b)
-                inner += coef[a0 + (int64_t)n0 * ((s1 + b) + (int64_t)n1 * (s2 + c))] * E1[b];
-            acc += inner * E2[c];
-        }
+        // mid[u][j2][b'][a0], b' relative to the offset's first sample of direction 1
+        const double* src = mid + ((u * L2 + j2) * (int64_t)nu1) * nu0 + a0;
+        for (int b = 0; b <= q1; ++b) acc += src[(int64_t)nu0 * (s1 + b)] * E1[b];
     } else {
-        for (int b = 0; b <= q1; ++b) acc += coef[a0 + (int64_t)n0 * (s1 + b)] * E1[b];
+        const double* src = samples + (sp.c + 1 + u) * sp.n_samples + sb.pos[0][v[0]][a0];
+        const int* p1 = sb.pos[1][v[1]];
+        for (int b = 0; b <= q1; ++b) acc += src[(int64_t)nu0 * p1[s1 + b]] * E1[b];
     }
     sb.partial[idx] = PolDF::from_double(acc);
 }
 
-cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, int M, double* samples,
+cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, double* samples,
                           const SplineBufs& sb, cudaStream_t s)
 {
-    int nsmax = 0;
-    for (int d = 0; d < sp.dim; ++d) nsmax = max(nsmax, sp.ns[d] + sp.qe[d] + 1);
+    (void)g;
+    int nkmax = 0;
+    for (int d = 0; d < sp.dim; ++d)
+        for (int v = 0; v < sp.nv; ++v) nkmax = max(nkmax, 2 * sp.ns[d][v] + sp.qe[d][v] + 1);
     launch_begin(K_SPLINE_SETUP, s);
-    k_spline_setup<<<sp.dim, 256, (size_t)nsmax * sizeof(double), s>>>(sp, M, sb);
+    k_spline_setup<<<dim3(sp.nv, sp.dim), 256, (size_t)nkmax * sizeof(double), s>>>(sp, sb);
     launch_end(K_SPLINE_SETUP, s);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int64_t S_up = sp.S - 1 - sp.c;
     for (int d = 0; d < sp.dim; ++d) {
-        const int64_t n = S_up * (sp.n_samples / sp.ns[d]);
+        const int64_t n = S_up * (sp.n_samples / sp.nu[d]);
         launch_begin(K_SPLINE_SOLVE, s);
         k_spline_solve<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sp, d, sb, samples);
         launch_end(K_SPLINE_SOLVE, s);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    const int64_t total = S_up * (sp.dim == 3 ? sp.L[2] : 1) * (int64_t)sp.L[1] * sp.ns[0];
+    if (sp.dim == 3) {
+        const int64_t nmid = S_up * sp.Lmax[2] * (int64_t)sp.nu[1] * sp.nu[0];
+        launch_begin(K_SPLINE_PARTIAL, s);
+        k_spline_mid<<<(unsigned)((nmid + kBlock - 1) / kBlock), kBlock, 0, s>>>(sp, sb, samples, sb.mid);
+        launch_end(K_SPLINE_PARTIAL, s);
+    }
+    const int64_t total = S_up * (sp.dim == 3 ? sp.Lmax[2] : 1) * (int64_t)sp.Lmax[1] * sp.nu[0];
     launch_begin(K_SPLINE_PARTIAL, s);
-    k_spline_partial<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(sp, sb, samples);
+    k_spline_partial<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(sp, sb, samples, sb.mid);
     launch_end(K_SPLINE_PARTIAL, s);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// K5, rows of Omega~: for each slot with column j = i + delta,
-//      j in Omega~, j > i : Phi~_delta(x~_i)                      (interpolated)
-//      j in Omega~, j < i : Phi~_{-delta}(x~_j)  (= A~_ji, the copied entry)
-//      j outside Omega~   : A_ji from the exact frame row j (= A_ij)
+// K5, rows of the region R = [r0, r1]^n of rows with interpolated entries (the
+// box Omega~, or the cardinal box with per-offset domains): for each slot with
+// column j = i + delta,
+//      j in R, j > i : Phi~_delta(x~_i)                      (interpolated)
+//      j in R, j < i : Phi~_{-delta}(x~_j)  (= A~_ji, the copied entry)
+//      j outside R   : A_ji from the exact frame row j (= A_ij)
 // then, for every row, diagonal := -(off-diagonal sum).
 // The interpolant is evaluated in double-float arithmetic on the FP32 pipe
 // (about 48 significand bits); the diagonal sums are FP64.
@@ -218,7 +291,7 @@ __device__ __forceinline__ T from_df(const DFAcc& a) { return PolDF::to_double(a
 template <>
 __device__ __forceinline__ float from_df<float>(const DFAcc& a) { return __fadd_rn(a.h, a.l); }
 
-// Pass 1 (rows of Omega~ only): one thread per (row, delta_1, delta_2) writes the
+// Pass 1 (rows of R only): one thread per (row, delta_1, delta_2) writes the
 // 2p+1 slots delta_0 = -p..p of that row.
 template <int P, int DIM, typename T>
 __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, SplineBufs sb, T* vals)
@@ -227,45 +300,52 @@ __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, SplineBuf
     constexpr int S = (DIM == 3) ? W * W * W : W * W;
     constexpr int C = (S - 1) / 2;
     constexpr int NPAIR = (DIM == 3) ? W * W : W;
-    const int L0 = sp.L[0], L1 = sp.L[1], L2 = (DIM == 3) ? sp.L[2] : 1;
+    const int R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
+    const int R2 = (DIM == 3) ? sp.r1[2] - sp.r0[2] + 1 : 1;
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)L0 * L1 * L2 * NPAIR;
+    const int64_t total = (int64_t)R0 * R1 * R2 * NPAIR;
     if (item >= total) return;
-    const int e0i = (int)(item % L0);
-    int64_t rest = item / L0;
+    const int e0i = (int)(item % R0);
+    int64_t rest = item / R0;
     const int pr = (int)(rest % NPAIR);
     rest /= NPAIR;
-    const int e1i = (int)(rest % L1);
-    const int e2i = (int)(rest / L1);
-    const int d1 = pr % W, d2 = (DIM == 3) ? pr / W : 0;
+    const int e1i = (int)(rest % R1);
+    const int e2i = (int)(rest / R1);
+    const int d1 = pr % W, d2 = (DIM == 3) ? pr / W : P;
     const int m0 = g.m[0], m1 = g.m[1];
     const int64_t N = (int64_t)m0 * m1 * ((DIM == 3) ? g.m[2] : 1);
-    const int kk0 = sp.k0[0], kk1 = sp.k0[1], kk2 = (DIM == 3) ? sp.k0[2] : 0;
-    const int i0 = kk0 + e0i, i1 = kk1 + e1i, i2 = kk2 + e2i;
+    const int i0 = sp.r0[0] + e0i, i1 = sp.r0[1] + e1i, i2 = (DIM == 3) ? sp.r0[2] + e2i : 0;
     const int64_t i = i0 + (int64_t)m0 * (i1 + (int64_t)m1 * i2);
     const int dl1 = d1 - P, dl2 = (DIM == 3) ? d2 - P : 0;
-    const int l1 = e1i + dl1, l2 = e2i + dl2;
-    const bool in12 = (l1 >= 0 && l1 < L1) && (l2 >= 0 && l2 < L2);
-    const int n0 = sp.ns[0], q0 = sp.qe[0];
-    const int sbase = W * (d1 + W * d2);
+    const int j1 = i1 + dl1, j2 = i2 + dl2;
+    const bool in12 = (j1 >= sp.r0[1] && j1 <= sp.r1[1]) && (DIM == 2 || (j2 >= sp.r0[2] && j2 <= sp.r1[2]));
+    const int L2x = (DIM == 3) ? sp.Lmax[2] : 1, L1x = sp.Lmax[1], nu0 = sp.nu[0];
+    // domain indices in directions 1, 2 of the upper evaluation (at i, variants d1, d2)
+    // and of the lower one (at j, variants 2P - d1, 2P - d2)
+    const int up1 = i1 - sp.k0[1][d1], up2 = (DIM == 3) ? i2 - sp.k0[2][d2] : 0;
+    const int lo1 = j1 - sp.k0[1][2 * P - d1], lo2 = (DIM == 3) ? j2 - sp.k0[2][2 * P - d2] : 0;
+    const int sbase = W * (d1 + W * ((DIM == 3) ? d2 : 0));
 #pragma unroll
     for (int d0 = 0; d0 < W; ++d0) {
         const int s = sbase + d0;
         if (s == C) continue;
-        const int l0 = e0i + d0 - P;
+        const int j0 = i0 + d0 - P;
         T out;
-        if (in12 && l0 >= 0 && l0 < L0) {
+        if (in12 && j0 >= sp.r0[0] && j0 <= sp.r1[0]) {
             // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
             const bool upper = s > C;
             const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
-            const int e0 = upper ? e0i : l0, e1 = upper ? e1i : l1, e2 = upper ? e2i : l2;
-            const float2* Pp = sb.partial + (((int64_t)u * L2 + e2) * L1 + e1) * n0 + sb.espan[0][e0];
-            const float2* E = sb.eval0 + e0;
-            DFAcc v = PolDF::zero();
-            for (int k = 0; k <= q0; ++k) PolDF::mac(v, E[(int64_t)k * L0], Pp[k]);
-            out = from_df<T>(v);
+            const int v0 = upper ? d0 : 2 * P - d0;
+            const int x0 = (upper ? i0 : j0) - sp.k0[0][v0];
+            const int x1 = upper ? up1 : lo1, x2 = upper ? up2 : lo2;
+            const float2* Pp = sb.partial + (((int64_t)u * L2x + x2) * L1x + x1) * nu0 + sb.espan[0][v0][x0];
+            const float2* E = sb.eval0[v0] + x0;
+            const int L0v = sp.L[0][v0];
+            DFAcc acc = PolDF::zero();
+            for (int k = 0; k <= sp.qe[0][v0]; ++k) PolDF::mac(acc, E[(int64_t)k * L0v], Pp[k]);
+            out = from_df<T>(acc);
         } else {
-            const int64_t jrow = (i0 + d0 - P) + (int64_t)m0 * ((i1 + dl1) + (int64_t)m1 * (i2 + dl2));
+            const int64_t jrow = j0 + (int64_t)m0 * (j1 + (int64_t)m1 * j2);
             out = vals[(int64_t)(S - 1 - s) * N + jrow];
         }
         vals[(int64_t)s * N + i] = out;
@@ -300,7 +380,8 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
     const int64_t N = (int64_t)g.m[0] * g.m[1] * (g.dim == 3 ? g.m[2] : 1);
     const unsigned gdiag = (unsigned)((N + kBlock - 1) / kBlock);
     if (!empty_box) {
-        const int64_t total = (int64_t)sp.L[0] * sp.L[1] * (g.dim == 3 ? (int64_t)sp.L[2] * W * W : W);
+        const int64_t R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
+        const int64_t total = R0 * R1 * (g.dim == 3 ? (int64_t)(sp.r1[2] - sp.r0[2] + 1) * W * W : W);
         const unsigned gfill = (unsigned)((total + kBlock - 1) / kBlock);
         launch_begin(K_FILL, s);
         if (g.dim == 3) {

@@ -291,3 +291,32 @@ def test_cg_fp32_iterative_refinement(iga):
     assert rel_res <= 1e-11
     uref, _, _ = oracle.cg(v32.astype(np.float64), prob, f, tol=1e-13)
     assert np.abs(u.cpu().numpy() - uref).max() <= 1e-8 * np.abs(uref).max()
+
+
+EDGE = [
+    # minimum mesh: n_el = p + 1 (m = 2p + 1), Omega~ empty -> every row exact
+    (W.Problem(dim=2, p=3, n_el=(4, 4), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0,
+               kappa_b=0.5), 2, 3),
+    (W.Problem(dim=3, p=2, n_el=(3, 3, 3), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5), 2, 3),
+    # Omega~ a single index per direction (L = 1): one sample, degree lowered to 0
+    (W.Problem(dim=2, p=2, n_el=(7, 7), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0,
+               kappa_b=0.5), 4, 3),
+    # strongly anisotropic meshes
+    (W.Problem(dim=3, p=2, n_el=(30, 7, 9), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5), 5, 2),
+    (W.Problem(dim=2, p=4, n_el=(120, 17), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0,
+               kappa_b=0.5), 7, 5),
+    # constant and polynomial coefficients on affine geometry
+    (W.Problem(dim=3, p=3, n_el=(15, 14, 13), map_kind="affine",
+               affine=(1.2, 0.1, 0.0, -0.1, 0.9, 0.2, 0.05, 0.0, 1.1, 0.0, 0.0, 0.0), kappa_kind="poly", kappa_deg=1,
+               kappa_poly=tuple([1.0, 0.3, 0.2, 0.1, 0.25, 0.0, 0.05, 0.1])), 3, 1),
+]
+
+
+@pytest.mark.parametrize("prob,M,q", EDGE, ids=lambda x: f"{x.dim}d_p{x.p}_{'x'.join(map(str, x.n_el))}"
+                         if hasattr(x, "dim") else str(x))
+def test_surrogate_edge_cases(iga, prob, M, q):
+    ref = oracle.surrogate_matrix(prob, M, q)
+    got = gpu_surr(iga, prob, M, q)
+    assert rel(got, ref) <= TOL64
+    ex = gpu_exact(iga, prob)
+    assert rel(ex, oracle.exact_matrix(prob)) <= TOL64

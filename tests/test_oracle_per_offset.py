@@ -85,16 +85,59 @@ def test_domain_holds_the_translation_invariant_entries(dim, p):
 
 
 def test_sample_examples():
-    """Lattice p + aM inside Omega~_delta plus its two ends (Sec. 6 per offset)."""
-    # p = 2, m = 20: cardinal [2, 17]
+    """Ends of Omega~_delta plus lattice points p + aM at least M/2 from both ends."""
+    # p = 2, m = 20: cardinal [2, 17], lattice 2, 6, 10, 14
+    assert po.union_samples(2, 20, 4) == [2, 3, 4, 6, 10, 14, 15, 16, 17]
     assert po.offset_samples(2, 20, 4, 0) == [2, 6, 10, 14, 17]
-    assert po.offset_samples(2, 20, 4, 2) == [2, 6, 10, 14, 15]
+    assert po.offset_samples(2, 20, 4, 2) == [2, 6, 10, 15]
     assert po.offset_samples(2, 20, 4, -1) == [3, 6, 10, 14, 17]
     assert po.offset_samples(2, 20, 4, -2) == [4, 6, 10, 14, 17]
     assert po.offset_samples(2, 20, 1, 1) == list(range(2, 17))
+    # p = 3, m = 67, M = 8: cardinal [3, 63]
+    assert po.union_samples(3, 67, 8) == [3, 4, 5, 6, 11, 19, 27, 35, 43, 51, 59, 60, 61, 62, 63]
+    assert po.offset_samples(3, 67, 8, -3) == [6, 11, 19, 27, 35, 43, 51, 59, 63]
+    assert po.offset_samples(3, 67, 8, 3) == [3, 11, 19, 27, 35, 43, 51, 60]
+    # end runs that meet: every cardinal index is a sample row
+    assert po.union_samples(3, 14, 8) == list(range(3, 11))
     # one cardinal index: offsets other than 0 have no domain
     assert po.offset_samples(2, 5, 4, 0) == [2]
     assert po.offset_samples(2, 5, 4, 1) == []
+
+
+@pytest.mark.parametrize("p,m,M", [(2, 20, 4), (3, 67, 8), (4, 100, 8), (1, 9, 3), (3, 14, 8), (2, 5, 4),
+                                   (5, 45, 6), (2, 34, 40), (4, 100, 3)])
+def test_offset_samples_are_quasi_uniform_and_shared(p, m, M):
+    """Each domain's ends are samples, spacing stays within [min(M, L)/2, 3M/2], and
+    every sample is one of the shared sample rows."""
+    union = set(po.union_samples(p, m, M))
+    for dd in range(-p, p + 1):
+        k0, k1 = po.offset_domain(p, m, dd)
+        if k1 < k0:
+            continue
+        t = po.offset_samples(p, m, M, dd)
+        assert t[0] == k0 and t[-1] == k1
+        assert set(t) <= union
+        gaps = np.diff(t)
+        if len(gaps):
+            assert gaps.max() <= 1.5 * M
+            assert gaps.min() >= min(M, k1 - k0) / 2 or len(gaps) == 1
+
+
+@pytest.mark.parametrize("p,m,M,q", [(5, 45, 6, 7), (3, 67, 8, 3), (4, 100, 8, 3), (2, 34, 40, 3), (3, 67, 8, 5)])
+def test_offset_interpolation_is_well_conditioned(p, m, M, q):
+    """Lebesgue constant of every offset's interpolant stays within a small factor of
+    the common-domain one (quasi-uniform knots, Sec. 4.1)."""
+    def leb(t):
+        t = np.asarray(t, dtype=float)
+        qe = min(q, len(t) - 1)
+        kn = oracle.interp_knots(t, qe)
+        Binv = np.linalg.inv(oracle.bspline_basis(kn, qe, t))
+        E = oracle.bspline_basis(kn, qe, np.arange(t[0], t[-1] + 1))
+        return np.abs(E @ Binv).sum(axis=1).max()
+    k0, k1 = oracle.omega_box(p, m)
+    common = leb(oracle.sample_indices(k0, k1, M))
+    worst = max(leb(po.offset_samples(p, m, M, dd)) for dd in range(-p, p + 1))
+    assert worst <= 3.0 * common + 1.0
 
 
 def test_M1_is_exact():
