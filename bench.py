@@ -136,13 +136,20 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic work model of the quadrature stages (what the kernels execute)
 # ---------------------------------------------------------------------------
-def _boxes(prob, M, surrogate):
+def _union_count(p, m, M):
+    """Sample rows per direction with per-offset domains: the lattice p + aM in the
+    cardinal range [p, m-p-1] and the p + 1 first and last cardinal indices."""
+    c0, c1 = p, m - p - 1
+    return len(set(range(c0, c1 + 1, M)) | set(range(c0, min(c0 + p, c1) + 1)) | set(range(max(c1 - p, c0), c1 + 1)))
+
+
+def _boxes(prob, M, surrogate, domains="common"):
     """Row boxes of the assembly: whole patch (exact) or frame slabs + one-row sample boxes."""
     p, m, dim = prob.p, list(prob.m), prob.dim
     if not surrogate:
         return [[(0, md) for md in m]], 0
-    k0 = 2 * p
-    k1 = [md - 2 * p - 1 for md in m]
+    k0 = p if domains == "per_offset" else 2 * p
+    k1 = [md - k0 - 1 for md in m]
     if any(b < k0 for b in k1):
         return [[(0, md) for md in m]], 0
     boxes = []
@@ -159,11 +166,14 @@ def _boxes(prob, M, surrogate):
                 else:
                     bx.append(full[e])
             boxes.append(bx)
-    ns = [ (b - k0) // M + 1 + (1 if (b - k0) % M else 0) for b in k1]
+    if domains == "per_offset":
+        ns = [_union_count(p, md, M) for md in m]
+    else:
+        ns = [(b - k0) // M + 1 + (1 if (b - k0) % M else 0) for b in k1]
     return boxes, int(np.prod(ns))
 
 
-def stage_fmas(prob, M, surrogate):
+def stage_fmas(prob, M, surrogate, domains="common"):
     """FP64 FMAs executed by stage Z / Y / X (per launch), closed form over the boxes."""
     p, dim = prob.p, prob.dim
     Q, Wd = p + 1, 2 * p + 1
@@ -177,8 +187,8 @@ def stage_fmas(prob, M, surrogate):
         ehi = min(ne - 1, lo + R - 1)
         return (ehi - elo + 1) * Q
 
-    boxes, nsamp = _boxes(prob, M, surrogate)
-    samp_box = [(2 * p, 1)] * dim
+    boxes, nsamp = _boxes(prob, M, surrogate, domains)
+    samp_box = [(2 * p, 1)] * dim           # every sample box: one row, p + 1 elements per direction
     tot = {"stage_z": 0, "stage_y": 0, "stage_x": 0}
     for bx, mult in [(b, 1) for b in boxes] + ([(samp_box, nsamp)] if nsamp else []):
         sv = [sum(nvalid(i, n_el[d]) for i in range(bx[d][0], bx[d][0] + bx[d][1])) for d in range(dim)]
@@ -200,11 +210,11 @@ def stage_fmas(prob, M, surrogate):
 DF64_FLOPS_PER_MAC = 15
 
 
-def kernel_work(prob, wl, arith: str, surrogate=True):
+def kernel_work(prob, wl, arith: str, surrogate=True, domains="common"):
     """Per-launch algorithmic work: flops of the contraction stages in the arithmetic
     they run in, bytes for the SpMV."""
     esz = 8 if wl.dtype == "f64" else 4
-    fm = stage_fmas(prob, wl.M, surrogate)
+    fm = stage_fmas(prob, wl.M, surrogate, domains)
     if arith == "fp64":
         work = {k: {"bound": "alu", "pipe": "fp64", "flops": 2.0 * v} for k, v in fm.items() if v}
     elif arith == "df64":
@@ -260,45 +270,62 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_throughput(wl, rows_budget: int, seed: int):
-    """Oracle surrogate assembly on a bounded sample: the sample-row setup in full plus
-    `rows_budget` seeded random rows, extrapolated to every row."""
-    import oracle
-    prob = wl.problem
-    t0 = time.perf_counter()
-    setup = oracle.surrogate_setup(prob, wl.M, wl.q)
-    t1 = time.perf_counter()
-    rows = W.sample_rows(prob.N, rows_budget, seed=seed)
-    oracle.surrogate_rows(prob, wl.M, wl.q, rows, setup)
-    t2 = time.perf_counter()
-    t_full = (t1 - t0) + (t2 - t1) * prob.N / len(rows)
-    n_setup = int(np.prod([len(s) for s in setup.samples])) if not setup.empty else 0
-    return prob.nnz / t_full, t2 - t0, {
-        "t_setup": t1 - t0, "t_rows": t2 - t1,
-        "cores": oracle.num_threads(),
-        "sample": f"oracle surrogate assembly: all {n_setup} exact sample rows plus {len(rows)} of {prob.N} rows "
-                  f"(seeded uniform, seed {seed}), time extrapolated to all rows",
-    }
+class OracleTimer:
+    """The oracle's surrogate assembly timed on a bounded sample of one workload.
+
+    The setup (exact quadrature of every sample row, the interpolation solves) is
+    timed once in full; each step times `rows` seeded random rows of the
+    surrogate and extrapolates them to all N rows."""
+
+    def __init__(self, wl, domains):
+        import oracle
+        from oracle import per_offset
+        self.wl, self.domains = wl, domains
+        prob = wl.problem
+        t0 = time.perf_counter()
+        if domains == "per_offset":
+            self.setup = per_offset.per_offset_setup(prob, wl.M, wl.q)
+            self.n_setup = int(np.prod([len(u) for u in self.setup.union]))
+            self._rows = lambda rows: per_offset.per_offset_rows(prob, wl.M, wl.q, rows, self.setup)
+        else:
+            self.setup = oracle.surrogate_setup(prob, wl.M, wl.q)
+            self.n_setup = int(np.prod([len(s) for s in self.setup.samples])) if not self.setup.empty else 0
+            self._rows = lambda rows: oracle.surrogate_rows(prob, wl.M, wl.q, rows, self.setup)
+        self.t_setup = time.perf_counter() - t0
+        self.cores = oracle.num_threads()
+
+    def step(self, rows_budget: int, seed: int):
+        prob = self.wl.problem
+        rows = W.sample_rows(prob.N, rows_budget, seed=seed)
+        t0 = time.perf_counter()
+        self._rows(rows)
+        t_rows = time.perf_counter() - t0
+        t_full = self.t_setup + t_rows * prob.N / len(rows)
+        sample = (f"oracle surrogate assembly ({self.domains} domains): all {self.n_setup} exact sample rows "
+                  f"({self.t_setup:.2f} s, timed once) plus {len(rows)} of {prob.N} rows (seeded uniform, seed "
+                  f"{seed}), time extrapolated to all rows")
+        return prob.nnz / t_full, t_rows, sample
 
 
-def cpu_baseline(wl, target_s: float = 15.0):
-    # calibrate the row count so that the sample costs ~target_s seconds of CPU work
-    v, dt, info = oracle_throughput(wl, 64, seed=0)
-    per_row = info["t_rows"] / 64
-    k = int(min(wl.problem.N, max(64, (target_s - info["t_setup"]) / max(per_row, 1e-6))))
-    v, dt, info = oracle_throughput(wl, k, seed=1)
-    out = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
-           "seconds": dt}
-    return out
+def cpu_baseline(wl, domains, target_s: float = 15.0):
+    timer = OracleTimer(wl, domains)
+    # calibrate the row count so that the sampled rows cost about target_s seconds
+    _, t64, _ = timer.step(64, seed=0)
+    k = int(min(wl.problem.N, max(64, (target_s - timer.t_setup) / max(t64 / 64, 1e-6))))
+    v, t_rows, sample = timer.step(k, seed=1)
+    return {"value": v, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample,
+            "seconds": timer.t_setup + t_rows}
 
 
 def run_reference(args, wl):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
+    timer = OracleTimer(wl, args.domains)
     vals = []
+    sample = ""
     for k in range(args.warmup + args.steps):
-        v, dt, info = oracle_throughput(wl, args.ref_rows, seed=k)
+        v, _, sample = timer.step(args.ref_rows, seed=k)
         if k >= args.warmup:
             vals.append(v)
     value = float(np.mean(vals))
@@ -307,18 +334,18 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.problem.nnz / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded); FP64 CPU oracle on the host cores",
-        "config": config_of(wl, world),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                         "sample": info["sample"]},
+        "config": config_of(wl, world, args.domains),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def config_of(wl, world):
+def config_of(wl, world, domains="common"):
     prob = wl.problem
     return {"workload": wl.name, "dim": prob.dim, "p": prob.p, "n_el": list(prob.n_el), "M": wl.M, "q": wl.q,
+            "domains": domains,
             "map": f"{prob.map_kind} amp {prob.map_amp}",
             "kappa": f"{prob.kappa_kind} a {prob.kappa_a} b {prob.kappa_b}",
             "N": prob.N, "nnz": prob.nnz, "slots": prob.S * prob.N, "values": wl.dtype,
@@ -339,7 +366,9 @@ def run_gpu(args, wl):
     iga.load()
     prob = wl.problem
     stream = torch.cuda.current_stream()
-    A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype)
+    primary = args.domains
+    other = "common" if primary == "per_offset" else "per_offset"
+    A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, domains=primary)
     E = iga.assemble_exact(prob, dtype=wl.dtype)
     tdt = A.torch_dtype
     gen = torch.Generator(device="cpu").manual_seed(0)
@@ -347,9 +376,11 @@ def run_gpu(args, wl):
     y = torch.empty_like(x)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)     # 256 MiB > L2
 
-    def step_surr():
-        iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A)
-        A.apply(x, y)
+    def surr_step(mat, domains):
+        def step():
+            iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=mat, domains=domains)
+            mat.apply(x, y)
+        return step
 
     def step_exact():
         iga.assemble_exact(prob, dtype=wl.dtype, out=E)
@@ -394,14 +425,18 @@ def run_gpu(args, wl):
         if rank == 0:
             print(json.dumps({"mode": "exact", "ms_per_step": ms_e, "kernels": prof_e}))
         return 0
-    ms_s, launches, prof, clk, _ = timed(step_surr, args.steps, args.warmup, profile=True, clocks=clocks)
+    ms_s, launches, prof, clk, _ = timed(surr_step(A, primary), args.steps, args.warmup, profile=True, clocks=clocks)
     if args.mode == "surrogate":        # profiling helper: the surrogate step alone
         if rank == 0:
-            print(json.dumps({"mode": "surrogate", "ms_per_step": ms_s, "kernels": prof}))
+            print(json.dumps({"mode": "surrogate", "domains": primary, "ms_per_step": ms_s, "kernels": prof}))
         return 0
     ms_e, launches_e, prof_e, _, _ = timed(step_exact, max(3, args.steps // 2), args.warmup, profile=True)
     ms_s_max = max_over_ranks(dist, ms_s, dev)
     ms_e_max = max_over_ranks(dist, ms_e, dev)
+    # the other choice of interpolation domains, for comparison
+    B = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, domains=other)
+    ms_o, _, prof_o, _, _ = timed(surr_step(B, other), max(3, args.steps // 2), args.warmup, profile=True)
+    ms_o_max = max_over_ranks(dist, ms_o, dev)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     xh = torch.empty(prob.N, dtype=tdt, pin_memory=True)
@@ -411,7 +446,7 @@ def run_gpu(args, wl):
     esz = 8 if wl.dtype == "f64" else 4
 
     def step_e2e():
-        iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A)
+        iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A, domains=primary)
         A.apply_host(xn, yn)
 
     for _ in range(args.warmup):
@@ -425,31 +460,35 @@ def run_gpu(args, wl):
     t_e2e = (time.perf_counter() - t0) / K2
     t_e2e = max_over_ranks(dist, t_e2e, dev)
 
-    # stated entry error of the surrogate: max |A~ - A| / max |A| over all stored entries (GPU copies)
-    vs, ve = A.values(), E.values()
-    entry_err = float((vs.double() - ve.double()).abs().max().item() / ve.double().abs().max().item())
-    del vs, ve
-    rowsum = float(A.apply(torch.ones_like(x)).double().abs().max().item())
+    def accuracy(mat):
+        """Stated entry error max |A~ - A| / max |A| over all stored entries (GPU copies), the
+        row sums, and the discrete-solution error of CG on both matrices with one load vector."""
+        vs, ve = mat.values(), E.values()
+        entry_err = float((vs.double() - ve.double()).abs().max().item() / ve.double().abs().max().item())
+        del vs, ve
+        rowsum = float(mat.apply(torch.ones_like(x)).double().abs().max().item())
+        solution = None
+        if not args.no_solve:
+            f = torch.from_numpy(W.rhs_vector(prob.N, seed=wl.seed)).to(dev)
+            u_e, it_e, res_e = E.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+            u_s, it_s, res_s = mat.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+            err = u_s - u_e
+            Ee = E.apply(err.to(tdt)).double()
+            Eu = E.apply(u_e.to(tdt)).double()
+            solution = {"rel_l2": float(err.norm() / u_e.norm()),
+                        "rel_energy": float(torch.sqrt(torch.dot(err, Ee) / torch.dot(u_e, Eu))),
+                        "cg_iters": {"exact": it_e, "surrogate": it_s}, "cg_rel_residual": max(res_e, res_s),
+                        "load": "f_i ~ U[-1,1] (seeded), homogeneous Dirichlet"}
+        return {"surrogate_vs_exact_max_rel": entry_err, "row_sum_max_abs": rowsum}, solution
 
-    # stated accuracy of the discrete solution: CG on both matrices, same load vector
-    solution = None
-    if not args.no_solve:
-        f = torch.from_numpy(W.rhs_vector(prob.N, seed=wl.seed)).to(dev)
-        u_e, it_e, res_e = E.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
-        u_s, it_s, res_s = A.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
-        err = u_s - u_e
-        Ee = E.apply(err.to(tdt)).double() if tdt == torch.float64 else E.apply(err.float()).double()
-        Eu = E.apply(u_e.to(tdt)).double()
-        solution = {"rel_l2": float(err.norm() / u_e.norm()),
-                    "rel_energy": float(torch.sqrt(torch.dot(err, Ee) / torch.dot(u_e, Eu))),
-                    "cg_iters": {"exact": it_e, "surrogate": it_s}, "cg_rel_residual": max(res_e, res_s),
-                    "load": "f_i ~ U[-1,1] (seeded), homogeneous Dirichlet"}
+    entry, solution = accuracy(A)
+    entry_o, solution_o = accuracy(B)
 
     if rank != 0:
         return 0
     peaks, peak_kind = measured_peaks()
     arith = iga.get_arithmetic(wl.dtype)
-    work = kernel_work(prob, wl, arith, surrogate=True)
+    work = kernel_work(prob, wl, arith, surrogate=True, domains=primary)
     per_kernel = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
     dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dom = per_kernel[dominant]
@@ -472,7 +511,7 @@ def run_gpu(args, wl):
                 "kernel": dominant, "peak_source": f"{peak_kind} hbm_gbs"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "kernel": dominant}
-    roof["traffic"] = ncu_traffic(dominant, wl.name)
+    roof["traffic"] = ncu_traffic(dominant, wl.name + ("" if primary == "common" else "_" + primary))
     roof["avg_launch_ms"] = avg_ms
     # SpMV against HBM, from the same timed region
     if "spmv" in per_kernel:
@@ -487,19 +526,23 @@ def run_gpu(args, wl):
     exact_value = aggregate_value(prob.nnz, world, ms_e_max * 1e-3)
     base = None
     if world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(wl, target_s=args.cpu_seconds)
+        base = cpu_baseline(wl, primary, target_s=args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_s_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": wl.dtype, "arith": {"contractions": arith, "coefficients": "fp64",
                                                          "fill": "df64", "spmv": wl.dtype},
         "data": "synthetic (seeded map/coefficient family, x ~ N(0,1))",
-        "config": config_of(wl, world),
+        "config": config_of(wl, world, primary),
         "exact": {"value": exact_value, "unit": UNIT, "ms_per_step": ms_e_max,
                   "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof_e.items() if v[0]}},
         "speedup_surrogate_vs_exact": ms_e_max / ms_s_max,
-        "entry_error": {"surrogate_vs_exact_max_rel": entry_err, "row_sum_max_abs": rowsum},
+        "entry_error": entry,
         "solution_error": solution,
+        other + "_domains": {"value": aggregate_value(prob.nnz, world, ms_o_max * 1e-3), "unit": UNIT,
+                             "ms_per_step": ms_o_max, "speedup_vs_exact": ms_e_max / ms_o_max,
+                             "entry_error": entry_o, "solution_error": solution_o,
+                             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof_o.items() if v[0]}},
         "kernels": per_kernel,
         "roofline": roof,
         "spmv_roofline": spmv_roof,
@@ -528,6 +571,8 @@ def main(argv=None):
     ap.add_argument("--no-solve", action="store_true", help="skip the CG solution-error report")
     ap.add_argument("--cg-tol", type=float, default=1e-10)
     ap.add_argument("--cg-maxit", type=int, default=20000)
+    ap.add_argument("--domains", choices=["common", "per_offset"], default="per_offset",
+                    help="interpolation domains of the headline surrogate (the other is reported beside it)")
     ap.add_argument("--mode", choices=["both", "surrogate", "exact"], default="both",
                     help="profiling helper: time only one of the two steps and print a short line")
     args = ap.parse_args(argv)

@@ -29,11 +29,13 @@ class Problem:
     map_kind: str = "identity"          # identity | affine | sinprod
     map_amp: float = 0.0
     affine: Optional[Tuple[float, ...]] = None   # 3x3 row-major matrix then 3-vector offset
-    kappa_kind: str = "const"           # const | sin2d | expsin3d | poly
+    kappa_kind: str = "const"           # const | sin2d | expsin3d | poly | bspline3
     kappa_a: float = 1.0
     kappa_b: float = 0.0
     kappa_deg: int = 0
     kappa_poly: Optional[Tuple[float, ...]] = None
+    kappa_nctrl: Optional[Tuple[int, ...]] = None    # bspline3: control values per direction
+    kappa_ctrl: Optional[Tuple[float, ...]] = None   # bspline3: c[a + n0 (b + n1 c)]
 
     @property
     def m(self) -> Tuple[int, ...]:
@@ -93,7 +95,21 @@ CFG_3D_P3_40 = Workload(
             kappa_kind="expsin3d", kappa_b=0.5),
     M=8, q=3, dtype="f64")
 
-WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4, CFG_3D_P3_40)}
+def lognormal_ctrl(nctrl: Tuple[int, ...], seed: int = 0, sigma: float = 0.25) -> Tuple[float, ...]:
+    """Control values c ~ exp(N(0, sigma)) of a B-spline diffusion coefficient, colexicographic."""
+    rng = np.random.default_rng(seed)
+    return tuple(float(v) for v in np.exp(rng.normal(0.0, sigma, size=int(np.prod(nctrl)))))
+
+
+# Differentiation case: p = 3, 48^3 elements, the 3-D sine-product map, and kappa a cubic
+# B-spline on the physical unit cube with 16^3 control values ~ exp(N(0, 0.25)); M = 8, q = 3.
+CFG_3D_P3_BSPLINE = Workload(
+    "3d_p3_48cube_bspline16_M8_q3",
+    Problem(dim=3, p=3, n_el=(48, 48, 48), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="bspline3", kappa_nctrl=(16, 16, 16), kappa_ctrl=lognormal_ctrl((16, 16, 16), seed=0)),
+    M=8, q=3, dtype="f64")
+
+WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4, CFG_3D_P3_40, CFG_3D_P3_BSPLINE)}
 
 
 def scaled(w: Workload, n_el: Tuple[int, ...], M: Optional[int] = None, p: Optional[int] = None) -> Workload:

@@ -68,6 +68,9 @@ extern "C" {
 #define IGA_KAPPA_SIN2D    1    /* a + b sin(2 pi x) sin(2 pi y) */
 #define IGA_KAPPA_EXPSIN3D 2    /* exp(b sin(2 pi x) cos(2 pi y) sin(2 pi z)) */
 #define IGA_KAPPA_POLY     3    /* sum_{a,b,c <= deg} poly[a + (deg+1)(b + (deg+1)c)] x^a y^b z^c, deg <= 3 */
+#define IGA_KAPPA_BSPLINE3 4    /* sum ctrl[a + n0 (b + n1 c)] N_a(x) N_b(y) N_c(z): cubic B-splines with open
+                                   uniform knots on [0, 1], nctrl_d - 3 elements per direction; the physical
+                                   point is clamped onto the unit cube */
 
 /*
  * Arithmetic of the sum-factorised quadrature contractions (process-wide,
@@ -102,6 +105,9 @@ typedef struct {
     int32_t deg;        /* IGA_KAPPA_POLY degree per direction (0..3) */
     double a, b;        /* constants of the closed forms above */
     double poly[64];    /* IGA_KAPPA_POLY coefficients */
+    int32_t nctrl[3];   /* IGA_KAPPA_BSPLINE3 control values per direction, 4..64 (entries beyond dim ignored) */
+    const double* ctrl; /* IGA_KAPPA_BSPLINE3 control values, DEVICE pointer owned by the caller; read by
+                           the kernels the call enqueues, so it must stay valid until they complete */
 } iga_kappa_t;
 
 typedef struct iga_matrix* iga_matrix_t;   /* opaque; owns device storage */
@@ -169,6 +175,25 @@ int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map
 int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_map_t* map,
                                    const iga_kappa_t* kappa, int M, int q, int domains,
                                    int dtype, void* stream, iga_matrix_t* A);
+
+/*
+ * Gradient with respect to the B-spline control values of kappa
+ * (IGA_KAPPA_BSPLINE3) of L = ybar^T A x, A the exact matrix (M = 0) or the
+ * surrogate with the common domain Omega~ (M >= 1, interpolation degree q), as
+ * assembled by iga_assemble_exact / iga_assemble_surrogate.  Every step of the
+ * surrogate is linear in kappa (the quadrature of eq. ChangeOfVars, the
+ * interpolation of Sec. 4.1, the copy and the diagonal of Sec. 5.3), and
+ *   dL/dc_k = sum_g N_k(phi(g)) s(g),
+ * s(g) the derivative of L with respect to kappa at Gauss point g (bilinear
+ * forms of the exact entries, the transposed interpolation of the interpolated
+ * ones).  The gradient with respect to x is A ybar (A is symmetric): use
+ * iga_apply.  The basis tables are recomputed by the call; FP64 throughout.
+ *   ybar, x: device FP64 [N], colexicographic.  grad: device FP64
+ *   [nctrl_0 nctrl_1 (nctrl_2)], overwritten.  kappa->ctrl is read.
+ *   Errors: IGA_EINVAL for another kappa kind, null pointers or M < 0.
+ */
+int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+                       int M, int q, const double* ybar, const double* x, double* grad, void* stream);
 
 /*
  * y = A x (eq. DiscreteVariationalProblems), stencil SpMV.  x and y are

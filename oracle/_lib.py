@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAP_KINDS = {"identity": 0, "affine": 1, "sinprod": 2}
-KAPPA_KINDS = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3}
+KAPPA_KINDS = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3, "bspline3": 4}
 
 
 class OrcProblem(ctypes.Structure):
@@ -38,6 +38,8 @@ class OrcProblem(ctypes.Structure):
         ("kappa_a", ctypes.c_double),
         ("kappa_b", ctypes.c_double),
         ("kappa_poly", ctypes.c_double * 64),
+        ("kappa_nctrl", ctypes.c_int32 * 3),
+        ("kappa_ctrl", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -105,6 +107,14 @@ def make_problem(prob) -> OrcProblem:
     coef = list(prob.kappa_poly) if prob.kappa_poly is not None else []
     for k in range(64):
         s.kappa_poly[k] = float(coef[k]) if k < len(coef) else 0.0
+    if prob.kappa_kind == "bspline3":
+        nc = list(prob.kappa_nctrl) + [1] * (3 - len(prob.kappa_nctrl))
+        for d in range(3):
+            s.kappa_nctrl[d] = int(nc[d])
+        ctrl = np.ascontiguousarray(np.asarray(prob.kappa_ctrl, dtype=np.float64))
+        assert ctrl.size == int(np.prod(nc[: prob.dim]))
+        s._ctrl_keepalive = ctrl                  # the struct only holds a pointer
+        s.kappa_ctrl = _dptr(ctrl)
     return s
 
 

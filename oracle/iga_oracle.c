@@ -40,7 +40,7 @@
 #define ORC_MAXP 8
 
 enum { ORC_MAP_IDENTITY = 0, ORC_MAP_AFFINE = 1, ORC_MAP_SINPROD = 2 };
-enum { ORC_KAPPA_CONST = 0, ORC_KAPPA_SIN2D = 1, ORC_KAPPA_EXPSIN3D = 2, ORC_KAPPA_POLY = 3 };
+enum { ORC_KAPPA_CONST = 0, ORC_KAPPA_SIN2D = 1, ORC_KAPPA_EXPSIN3D = 2, ORC_KAPPA_POLY = 3, ORC_KAPPA_BSPLINE3 = 4 };
 
 /* Problem description (mirrored by a ctypes Structure in oracle/_lib.py). */
 typedef struct {
@@ -55,6 +55,8 @@ typedef struct {
     double kappa_a;       /* constant / offset */
     double kappa_b;       /* amplitude */
     double kappa_poly[64];/* coef[a + (deg+1)(b + (deg+1)c)] of x^a y^b z^c */
+    int32_t kappa_nctrl[3];      /* ORC_KAPPA_BSPLINE3: control values per direction (4..64) */
+    const double* kappa_ctrl;    /* ORC_KAPPA_BSPLINE3: c[a + n0 (b + n1 c)], host memory */
 } orc_problem;
 
 static const double ORC_PI = 3.14159265358979323846;
@@ -218,6 +220,31 @@ double orc_kappa(const orc_problem* P, const double* x)
                 }
         return v;
     }
+    case ORC_KAPPA_BSPLINE3: {
+        /* cubic tensor-product B-spline on the physical unit cube, open uniform
+           knots with nctrl_d - 3 elements per direction; points outside [0,1]
+           are clamped onto it */
+        double N[3][64], D[64];
+        for (int d = 0; d < n; ++d) {
+            const int nc = P->kappa_nctrl[d];
+            if (nc < 4 || nc > 64) return NAN;
+            double t[64 + 4];
+            orc_open_uniform_knots(3, nc - 3, t);
+            double xd = x[d] < 0.0 ? 0.0 : (x[d] > 1.0 ? 1.0 : x[d]);
+            orc_bspline_all(3, nc + 4, t, xd, N[d], D);
+        }
+        double v = 0.0;
+        const int n2 = (n == 3) ? P->kappa_nctrl[2] : 1;
+        for (int c = 0; c < n2; ++c)
+            for (int b = 0; b < P->kappa_nctrl[1]; ++b)
+                for (int a = 0; a < P->kappa_nctrl[0]; ++a) {
+                    double term = P->kappa_ctrl[a + P->kappa_nctrl[0] * (b + P->kappa_nctrl[1] * c)];
+                    term *= N[0][a] * N[1][b];
+                    if (n == 3) term *= N[2][c];
+                    v += term;
+                }
+        return v;
+    }
     default:
         return NAN;
     }
@@ -323,6 +350,10 @@ static int problem_ok(const orc_problem* P)
     if (P->dim < 2 || P->dim > 3) return 0;
     if (P->p < 1 || P->p > ORC_MAXP) return 0;
     for (int d = 0; d < P->dim; ++d) if (P->n_el[d] < 1) return 0;
+    if (P->kappa_kind == ORC_KAPPA_BSPLINE3) {
+        if (!P->kappa_ctrl) return 0;
+        for (int d = 0; d < P->dim; ++d) if (P->kappa_nctrl[d] < 4 || P->kappa_nctrl[d] > 64) return 0;
+    }
     return 1;
 }
 

@@ -28,7 +28,7 @@ __all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "load",
 F64, F32 = 0, 1
 ARITH = {"fp64": 0, "df64": 1, "fp32": 2}
 _MAP = {"identity": 0, "affine": 1, "sinprod": 2}
-_KAPPA = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3}
+_KAPPA = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3, "bspline3": 4}
 _lock = threading.Lock()
 _lib = None
 
@@ -49,7 +49,8 @@ class Map(ctypes.Structure):
 
 class Kappa(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("deg", ctypes.c_int32), ("a", ctypes.c_double),
-                ("b", ctypes.c_double), ("poly", ctypes.c_double * 64)]
+                ("b", ctypes.c_double), ("poly", ctypes.c_double * 64), ("nctrl", ctypes.c_int32 * 3),
+                ("ctrl", ctypes.c_void_p)]
 
 
 def load():
@@ -72,6 +73,8 @@ def load():
         L.iga_assemble_surrogate_domains.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                                      ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, vp, ctypes.POINTER(H)]
+        L.iga_kappa_gradient.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                         ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.iga_apply.argtypes = [H, vp, vp, vp]
         L.iga_apply_host.argtypes = [H, vp, vp, vp]
         L.iga_matrix_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -103,7 +106,7 @@ def _stream_ptr(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def _structs(prob):
+def _structs(prob, ctrl=None):
     pt = Patch()
     pt.dim = int(prob.dim)
     for d in range(3):
@@ -122,6 +125,18 @@ def _structs(prob):
     poly = getattr(prob, "kappa_poly", None) or ()
     for k in range(64):
         kp.poly[k] = float(poly[k]) if k < len(poly) else 0.0
+    if prob.kappa_kind == "bspline3":
+        import torch
+        nc = list(prob.kappa_nctrl) + [1] * (3 - len(prob.kappa_nctrl))
+        for d in range(3):
+            kp.nctrl[d] = int(nc[d])
+        if ctrl is None:
+            ctrl = torch.tensor(prob.kappa_ctrl, dtype=torch.float64, device="cuda")
+        if not (ctrl.is_cuda and ctrl.dtype == torch.float64 and ctrl.is_contiguous()
+                and ctrl.numel() == int(np.prod(nc[: prob.dim]))):
+            raise ValueError("kappa control values must be a contiguous float64 CUDA tensor of prod(nctrl) entries")
+        kp.ctrl = ctrl.data_ptr()
+        kp._ctrl_keepalive = ctrl                    # the struct only holds the device pointer
     return pt, mp, kp
 
 
@@ -225,25 +240,34 @@ class Matrix:
             pass
 
 
-def assemble_exact(prob, dtype="f64", stream=None, out: Optional[Matrix] = None) -> Matrix:
-    """Exact Gauss-quadrature stiffness matrix on the GPU (iga_assemble_exact)."""
-    pt, mp, kp = _structs(prob)
+def _keep(mat: "Matrix", kp) -> "Matrix":
+    """The matrix holds the control-value tensor its assembly read (kernels may still run)."""
+    mat._kappa_ctrl = getattr(kp, "_ctrl_keepalive", None)
+    return mat
+
+
+def assemble_exact(prob, dtype="f64", stream=None, out: Optional[Matrix] = None, kappa_ctrl=None) -> Matrix:
+    """Exact Gauss-quadrature stiffness matrix on the GPU (iga_assemble_exact).
+
+    kappa_ctrl: optional float64 CUDA tensor of B-spline control values (kappa kind 'bspline3');
+    by default they are copied from the problem description."""
+    pt, mp, kp = _structs(prob, kappa_ctrl)
     h = ctypes.c_void_p(out.handle.value if out is not None else None)
     _check(load().iga_assemble_exact(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
                                      _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
-    return out if out is not None else Matrix(h.value)
+    return _keep(out if out is not None else Matrix(h.value), kp)
 
 
 DOMAINS = {"common": 0, "per_offset": 1}       # IGA_DOMAINS_COMMON / IGA_DOMAINS_PER_OFFSET
 
 
 def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Optional[Matrix] = None,
-                       domains: str = "common") -> Matrix:
+                       domains: str = "common", kappa_ctrl=None) -> Matrix:
     """Symmetric kernel-preserving surrogate stiffness matrix on the GPU.
 
     domains='common' interpolates on Omega~ (iga_assemble_surrogate); 'per_offset'
     on each Omega~_delta (iga_assemble_surrogate_domains)."""
-    pt, mp, kp = _structs(prob)
+    pt, mp, kp = _structs(prob, kappa_ctrl)
     h = ctypes.c_void_p(out.handle.value if out is not None else None)
     st = ctypes.c_void_p(_stream_ptr(stream))
     if domains == "common":
@@ -253,7 +277,7 @@ def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Opti
         _check(load().iga_assemble_surrogate_domains(ctypes.byref(pt), int(prob.p), ctypes.byref(mp),
                                                      ctypes.byref(kp), int(M), int(q), DOMAINS[domains],
                                                      _dtype_code(dtype), st, ctypes.byref(h)))
-    return out if out is not None else Matrix(h.value)
+    return _keep(out if out is not None else Matrix(h.value), kp)
 
 
 def set_arithmetic(dtype, arith: str):
@@ -287,3 +311,65 @@ def profile_read():
     ms = (ctypes.c_double * n)()
     _check(L.iga_profile_read(n, la, ms))
     return {L.iga_kernel_name(k).decode(): (int(la[k]), float(ms[k])) for k in range(n)}
+
+
+def kappa_gradient(prob, ybar, x, M: int = 0, q: int = 3, kappa_ctrl=None, stream=None):
+    """dL/dc for L = ybar^T A x and the B-spline control values c of kappa (iga_kappa_gradient).
+
+    A is the exact matrix (M = 0) or the common-domain surrogate (M >= 1, q).  ybar, x:
+    float64 CUDA tensors of N entries.  Returns a float64 CUDA tensor of prod(nctrl) entries."""
+    import torch
+    for v in (ybar, x):
+        if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64 and v.is_contiguous()
+                and v.numel() == prob.N):
+            raise ValueError("ybar and x must be contiguous float64 CUDA tensors of N entries")
+    pt, mp, kp = _structs(prob, kappa_ctrl)
+    nc = int(np.prod(prob.kappa_nctrl[: prob.dim])) if prob.kappa_kind == "bspline3" else 1
+    grad = torch.empty(nc, dtype=torch.float64, device=ybar.device)
+    _check(load().iga_kappa_gradient(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp), int(M),
+                                     int(q), ctypes.c_void_p(ybar.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return grad
+
+
+def _stiffness_apply_function():
+    import torch
+
+    class StiffnessApply(torch.autograd.Function):
+        """y = A(c) x for the exact (M = 0) or surrogate (M >= 1) matrix of a B-spline kappa with
+        control values c; backward gives A ybar for x and iga_kappa_gradient for c."""
+
+        @staticmethod
+        def forward(ctx, ctrl, x, prob, M, q):
+            ctrl = ctrl.detach().contiguous()
+            x = x.detach().contiguous()
+            if M >= 1:
+                A = assemble_surrogate(prob, M, q, dtype="f64", kappa_ctrl=ctrl)
+            else:
+                A = assemble_exact(prob, dtype="f64", kappa_ctrl=ctrl)
+            y = A.apply(x)
+            ctx.save_for_backward(ctrl, x)
+            ctx.A, ctx.prob, ctx.M, ctx.q = A, prob, M, q
+            return y
+
+        @staticmethod
+        def backward(ctx, ybar):
+            ctrl, x = ctx.saved_tensors
+            ybar = ybar.contiguous()
+            gc = kappa_gradient(ctx.prob, ybar, x, ctx.M, ctx.q, kappa_ctrl=ctrl) if ctx.needs_input_grad[0] else None
+            gx = ctx.A.apply(ybar) if ctx.needs_input_grad[1] else None
+            return gc, gx, None, None, None
+
+    return StiffnessApply
+
+
+_STIFFNESS_APPLY = None
+
+
+def stiffness_apply(ctrl, x, prob, M: int = 0, q: int = 3):
+    """Differentiable y = A(kappa_c) x (torch.autograd): gradients for the control values c
+    (float64 CUDA tensor) and for x."""
+    global _STIFFNESS_APPLY
+    if _STIFFNESS_APPLY is None:
+        _STIFFNESS_APPLY = _stiffness_apply_function()
+    return _STIFFNESS_APPLY.apply(ctrl, x, prob, M, q)

@@ -57,7 +57,8 @@ std::vector<cudaEvent_t> g_events;
 thread_local cudaEvent_t t_begin = nullptr;
 
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
-                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg"};
+                             "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg",
+                             "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter"};
 
 cudaEvent_t take_event()
 {
@@ -131,6 +132,12 @@ int check_geometry(const iga_patch_t* patch, int p, const iga_map_t* map, const 
     case IGA_KAPPA_POLY:
         if (kappa->deg < 0 || kappa->deg > 3) return fail(IGA_EINVAL, "polynomial kappa degree must be 0..3");
         break;
+    case IGA_KAPPA_BSPLINE3:
+        if (!kappa->ctrl) return fail(IGA_EINVAL, "IGA_KAPPA_BSPLINE3 needs a control value pointer");
+        for (int d = 0; d < g.dim; ++d)
+            if (kappa->nctrl[d] < 4 || kappa->nctrl[d] > 64)
+                return fail(IGA_EINVAL, "IGA_KAPPA_BSPLINE3: nctrl[%d] = %d outside 4..64", d, kappa->nctrl[d]);
+        break;
     default:
         return fail(IGA_EINVAL, "unknown kappa kind %d", kappa->kind);
     }
@@ -139,6 +146,10 @@ int check_geometry(const iga_patch_t* patch, int p, const iga_map_t* map, const 
     g.ka = kappa->a;
     g.kb = kappa->b;
     for (int k = 0; k < 64; ++k) g.poly[k] = kappa->poly[k];
+    if (kappa->kind == IGA_KAPPA_BSPLINE3) {
+        for (int d = 0; d < 3; ++d) g.knc[d] = (d < g.dim) ? kappa->nctrl[d] : 1;
+        g.kctrl = kappa->ctrl;
+    }
     return IGA_OK;
 }
 
@@ -197,6 +208,103 @@ SampleAxis per_offset_axis(int p, int m, int M)
     return a;
 }
 
+// Interpolation plan (SplinePlan) of a surrogate: region of rows with
+// interpolated entries [k0, k1] per direction -- the box Omega~ = [2p, m-2p-1]
+// (Sec. 4), or the cardinal box [p, m-p-1] with per-offset domains (Sec. 3.2) --
+// its sample axes and, per direction and offset component, the interpolation
+// domain and samples.  empty = 1 when the region has no row.
+int plan_spline(const Geo& g, int p, int M, int q, int domains, SplinePlan& sp, int& empty, int k1[3])
+{
+    const int dim = g.dim, W = 2 * p + 1;
+    const int S = (dim == 3) ? W * W * W : W * W;
+    memset(&sp, 0, sizeof(sp));
+    sp.dim = dim; sp.q = q; sp.S = S; sp.c = (S - 1) / 2; sp.nv = W;
+    sp.all = (domains == IGA_DOMAINS_COMMON);
+    empty = 0;
+    const bool per_offset = (domains == IGA_DOMAINS_PER_OFFSET);
+    const int k0 = per_offset ? p : 2 * p;
+    for (int d = 0; d < dim; ++d) {
+        k1[d] = g.m[d] - k0 - 1;
+        if (k1[d] < k0) empty = 1;
+    }
+    if (empty) return IGA_OK;
+    for (int d = 0; d < 3; ++d) {
+        if (d >= dim) {
+            sp.ax[d] = common_axis(0, 0, 1);
+            sp.nu[d] = 1;
+            sp.r0[d] = sp.r1[d] = 0;
+            sp.Lmax[d] = 1;
+            for (int v = 0; v < W; ++v) { sp.L[d][v] = 1; sp.ns[d][v] = 1; }
+            continue;
+        }
+        sp.ax[d] = per_offset ? per_offset_axis(p, g.m[d], M) : common_axis(k0, k1[d], M);
+        sp.nu[d] = sp.ax[d].n;
+        if (sp.nu[d] > kMaxSamplesPerDir)
+            return fail(IGA_EUNSUPPORTED, "more than %d samples per direction", kMaxSamplesPerDir);
+        sp.r0[d] = k0;
+        sp.r1[d] = k1[d];
+        sp.Lmax[d] = 0;
+        for (int v = 0; v < W; ++v) {
+            const int dd = v - p;
+            // domain of the offset component dd: Omega~_delta (Sec. 3.2) or Omega~
+            const int lo = per_offset ? k0 + std::max(0, -dd) : k0;
+            const int hi = per_offset ? k1[d] - std::max(0, dd) : k1[d];
+            if (hi < lo) { sp.L[d][v] = 0; sp.ns[d][v] = 0; sp.k0[d][v] = lo; continue; }
+            sp.k0[d][v] = lo;
+            sp.L[d][v] = hi - lo + 1;
+            int ns = 0;
+            for (int a = 0; a < sp.nu[d]; ++a) ns += variant_sample(sp.ax[d], sp.all, axis_sample(sp.ax[d], a), lo, hi);
+            sp.ns[d][v] = ns;
+            sp.qe[d][v] = std::min(q, ns - 1);
+            sp.Lmax[d] = std::max(sp.Lmax[d], sp.L[d][v]);
+        }
+    }
+    sp.n_samples = 1;
+    for (int d = 0; d < dim; ++d) sp.n_samples *= sp.nu[d];
+    return IGA_OK;
+}
+
+// Scratch offsets of the interpolation tables of a plan.
+struct SplineLayout {
+    int64_t lu[3][kMaxV], eval[3][kMaxV], eval0[kMaxV], ints = 0;
+    int64_t espan[3][kMaxV], pos[3][kMaxV], inv[3][kMaxV];
+};
+
+void spline_layout(Layout& lay, const SplinePlan& sp, SplineLayout& o)
+{
+    memset(&o, 0, sizeof(o));
+    int64_t nints = 2 * 3 * kMaxV + 8;
+    for (int d = 0; d < sp.dim; ++d)
+        for (int v = 0; v < sp.nv; ++v) {
+            const int64_t L = sp.L[d][v];
+            o.lu[d][v] = lay.take((int64_t)sp.ns[d][v] * sp.ns[d][v]);
+            o.eval[d][v] = lay.take(L * (sp.qe[d][v] + 1));
+            if (d == 0) o.eval0[v] = lay.take(L * (sp.qe[d][v] + 1));
+            o.espan[d][v] = nints;
+            nints += align_up(L + 1, 8);
+            o.pos[d][v] = nints;
+            nints += align_up(sp.ns[d][v] + 1, 8);
+            o.inv[d][v] = nints;
+            nints += align_up(sp.nu[d] + 1, 8);
+        }
+    o.ints = lay.take(div_up(nints, 2));
+}
+
+void spline_bufs(double* scratch, const SplinePlan& sp, const SplineLayout& o, SplineBufs& sb)
+{
+    int* ints = (int*)(scratch + o.ints);
+    sb.band = ints;
+    for (int d = 0; d < sp.dim; ++d)
+        for (int v = 0; v < sp.nv; ++v) {
+            sb.lu[d][v] = scratch + o.lu[d][v];
+            sb.eval[d][v] = scratch + o.eval[d][v];
+            sb.espan[d][v] = ints + o.espan[d][v];
+            sb.pos[d][v] = ints + o.pos[d][v];
+            sb.inv[d][v] = ints + o.inv[d][v];
+            if (d == 0) sb.eval0[v] = reinterpret_cast<float2*>(scratch + o.eval0[v]);
+        }
+}
+
 int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
              int M, int q, int domains, int dtype, void* stream_v, iga_matrix_t* out)
 {
@@ -237,56 +345,15 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     memset(&bs, 0, sizeof(bs));
     SplinePlan sp;
     memset(&sp, 0, sizeof(sp));
-    sp.dim = dim; sp.q = q; sp.S = S; sp.c = (S - 1) / 2; sp.nv = W;
-    sp.all = (domains == IGA_DOMAINS_COMMON);
     int empty = 0;
     bool do_spline = false;
     std::vector<Box> boxes;
     if (surrogate) {
-        // region of rows with interpolated entries, [r0, r1] per direction: the box
-        // Omega~ = [2p, m-2p-1] (Sec. 4), or the cardinal box [p, m-p-1] with
-        // per-offset domains (Sec. 3.2); the frame outside it is exact
-        const bool per_offset = (domains == IGA_DOMAINS_PER_OFFSET);
-        const int k0 = per_offset ? p : 2 * p;
+        const int k0 = (domains == IGA_DOMAINS_PER_OFFSET) ? p : 2 * p;
         int k1[3] = {0, 0, 0};
-        for (int d = 0; d < dim; ++d) {
-            k1[d] = g.m[d] - k0 - 1;
-            if (k1[d] < k0) empty = 1;
-        }
+        rc = plan_spline(g, p, M, q, domains, sp, empty, k1);
+        if (rc) return rc;
         if (!empty) {
-            for (int d = 0; d < 3; ++d) {
-                if (d >= dim) {
-                    sp.ax[d] = common_axis(0, 0, 1);
-                    sp.nu[d] = 1;
-                    sp.r0[d] = sp.r1[d] = 0;
-                    sp.Lmax[d] = 1;
-                    for (int v = 0; v < W; ++v) { sp.L[d][v] = 1; sp.ns[d][v] = 1; }
-                    continue;
-                }
-                sp.ax[d] = per_offset ? per_offset_axis(p, g.m[d], M) : common_axis(k0, k1[d], M);
-                sp.nu[d] = sp.ax[d].n;
-                if (sp.nu[d] > kMaxSamplesPerDir)
-                    return fail(IGA_EUNSUPPORTED, "more than %d samples per direction", kMaxSamplesPerDir);
-                sp.r0[d] = k0;
-                sp.r1[d] = k1[d];
-                sp.Lmax[d] = 0;
-                for (int v = 0; v < W; ++v) {
-                    const int dd = v - p;
-                    // domain of the offset component dd: Omega~_delta (Sec. 3.2) or Omega~
-                    const int lo = per_offset ? k0 + std::max(0, -dd) : k0;
-                    const int hi = per_offset ? k1[d] - std::max(0, dd) : k1[d];
-                    if (hi < lo) { sp.L[d][v] = 0; sp.ns[d][v] = 0; sp.k0[d][v] = lo; continue; }
-                    sp.k0[d][v] = lo;
-                    sp.L[d][v] = hi - lo + 1;
-                    int ns = 0;
-                    for (int a = 0; a < sp.nu[d]; ++a) ns += variant_sample(sp.ax[d], sp.all, axis_sample(sp.ax[d], a), lo, hi);
-                    sp.ns[d][v] = ns;
-                    sp.qe[d][v] = std::min(q, ns - 1);
-                    sp.Lmax[d] = std::max(sp.Lmax[d], sp.L[d][v]);
-                }
-            }
-            sp.n_samples = 1;
-            for (int d = 0; d < dim; ++d) sp.n_samples *= sp.nu[d];
             for (int d = 0; d < 3; ++d) bs.ax[d] = sp.ax[d];
             bs.n_samples = sp.n_samples;
             do_spline = true;
@@ -351,10 +418,8 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         }
         bs.box[k] = b;
     }
-    int64_t o_samples = 0, o_lu[3][kMaxV], o_eval[3][kMaxV], o_eval0[kMaxV], o_partial = 0, o_ints = 0, o_mid = 0;
-    int64_t i_espan[3][kMaxV], i_pos[3][kMaxV], i_inv[3][kMaxV];
-    memset(o_lu, 0, sizeof(o_lu)); memset(o_eval, 0, sizeof(o_eval)); memset(o_eval0, 0, sizeof(o_eval0));
-    memset(i_espan, 0, sizeof(i_espan)); memset(i_pos, 0, sizeof(i_pos)); memset(i_inv, 0, sizeof(i_inv));
+    int64_t o_samples = 0, o_partial = 0, o_mid = 0;
+    SplineLayout slo;
     if (do_spline) {
         Box sbx;                         // shape of every sample box: one row, p + 1 elements per direction
         memset(&sbx, 0, sizeof(sbx));
@@ -371,24 +436,10 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
             nblk[s] += bs.bper_s[s] * sp.n_samples;
         }
         o_samples = lay.take((int64_t)S * sp.n_samples);
-        int64_t nints = 2 * 3 * kMaxV + 8;
-        for (int d = 0; d < dim; ++d)
-            for (int v = 0; v < W; ++v) {
-                const int64_t L = sp.L[d][v];
-                o_lu[d][v] = lay.take((int64_t)sp.ns[d][v] * sp.ns[d][v]);
-                o_eval[d][v] = lay.take(L * (sp.qe[d][v] + 1));
-                if (d == 0) o_eval0[v] = lay.take(L * (sp.qe[d][v] + 1));
-                i_espan[d][v] = nints;
-                nints += align_up(L + 1, 8);
-                i_pos[d][v] = nints;
-                nints += align_up(sp.ns[d][v] + 1, 8);
-                i_inv[d][v] = nints;
-                nints += align_up(sp.nu[d] + 1, 8);
-            }
+        spline_layout(lay, sp, slo);
         const int64_t S_up = S - 1 - sp.c;
         o_mid = lay.take(dim == 3 ? S_up * sp.Lmax[2] * (int64_t)sp.nu[1] * sp.nu[0] : 1);
         o_partial = lay.take(S_up * (dim == 3 ? sp.Lmax[2] : 1) * (int64_t)sp.Lmax[1] * sp.nu[0]);
-        o_ints = lay.take(div_up(nints, 2));
     }
     for (int s = 0; s < 4; ++s)
         if (nblk[s] > 0x7fffffffLL) return fail(IGA_EUNSUPPORTED, "problem too large for one launch");
@@ -446,17 +497,7 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     SplineBufs sb;
     memset(&sb, 0, sizeof(sb));
     if (do_spline) {
-        int* ints = (int*)P(o_ints);
-        sb.band = ints;
-        for (int d = 0; d < dim; ++d)
-            for (int v = 0; v < W; ++v) {
-                sb.lu[d][v] = P(o_lu[d][v]);
-                sb.eval[d][v] = P(o_eval[d][v]);
-                sb.espan[d][v] = ints + i_espan[d][v];
-                sb.pos[d][v] = ints + i_pos[d][v];
-                sb.inv[d][v] = ints + i_inv[d][v];
-                if (d == 0) sb.eval0[v] = reinterpret_cast<float2*>(P(o_eval0[v]));
-            }
+        spline_bufs(scratch, sp, slo, sb);
         sb.partial = reinterpret_cast<float2*>(P(o_partial));
         sb.mid = P(o_mid);
         if (ce == cudaSuccess) { stage = "spline interpolation"; ce = launch_spline(g, sp, samples, sb, st); }
@@ -549,6 +590,126 @@ int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map
                            int M, int q, int dtype, void* stream, iga_matrix_t* A)
 {
     return assemble(patch, p, map, kappa, true, M, q, IGA_DOMAINS_COMMON, dtype, stream, A);
+}
+
+int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, int M,
+                       int q, const double* ybar, const double* x, double* grad, void* stream_v)
+{
+    t_err.clear();
+    Geo g;
+    int rc = check_geometry(patch, p, map, kappa, g);
+    if (rc) return rc;
+    if (kappa->kind != IGA_KAPPA_BSPLINE3) return fail(IGA_EINVAL, "the kappa gradient needs IGA_KAPPA_BSPLINE3");
+    if (!ybar || !x || !grad) return fail(IGA_EINVAL, "ybar, x and grad must be non-null device pointers");
+    if (M < 0) return fail(IGA_EINVAL, "M must be 0 (exact matrix) or >= 1 (surrogate), got %d", M);
+    if (M >= 1 && (q < 0 || q > kMaxQ))
+        return fail(IGA_EUNSUPPORTED, "interpolation degree q must be in 0..%d (got %d)", kMaxQ, q);
+    const int dim = g.dim, Q = p + 1;
+    int64_t N = 1, nctrl = 1, npts = 1;
+    int64_t G[3] = {1, 1, 1};
+    for (int d = 0; d < dim; ++d) {
+        N *= g.m[d];
+        nctrl *= g.knc[d];
+        G[d] = (int64_t)g.n_el[d] * Q;
+        npts *= G[d];
+    }
+    cudaStream_t st = (cudaStream_t)stream_v;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+
+    SplinePlan sp;
+    memset(&sp, 0, sizeof(sp));
+    int empty = 1, k1[3] = {0, 0, 0};
+    if (M >= 1) {
+        rc = plan_spline(g, p, M, q, IGA_DOMAINS_COMMON, sp, empty, k1);
+        if (rc) return rc;
+    }
+    const bool sur = (M >= 1) && !empty;       // an empty Omega~ leaves the exact matrix
+
+    // ---------------- scratch ----------------
+    Layout lay;
+    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_tdf[3];
+    for (int d = 0; d < 3; ++d) {
+        const int64_t Gd = (d < dim) ? G[d] : 1;
+        o_gx[d] = lay.take(Gd); o_sx[d] = lay.take(2 * Gd); o_cx[d] = lay.take(2 * Gd); o_wq[d] = lay.take(Gd);
+        o_bv[d] = lay.take(Gd * Q); o_bd[d] = lay.take(Gd * Q); o_tdf[d] = lay.take(4 * Gd);
+    }
+    const int64_t m2 = (dim == 3) ? g.m[2] : 1;
+    const int64_t tot0 = m2 * g.m[1] * G[0], tot1 = m2 * G[1] * G[0];
+    const int nvec = sur ? 6 : 2;
+    const int64_t o_W0 = lay.take(2 * tot0);
+    int64_t o_W1[6];
+    for (int v = 0; v < nvec; ++v) o_W1[v] = lay.take(3 * tot1);
+    const int64_t o_vec = sur ? lay.take(4 * N) : 0;
+    const int64_t o_spt = lay.take(npts);
+    SplineLayout slo;
+    int64_t o_C0 = 0, o_C1 = 0, o_tab = 0;
+    if (sur) {
+        spline_layout(lay, sp, slo);
+        const int P = p;
+        const int64_t S_up = sp.S - 1 - sp.c;
+        const int64_t L1 = sp.L[1][P], L2 = (dim == 3) ? sp.L[2][P] : 1;
+        o_C0 = lay.take(S_up * L2 * L1 * sp.nu[0]);
+        o_C1 = lay.take(dim == 3 ? S_up * L2 * (int64_t)sp.nu[1] * sp.nu[0] : 1);
+        o_tab = lay.take(S_up * sp.n_samples);
+    }
+    cudaMemPool_t pool;
+    if ((ce = device_pool(dev, &pool)) != cudaSuccess) return cuda_fail(ce, "creating the memory pool");
+    double* scratch = nullptr;
+    ce = cudaMallocFromPoolAsync((void**)&scratch, (size_t)lay.total * sizeof(double), pool, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "allocating scratch");
+    auto P = [&](int64_t off) { return scratch + off; };
+
+    // ---------------- launches ----------------
+    double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3];
+    float2* tdf[3];
+    AdjTables T;
+    for (int d = 0; d < 3; ++d) {
+        gx[d] = P(o_gx[d]); sx[d] = P(o_sx[d]); cx[d] = P(o_cx[d]); wq[d] = P(o_wq[d]);
+        bv[d] = P(o_bv[d]); bd[d] = P(o_bd[d]); tdf[d] = reinterpret_cast<float2*>(P(o_tdf[d]));
+        T.gx[d] = gx[d]; T.wq[d] = wq[d]; T.bv[d] = bv[d]; T.bd[d] = bd[d];
+    }
+    const char* stage = "basis tables";
+    ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
+    // vectors whose bilinear forms carry the exact entries
+    const double* vecs[6] = {ybar, x, nullptr, nullptr, nullptr, nullptr};
+    if (sur && ce == cudaSuccess) {
+        stage = "restricted vectors";
+        ce = launch_adj_vectors(g, sp, ybar, x, P(o_vec), st);
+        for (int k = 0; k < 4; ++k) vecs[2 + k] = P(o_vec) + k * N;
+    }
+    for (int v = 0; v < nvec && ce == cudaSuccess; ++v) {
+        stage = "gradient fields";
+        ce = launch_adj_grad_field(g, T, vecs[v], P(o_W0), P(o_W1[v]), st);
+    }
+    AdjTerms terms;
+    memset(&terms, 0, sizeof(terms));
+    terms.tot1 = tot1;
+    terms.n = sur ? 3 : 1;
+    terms.sign[0] = 1.0; terms.Wa[0] = P(o_W1[0]); terms.Wb[0] = P(o_W1[1]);
+    if (sur) {
+        terms.sign[1] = -1.0; terms.Wa[1] = P(o_W1[2]); terms.Wb[1] = P(o_W1[3]);
+        terms.sign[2] = 1.0; terms.Wa[2] = P(o_W1[4]); terms.Wb[2] = P(o_W1[5]);
+    }
+    if (ce == cudaSuccess) { stage = "point field"; ce = launch_adj_points(g, T, terms, P(o_spt), st); }
+    if (sur) {
+        SplineBufs sb;
+        memset(&sb, 0, sizeof(sb));
+        spline_bufs(scratch, sp, slo, sb);
+        if (ce == cudaSuccess) { stage = "spline tables"; ce = launch_spline_setup(sp, sb, st); }
+        if (ce == cudaSuccess) {
+            stage = "transposed interpolation";
+            ce = launch_adj_interp(g, sp, sb, ybar, x, P(o_C0), P(o_C1), P(o_tab), st);
+        }
+        if (ce == cudaSuccess) { stage = "sample rows"; ce = launch_adj_samples(g, T, sp, P(o_tab), P(o_spt), st); }
+    }
+    if (ce == cudaSuccess) { stage = "gradient reset"; ce = cudaMemsetAsync(grad, 0, (size_t)nctrl * sizeof(double), st); }
+    if (ce == cudaSuccess) { stage = "control scatter"; ce = launch_adj_scatter(g, T, P(o_spt), grad, st); }
+    cudaError_t fe = cudaFreeAsync(scratch, st);
+    if (ce == cudaSuccess) ce = fe;
+    if (ce != cudaSuccess) return cuda_fail(ce, stage);
+    return IGA_OK;
 }
 
 int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,

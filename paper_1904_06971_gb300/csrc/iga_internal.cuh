@@ -23,6 +23,8 @@ struct Geo {
     int kappa_kind, kappa_deg;
     double ka, kb;
     double poly[64];
+    int knc[3];               // IGA_KAPPA_BSPLINE3: control values per direction
+    const double* kctrl;      // IGA_KAPPA_BSPLINE3: control values (device)
     // double-float copies (hi, lo) of amp, ka, kb for the double-float coefficient path
     float amp_df[2], ka_df[2], kb_df[2];
     int coef_df;              // evaluate the coefficient tensor in double-float arithmetic
@@ -119,7 +121,8 @@ struct Tables {
 
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
-    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE, K_NUM
+    K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE,
+    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
@@ -196,6 +199,35 @@ cudaError_t launch_fill(const Geo& g, const SplinePlan& sp, int empty_box, const
                         void* ell, int ell_f32, cudaStream_t s);
 cudaError_t launch_spmv(int dim, int p, const int m[3], const void* values, int f32,
                         const void* x, void* y, cudaStream_t s);
+// K4 part 1 alone: knots, collocation LU and evaluation tables of every variant.
+cudaError_t launch_spline_setup(const SplinePlan& sp, const SplineBufs& sb, cudaStream_t s);
+
+// ---- adjoint with respect to B-spline control values of kappa (k_adjoint.cu) ----
+struct AdjTables {
+    const double* gx[3];      // [G] Gauss point coordinates
+    const double* wq[3];      // [G] weights (times h)
+    const double* bv[3];      // [G][p+1] values of the active basis functions
+    const double* bd[3];      // [G][p+1] their derivatives
+};
+constexpr int kMaxAdjTerms = 3;
+// s(g) = w_g sum_t sign_t grad u_{a_t}^T G grad u_{b_t}; Wa/Wb are direction-1 partial sums (pass 1)
+struct AdjTerms {
+    int n;
+    double sign[kMaxAdjTerms];
+    const double* Wa[kMaxAdjTerms];
+    const double* Wb[kMaxAdjTerms];
+    int64_t tot1;             // entries per component of a pass-1 array
+};
+cudaError_t launch_adj_vectors(const Geo& g, const SplinePlan& sp, const double* ybar, const double* x, double* out,
+                               cudaStream_t s);
+cudaError_t launch_adj_grad_field(const Geo& g, const AdjTables& T, const double* v, double* W0, double* W1,
+                                  cudaStream_t s);
+cudaError_t launch_adj_points(const Geo& g, const AdjTables& T, const AdjTerms& terms, double* spt, cudaStream_t s);
+cudaError_t launch_adj_interp(const Geo& g, const SplinePlan& sp, const SplineBufs& sb, const double* ybar,
+                              const double* x, double* C0, double* C1, double* table, cudaStream_t s);
+cudaError_t launch_adj_samples(const Geo& g, const AdjTables& T, const SplinePlan& sp, const double* phibar,
+                               double* spt, cudaStream_t s);
+cudaError_t launch_adj_scatter(const Geo& g, const AdjTables& T, const double* spt, double* grad, cudaStream_t s);
 
 // Scratch sizes (doubles) of a box for the quadrature stages.
 inline int64_t box_coef_len(int dim, int p, const Box& b) {

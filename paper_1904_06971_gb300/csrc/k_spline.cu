@@ -242,17 +242,22 @@ __global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* sam
     sb.partial[idx] = PolDF::from_double(acc);
 }
 
-cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, double* samples,
-                          const SplineBufs& sb, cudaStream_t s)
+cudaError_t launch_spline_setup(const SplinePlan& sp, const SplineBufs& sb, cudaStream_t s)
 {
-    (void)g;
     int nkmax = 0;
     for (int d = 0; d < sp.dim; ++d)
         for (int v = 0; v < sp.nv; ++v) nkmax = max(nkmax, 2 * sp.ns[d][v] + sp.qe[d][v] + 1);
     launch_begin(K_SPLINE_SETUP, s);
     k_spline_setup<<<dim3(sp.nv, sp.dim), 256, (size_t)nkmax * sizeof(double), s>>>(sp, sb);
     launch_end(K_SPLINE_SETUP, s);
-    cudaError_t err = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, double* samples,
+                          const SplineBufs& sb, cudaStream_t s)
+{
+    (void)g;
+    cudaError_t err = launch_spline_setup(sp, sb, s);
     if (err != cudaSuccess) return err;
     const int64_t S_up = sp.S - 1 - sp.c;
     for (int d = 0; d < sp.dim; ++d) {

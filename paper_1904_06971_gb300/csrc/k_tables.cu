@@ -224,6 +224,34 @@ cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
 // ([field][g2][g1][g0], g0 fastest).  Fields: 3-D C00 C01 C02 C11 C12 C22,
 // 2-D C00 C01 C11.
 // ---------------------------------------------------------------------------
+// The four cubic B-splines first..first+3 that are nonzero at x in [0, 1] on the
+// open uniform knot vector with ne elements (knots 0 x4, k/ne, 1 x4), by the
+// triangular Cox-de Boor recursion.
+__device__ __forceinline__ double cubic_knot(int j, int ne)
+{
+    return j <= 3 ? 0.0 : (j >= ne + 3 ? 1.0 : (double)(j - 3) / (double)ne);
+}
+__device__ void cubic_open_basis(int ne, double x, int& first, double N[4])
+{
+    int e = (int)(x * ne);
+    e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
+    const int mu = e + 3;
+    double left[4], right[4];
+    N[0] = 1.0;
+    for (int k = 1; k <= 3; ++k) {
+        left[k] = x - cubic_knot(mu + 1 - k, ne);
+        right[k] = cubic_knot(mu + k, ne) - x;
+        double saved = 0.0;
+        for (int r = 0; r < k; ++r) {
+            const double tmp = N[r] / (right[r + 1] + left[k - r]);
+            N[r] = saved + right[r + 1] * tmp;
+            saved = left[k - r] * tmp;
+        }
+        N[k] = saved;
+    }
+    first = e;
+}
+
 __device__ double kappa_at(const Geo& g, const double* x)
 {
     switch (g.kappa_kind) {
@@ -246,6 +274,24 @@ __device__ double kappa_at(const Geo& g, const double* x)
             }
             v = (g.dim == 3) ? v * x[2] + vb : vb;
         }
+        return v;
+    }
+    case IGA_KAPPA_BSPLINE3: {
+        int f[3] = {0, 0, 0};
+        double N[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
+        for (int d = 0; d < g.dim; ++d) {
+            const double xd = fmin(fmax(x[d], 0.0), 1.0);
+            cubic_open_basis(g.knc[d] - 3, xd, f[d], N[d]);
+        }
+        const int n0 = g.knc[0], n1 = g.knc[1];
+        const int nc2 = (g.dim == 3) ? 4 : 1;
+        double v = 0.0;
+        for (int c = 0; c < nc2; ++c)
+            for (int b = 0; b < 4; ++b) {
+                const double* row = g.kctrl + f[0] + (int64_t)n0 * ((f[1] + b) + (int64_t)n1 * (f[2] + c));
+                const double w = N[1][b] * N[2][c];
+                v += w * (((row[0] * N[0][0] + row[1] * N[0][1]) + row[2] * N[0][2]) + row[3] * N[0][3]);
+            }
         return v;
     }
     default:

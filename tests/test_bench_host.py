@@ -16,6 +16,7 @@ import iga_workloads as W
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
+from oracle import per_offset as po  # noqa: E402
 
 
 def _free_port():
@@ -51,20 +52,23 @@ def test_max_over_ranks_gloo_two_ranks():
     assert [o[2] for o in out] == [100.0, 100.0]      # 100 units x 2 ranks / 2 s
 
 
-def _brute_stage_fmas(prob, M, surrogate):
+def _brute_stage_fmas(prob, M, surrogate, domains="common"):
     """Count the FMAs of the three stage loops literally (tiny problems)."""
     p, dim = prob.p, prob.dim
     Q, Wd = p + 1, 2 * p + 1
-    boxes, ns = bench._boxes(prob, M, surrogate)
+    boxes, ns = bench._boxes(prob, M, surrogate, domains)
     if ns:
-        k0 = 2 * p
-        samples = []
-        for d in range(dim):
-            k1 = prob.m[d] - 2 * p - 1
-            s = list(range(k0, k1 + 1, M))
-            if s[-1] != k1:
-                s.append(k1)
-            samples.append(s)
+        if domains == "per_offset":
+            samples = [po.union_samples(p, prob.m[d], M) for d in range(dim)]
+        else:
+            k0 = 2 * p
+            samples = []
+            for d in range(dim):
+                k1 = prob.m[d] - 2 * p - 1
+                s = list(range(k0, k1 + 1, M))
+                if s[-1] != k1:
+                    s.append(k1)
+                samples.append(s)
         import itertools
         for c in itertools.product(*samples):
             boxes = boxes + [[(ci, 1) for ci in c]]
@@ -98,14 +102,16 @@ def _brute_stage_fmas(prob, M, surrogate):
     return tot
 
 
-@pytest.mark.parametrize("prob,M,surr", [
-    (W.Problem(dim=3, p=2, n_el=(13, 12, 14)), 3, True),
-    (W.Problem(dim=3, p=3, n_el=(9, 8, 10)), 2, False),
-    (W.Problem(dim=2, p=2, n_el=(20, 23)), 4, True),
+@pytest.mark.parametrize("prob,M,surr,domains", [
+    (W.Problem(dim=3, p=2, n_el=(13, 12, 14)), 3, True, "common"),
+    (W.Problem(dim=3, p=3, n_el=(9, 8, 10)), 2, False, "common"),
+    (W.Problem(dim=2, p=2, n_el=(20, 23)), 4, True, "common"),
+    (W.Problem(dim=3, p=2, n_el=(13, 12, 14)), 3, True, "per_offset"),
+    (W.Problem(dim=2, p=3, n_el=(25, 22)), 4, True, "per_offset"),
 ])
-def test_stage_fma_model_matches_loop_count(prob, M, surr):
-    got = bench.stage_fmas(prob, M, surr)
-    ref = _brute_stage_fmas(prob, M, surr)
+def test_stage_fma_model_matches_loop_count(prob, M, surr, domains):
+    got = bench.stage_fmas(prob, M, surr, domains)
+    ref = _brute_stage_fmas(prob, M, surr, domains)
     assert got == ref
 
 
