@@ -356,6 +356,55 @@ def config_of(wl, world, domains="common"):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
+def adjoint_report(iga, torch, dev, steps: int, warmup: int):
+    """Gradient of L = ybar^T A~(c) x with respect to the 16^3 B-spline control values of
+    kappa and x on the 48^3, p = 3 workload: forward (assembly + SpMV) and backward
+    (iga_kappa_gradient + SpMV), CUDA events, inputs resident."""
+    wl = W.CFG_3D_P3_BSPLINE
+    prob = wl.problem
+    gen = torch.Generator(device="cpu").manual_seed(wl.seed)
+    x = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dev)
+    ybar = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dev)
+    ctrl = torch.tensor(prob.kappa_ctrl, dtype=torch.float64, device=dev)
+    out = {"workload": wl.name, "controls": ctrl.numel(), "unit": "ms"}
+    for M, key in ((wl.M, "surrogate"), (0, "exact")):
+        A = iga.assemble_surrogate(prob, M, wl.q, kappa_ctrl=ctrl) if M else iga.assemble_exact(prob, kappa_ctrl=ctrl)
+        y = torch.empty_like(x)
+        gx = torch.empty_like(x)
+
+        def fwd():
+            if M:
+                iga.assemble_surrogate(prob, M, wl.q, out=A, kappa_ctrl=ctrl)
+            else:
+                iga.assemble_exact(prob, out=A, kappa_ctrl=ctrl)
+            A.apply(x, y)
+
+        def bwd():
+            iga.kappa_gradient(prob, ybar, x, M, wl.q, kappa_ctrl=ctrl)
+            A.apply(ybar, gx)
+
+        res = {}
+        for name, fn in (("forward", fwd), ("backward", bwd)):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            iga.profile_read()
+            iga.profile_enable(True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(steps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            iga.profile_enable(False)
+            prof = iga.profile_read()
+            res[name + "_ms"] = a.elapsed_time(b) / steps
+            res[name + "_kernels"] = {k: round(v[1] / steps, 4) for k, v in prof.items() if v[0]}
+        out[key] = res
+        A.destroy()
+    return out
+
+
 def run_gpu(args, wl):
     import torch
     world, rank, local = dist_env()
@@ -549,6 +598,7 @@ def run_gpu(args, wl):
         "cpu_baseline": base,
         "e2e": {"value": aggregate_value(prob.nnz, world, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": prob.N * esz, "d2h_bytes_per_step": prob.N * esz},
+        "adjoint": adjoint_report(iga, torch, dev, steps=5, warmup=3) if not args.no_adjoint else None,
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -569,9 +619,10 @@ def main(argv=None):
     ap.add_argument("--ref-rows", type=int, default=48, help="rows per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the CG solution-error report")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the kappa-gradient timing")
     ap.add_argument("--cg-tol", type=float, default=1e-10)
     ap.add_argument("--cg-maxit", type=int, default=20000)
-    ap.add_argument("--domains", choices=["common", "per_offset"], default="per_offset",
+    ap.add_argument("--domains", choices=["common", "per_offset"], default="common",
                     help="interpolation domains of the headline surrogate (the other is reported beside it)")
     ap.add_argument("--mode", choices=["both", "surrogate", "exact"], default="both",
                     help="profiling helper: time only one of the two steps and print a short line")

@@ -668,7 +668,7 @@ int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, co
     for (int d = 0; d < 3; ++d) {
         gx[d] = P(o_gx[d]); sx[d] = P(o_sx[d]); cx[d] = P(o_cx[d]); wq[d] = P(o_wq[d]);
         bv[d] = P(o_bv[d]); bd[d] = P(o_bd[d]); tdf[d] = reinterpret_cast<float2*>(P(o_tdf[d]));
-        T.gx[d] = gx[d]; T.wq[d] = wq[d]; T.bv[d] = bv[d]; T.bd[d] = bd[d];
+        T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.wq[d] = wq[d]; T.bv[d] = bv[d]; T.bd[d] = bd[d];
     }
     const char* stage = "basis tables";
     ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);

@@ -205,6 +205,8 @@ cudaError_t launch_spline_setup(const SplinePlan& sp, const SplineBufs& sb, cuda
 // ---- adjoint with respect to B-spline control values of kappa (k_adjoint.cu) ----
 struct AdjTables {
     const double* gx[3];      // [G] Gauss point coordinates
+    const double* sx[3];      // [G] sin(pi xi) (first G entries of the basis tables)
+    const double* cx[3];      // [G] cos(pi xi)
     const double* wq[3];      // [G] weights (times h)
     const double* bv[3];      // [G][p+1] values of the active basis functions
     const double* bd[3];      // [G][p+1] their derivatives

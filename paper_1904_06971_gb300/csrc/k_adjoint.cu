@@ -22,6 +22,7 @@
 // The basis tables are recomputed by every call; everything is FP64.
 #include <math_constants.h>
 
+#include "bspline3.cuh"
 #include "iga_internal.cuh"
 
 namespace iga {
@@ -56,33 +57,49 @@ __device__ void adj_geometry(const Geo& g, const double* xi, const double* s1, c
     } else {
         for (int a = 0; a < n; ++a) x[a] = xi[a];
     }
-    double inv[3][3], det;
+    // adjugate: J^{-1} = adj(J) / det, so G = |det| adj adj^T / det^2 = adj adj^T / |det|
+    double adj[3][3], det;
     if (n == 2) {
         det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-        inv[0][0] = J[1][1] / det; inv[0][1] = -J[0][1] / det;
-        inv[1][0] = -J[1][0] / det; inv[1][1] = J[0][0] / det;
+        adj[0][0] = J[1][1]; adj[0][1] = -J[0][1];
+        adj[1][0] = -J[1][0]; adj[1][1] = J[0][0];
     } else {
-        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-        det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-        inv[0][0] = c00 / det;
-        inv[1][0] = c01 / det;
-        inv[2][0] = c02 / det;
-        inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
-        inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
-        inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
-        inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
-        inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
-        inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+        adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
     }
-    const double ad = fabs(det);
+    const double rd = 1.0 / fabs(det);
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) {
             double v = 0.0;
-            for (int k = 0; k < n; ++k) v += inv[a][k] * inv[b][k];
-            G[a][b] = ad * v;
+            for (int k = 0; k < n; ++k) v += adj[a][k] * adj[b][k];
+            G[a][b] = rd * v;
         }
+}
+
+// physical point alone (no Jacobian)
+__device__ __forceinline__ void adj_point(const Geo& g, const double* xi, const double* s1, double* x)
+{
+    const int n = g.dim;
+    if (g.map_kind == IGA_MAP_SINPROD) {
+        double P = 1.0;
+        for (int d = 0; d < n; ++d) P *= s1[d];
+        for (int a = 0; a < n; ++a) x[a] = xi[a] + g.amp * P;
+    } else if (g.map_kind == IGA_MAP_AFFINE) {
+        for (int a = 0; a < n; ++a) {
+            x[a] = g.aff[9 + a];
+            for (int b = 0; b < n; ++b) x[a] += g.aff[a * 3 + b] * xi[b];
+        }
+    } else {
+        for (int a = 0; a < n; ++a) x[a] = xi[a];
+    }
 }
 
 __device__ __forceinline__ double quad_form(int n, const double G[3][3], const double* u, const double* v)
@@ -186,7 +203,8 @@ __global__ void k_adj_points(Geo g, AdjTables T, AdjTerms terms, double* spt)
     double w = 1.0;
     for (int d = 0; d < g.dim; ++d) {
         xi[d] = T.gx[d][gg[d]];
-        sincospi(xi[d], &s1[d], &c1[d]);
+        s1[d] = T.sx[d][gg[d]];
+        c1[d] = T.cx[d][gg[d]];
         w *= T.wq[d][gg[d]];
     }
     adj_geometry(g, xi, s1, c1, x, G);
@@ -342,7 +360,8 @@ __global__ void k_adj_samples(Geo g, AdjTables T, SplinePlan sp, const double* p
         double w = 1.0;
         for (int d = 0; d < n; ++d) {
             xi[d] = T.gx[d][gg[d]];
-            sincospi(xi[d], &s1[d], &c1[d]);
+            s1[d] = T.sx[d][gg[d]];
+            c1[d] = T.cx[d][gg[d]];
             w *= T.wq[d][gg[d]];
         }
         adj_geometry(g, xi, s1, c1, x, G);
@@ -377,119 +396,124 @@ __global__ void k_adj_samples(Geo g, AdjTables T, SplinePlan sp, const double* p
 }
 
 // ---------------------------------------------------------------------------
-// dL/dc_k = sum_g N_k(phi(g)) s(g).  One warp per element: its points' 4^n
-// contributions go to a shared window of 5^n control values around the smallest
-// span the warp touches (an element maps into at most two spans per direction
-// when its physical size is below the spline's), then to global memory with one
-// atomic per window entry.  Lanes whose span lies outside the window add directly.
+// dL/dc_k = sum_g N_k(phi(g)) s(g).  One warp per element.  An element maps into
+// at most two spans of the kappa spline per direction when its physical size is
+// below the spline's, so its contributions fall into a window of 5^n control
+// values starting at the smallest span its points touch.  The points' data
+// (s(g), the 4 basis values per direction, the span offsets) are staged in
+// shared memory 64 at a time; lane (kb, kc) then owns the window line
+// (0..4, kb, kc) and sums the contributions of all points into 5 registers, so
+// the element needs no atomics until one global atomic per window entry.
+// Points whose span falls outside the window add their contributions directly.
 // ---------------------------------------------------------------------------
 constexpr int kScatterWarps = 4;
-
-__device__ __forceinline__ double kcubic_knot(int j, int ne)
-{
-    return j <= 3 ? 0.0 : (j >= ne + 3 ? 1.0 : (double)(j - 3) / (double)ne);
-}
-__device__ void kcubic_basis(int ne, double x, int& first, double N[4])
-{
-    int e = (int)(x * ne);
-    e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
-    const int mu = e + 3;
-    double left[4], right[4];
-    N[0] = 1.0;
-    for (int k = 1; k <= 3; ++k) {
-        left[k] = x - kcubic_knot(mu + 1 - k, ne);
-        right[k] = kcubic_knot(mu + k, ne) - x;
-        double saved = 0.0;
-        for (int r = 0; r < k; ++r) {
-            const double tmp = N[r] / (right[r + 1] + left[k - r]);
-            N[r] = saved + right[r + 1] * tmp;
-            saved = left[k - r] * tmp;
-        }
-        N[k] = saved;
-    }
-    first = e;
-}
+constexpr int kStage = 64;
 
 __global__ void __launch_bounds__(32 * kScatterWarps) k_adj_scatter(Geo g, AdjTables T, const double* spt,
                                                                     double* grad)
 {
-    __shared__ double win[kScatterWarps][125];
+    __shared__ double sN[kScatterWarps][kStage][13];   // s(g) then N0[4], N1[4], N2[4]
+    __shared__ int sO[kScatterWarps][kStage];          // window offsets o0 + 4 o1 + 16 o2, or -1
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int p = g.p, Q = p + 1, n = g.dim;
     const int G0 = g.n_el[0] * Q, G1 = g.n_el[1] * Q;
     const int64_t nel = (int64_t)g.n_el[0] * g.n_el[1] * (n == 3 ? g.n_el[2] : 1);
-    int npt = 1, nwin = 1;
-    for (int d = 0; d < n; ++d) { npt *= Q; nwin *= 5; }
+    int npt = 1;
+    for (int d = 0; d < n; ++d) npt *= Q;
     const int n0 = g.knc[0], n1 = g.knc[1];
+    // the window line of this lane
+    const bool owner = (n == 3) ? lane < 25 : lane < 5;
+    const int kb = lane % 5, kc = (n == 3) ? lane / 5 : 0;
     for (int64_t el = (int64_t)blockIdx.x * kScatterWarps + wid; el < nel; el += (int64_t)gridDim.x * kScatterWarps) {
         const int e[3] = {(int)(el % g.n_el[0]), (int)((el / g.n_el[0]) % g.n_el[1]),
                           (int)(el / ((int64_t)g.n_el[0] * g.n_el[1]))};
-        for (int k = lane; k < nwin; k += 32) win[wid][k] = 0.0;
-        // pass 1: the smallest span per direction over the element's points
+        // smallest span per direction over the element's points
         int flo[3] = {1 << 30, 1 << 30, 1 << 30};
         for (int t = lane; t < npt; t += 32) {
             int rem = t;
-            double xi[3] = {0, 0, 0}, s1[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, x[3], G[3][3];
+            double xi[3] = {0, 0, 0}, s1[3] = {0, 0, 0}, x[3];
             for (int d = 0; d < n; ++d) {
                 const int gd = e[d] * Q + rem % Q;
                 rem /= Q;
                 xi[d] = T.gx[d][gd];
-                sincospi(xi[d], &s1[d], &c1[d]);
+                s1[d] = T.sx[d][gd];
             }
-            adj_geometry(g, xi, s1, c1, x, G);
+            adj_point(g, xi, s1, x);
             for (int d = 0; d < n; ++d) {
-                const double xd = fmin(fmax(x[d], 0.0), 1.0);
-                int f;
-                double N[4];
-                kcubic_basis(g.knc[d] - 3, xd, f, N);
+                const int ne = g.knc[d] - 3;
+                int f = (int)(fmin(fmax(x[d], 0.0), 1.0) * ne);
+                f = f > ne - 1 ? ne - 1 : f;
                 flo[d] = min(flo[d], f);
             }
         }
         for (int d = 0; d < n; ++d) flo[d] = __reduce_min_sync(0xffffffffu, flo[d]);
-        __syncwarp();
-        // pass 2: accumulate
-        for (int t = lane; t < npt; t += 32) {
-            int rem = t;
-            int gd[3] = {0, 0, 0};
-            double xi[3] = {0, 0, 0}, s1[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, x[3], G[3][3];
-            for (int d = 0; d < n; ++d) {
-                gd[d] = e[d] * Q + rem % Q;
-                rem /= Q;
-                xi[d] = T.gx[d][gd[d]];
-                sincospi(xi[d], &s1[d], &c1[d]);
-            }
-            adj_geometry(g, xi, s1, c1, x, G);
-            const double sv = spt[gd[0] + (int64_t)G0 * (gd[1] + (int64_t)G1 * gd[2])];
-            int f[3] = {0, 0, 0};
-            double N[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
-            bool inwin = true;
-            for (int d = 0; d < n; ++d) {
-                const double xd = fmin(fmax(x[d], 0.0), 1.0);
-                kcubic_basis(g.knc[d] - 3, xd, f[d], N[d]);
-                inwin = inwin && (f[d] - flo[d] <= 1);
-            }
-            const int cmax = (n == 3) ? 4 : 1;
-            for (int c = 0; c < cmax; ++c)
-                for (int b = 0; b < 4; ++b)
-                    for (int a = 0; a < 4; ++a) {
-                        const double val = sv * N[0][a] * N[1][b] * N[2][c];
-                        if (inwin) {
-                            const int k = (f[0] - flo[0] + a) + 5 * ((f[1] - flo[1] + b) + 5 * (n == 3 ? f[2] - flo[2] + c : 0));
-                            atomicAdd(&win[wid][k], val);
-                        } else {
-                            atomicAdd(grad + (f[0] + a) + (int64_t)n0 * ((f[1] + b) + (int64_t)n1 * (f[2] + c)), val);
-                        }
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int base = 0; base < npt; base += kStage) {
+            __syncwarp();
+            for (int tl = lane; tl < kStage; tl += 32) {
+                const int t = base + tl;
+                int o = -1;
+                if (t < npt) {
+                    int rem = t;
+                    int gd[3] = {0, 0, 0};
+                    double xi[3] = {0, 0, 0}, s1[3] = {0, 0, 0}, x[3];
+                    for (int d = 0; d < n; ++d) {
+                        gd[d] = e[d] * Q + rem % Q;
+                        rem /= Q;
+                        xi[d] = T.gx[d][gd[d]];
+                        s1[d] = T.sx[d][gd[d]];
                     }
+                    adj_point(g, xi, s1, x);
+                    const double sv = spt[gd[0] + (int64_t)G0 * (gd[1] + (int64_t)G1 * gd[2])];
+                    int f[3] = {0, 0, 0};
+                    double N[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
+                    bool inwin = true;
+                    for (int d = 0; d < n; ++d) {
+                        cubic_open_basis(g.knc[d] - 3, fmin(fmax(x[d], 0.0), 1.0), f[d], N[d]);
+                        inwin = inwin && (f[d] - flo[d] <= 1);
+                    }
+                    if (inwin) {
+                        o = (f[0] - flo[0]) + 4 * (f[1] - flo[1]) + 16 * (n == 3 ? f[2] - flo[2] : 0);
+                        sN[wid][tl][0] = sv;
+                        for (int d = 0; d < 3; ++d)
+                            for (int a = 0; a < 4; ++a) sN[wid][tl][1 + 4 * d + a] = N[d][a];
+                    } else {
+                        const int cmax = (n == 3) ? 4 : 1;
+                        for (int c = 0; c < cmax; ++c)
+                            for (int b = 0; b < 4; ++b)
+                                for (int a = 0; a < 4; ++a)
+                                    atomicAdd(grad + (f[0] + a) + (int64_t)n0 * ((f[1] + b) + (int64_t)n1 * (f[2] + c)),
+                                              sv * N[0][a] * N[1][b] * N[2][c]);
+                    }
+                }
+                sO[wid][tl] = o;
+            }
+            __syncwarp();
+            if (owner) {
+                const int cnt = min(kStage, npt - base);
+                for (int tl = 0; tl < cnt; ++tl) {
+                    const int o = sO[wid][tl];
+                    if (o < 0) continue;
+                    const int b = kb - ((o >> 2) & 3), c = kc - (o >> 4), o0 = o & 3;
+                    if (b < 0 || b > 3 || c < 0 || c > 3) continue;
+                    const double* D = sN[wid][tl];
+                    const double w = D[0] * D[5 + b] * D[9 + c];
+#pragma unroll
+                    for (int ka = 0; ka < 5; ++ka) {
+                        const int a = ka - o0;
+                        if (a >= 0 && a <= 3) acc[ka] += w * D[1 + a];
+                    }
+                }
+            }
         }
-        __syncwarp();
-        for (int k = lane; k < nwin; k += 32) {
-            const double v = win[wid][k];
-            const int a = k % 5, b = (k / 5) % 5, c = k / 25;
-            const int ka = flo[0] + a, kb = flo[1] + b, kc = (n == 3) ? flo[2] + c : 0;
-            if (v != 0.0 && ka < g.knc[0] && kb < g.knc[1] && (n == 2 || kc < g.knc[2]))
-                atomicAdd(grad + ka + (int64_t)n0 * (kb + (int64_t)n1 * kc), v);
+        if (owner) {
+            const int kbg = flo[1] + kb, kcg = (n == 3) ? flo[2] + kc : 0;
+            if (kbg < g.knc[1] && (n == 2 || kcg < g.knc[2]))
+                for (int ka = 0; ka < 5; ++ka) {
+                    const int kag = flo[0] + ka;
+                    if (acc[ka] != 0.0 && kag < g.knc[0]) atomicAdd(grad + kag + (int64_t)n0 * (kbg + (int64_t)n1 * kcg), acc[ka]);
+                }
         }
-        __syncwarp();
     }
 }
 

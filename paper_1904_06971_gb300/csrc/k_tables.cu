@@ -6,6 +6,7 @@
 
 #include "arith.cuh"
 #include "dfmath.cuh"
+#include "bspline3.cuh"
 #include "iga_internal.cuh"
 
 namespace iga {
@@ -224,34 +225,6 @@ cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
 // ([field][g2][g1][g0], g0 fastest).  Fields: 3-D C00 C01 C02 C11 C12 C22,
 // 2-D C00 C01 C11.
 // ---------------------------------------------------------------------------
-// The four cubic B-splines first..first+3 that are nonzero at x in [0, 1] on the
-// open uniform knot vector with ne elements (knots 0 x4, k/ne, 1 x4), by the
-// triangular Cox-de Boor recursion.
-__device__ __forceinline__ double cubic_knot(int j, int ne)
-{
-    return j <= 3 ? 0.0 : (j >= ne + 3 ? 1.0 : (double)(j - 3) / (double)ne);
-}
-__device__ void cubic_open_basis(int ne, double x, int& first, double N[4])
-{
-    int e = (int)(x * ne);
-    e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
-    const int mu = e + 3;
-    double left[4], right[4];
-    N[0] = 1.0;
-    for (int k = 1; k <= 3; ++k) {
-        left[k] = x - cubic_knot(mu + 1 - k, ne);
-        right[k] = cubic_knot(mu + k, ne) - x;
-        double saved = 0.0;
-        for (int r = 0; r < k; ++r) {
-            const double tmp = N[r] / (right[r + 1] + left[k - r]);
-            N[r] = saved + right[r + 1] * tmp;
-            saved = left[k - r] * tmp;
-        }
-        N[k] = saved;
-    }
-    first = e;
-}
-
 __device__ double kappa_at(const Geo& g, const double* x)
 {
     switch (g.kappa_kind) {
