@@ -146,3 +146,28 @@ def random_problem(rng: np.random.Generator, dim: int, p: int, n_el_range=(5, 12
                        kappa_kind="sin2d", kappa_a=1.0, kappa_b=float(rng.uniform(0, 0.5)))
     return Problem(dim=3, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp,
                    kappa_kind="expsin3d", kappa_b=float(rng.uniform(0, 0.5)))
+
+
+def batch_items(n2d: int = 192, n3d: int = 64, seed: int = 0):
+    """The batching workload: n2d 2-D patches (p in 2..5, 16..256 elements per direction)
+    and n3d 3-D patches (p in 2..4, 8..48 elements per direction), uniform random; each
+    with its own sine-product map (amplitude U[0, 0.05]) and coefficient (2-D:
+    1 + b sin sin, 3-D: exp(b sin cos sin), b ~ U[0, 0.5]); M in {4, 8}, q = 3.
+    Returns a list of (Problem, M, q)."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for k in range(n2d + n3d):
+        if k < n2d:
+            p = int(rng.integers(2, 6))
+            n_el = tuple(int(rng.integers(16, 257)) for _ in range(2))
+            amp, b = float(rng.uniform(0.0, 0.05)), float(rng.uniform(0.0, 0.5))
+            prob = Problem(dim=2, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp, kappa_kind="sin2d",
+                           kappa_a=1.0, kappa_b=b)
+        else:
+            p = int(rng.integers(2, 5))
+            n_el = tuple(int(rng.integers(8, 49)) for _ in range(3))
+            amp, b = float(rng.uniform(0.0, 0.05)), float(rng.uniform(0.0, 0.5))
+            prob = Problem(dim=3, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp, kappa_kind="expsin3d", kappa_b=b)
+        M = int(rng.choice([4, 8]))
+        items.append((prob, M, 3))
+    return items

@@ -196,6 +196,42 @@ int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, co
                        int M, int q, const double* ybar, const double* x, double* grad, void* stream);
 
 /*
+ * Batched assembly (no counterpart in the paper, which assembles one patch):
+ * many patches of uneven size, degree, map and coefficient as one CUDA graph.
+ * Item k is assembled like iga_assemble_surrogate_domains (M >= 1) or
+ * iga_assemble_exact (M = 0) into A[k].
+ *   First call with any A[k] == NULL: every matrix is created by an eager
+ *   assembly on `stream` (handles returned in A).  Calls with all handles set:
+ *   the batch (descriptions, handles, dtype and contraction arithmetic) is
+ *   looked up in a graph cache; on a miss the kernel chains of all patches are
+ *   captured on B concurrent branches (B = 1, 2, 4, ..., 32 tried, the fastest of
+ *   two timed replays kept -- this first graph call synchronises), on a hit the
+ *   cached graph is launched on `stream` as one graph launch.  Device pointers in
+ *   the descriptions (IGA_KAPPA_BSPLINE3 control values) are captured by address.
+ *   Errors: IGA_EINVAL for n < 1, null arrays or a bad dtype; item errors as for
+ *   the single-patch calls.
+ */
+typedef struct {
+    iga_patch_t patch;
+    int32_t p;
+    iga_map_t map;
+    iga_kappa_t kappa;
+    int32_t M;          /* >= 1: surrogate with sampling parameter M; 0: exact matrix */
+    int32_t q;          /* interpolation degree (surrogate) */
+    int32_t domains;    /* IGA_DOMAINS_* (surrogate) */
+} iga_batch_item_t;
+
+int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* stream, iga_matrix_t* A);
+
+/* The calling thread's last iga_assemble_batch: concurrent branches of its graph
+ * (0 for the eager first call), kernels per replay, 1 if the graph came from the
+ * cache, and the tuned replay time in ms (0 unless a graph was tuned). */
+int iga_batch_info(int* branches, int64_t* kernels, int* cached, float* tuned_ms);
+
+/* Destroys every cached batch graph. */
+int iga_batch_release(void);
+
+/*
  * y = A x (eq. DiscreteVariationalProblems), stencil SpMV.  x and y are
  * caller-owned DEVICE arrays of N elements of the matrix dtype (double for
  * IGA_F64, float for IGA_F32); x and y must not overlap.

@@ -53,6 +53,11 @@ class Kappa(ctypes.Structure):
                 ("ctrl", ctypes.c_void_p)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("patch", Patch), ("p", ctypes.c_int32), ("map", Map), ("kappa", Kappa), ("M", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("domains", ctypes.c_int32)]
+
+
 def load():
     """Build (if stale) and load the in-tree libiga.so."""
     global _lib
@@ -75,6 +80,10 @@ def load():
                                                      ctypes.c_int, vp, ctypes.POINTER(H)]
         L.iga_kappa_gradient.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                          ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+        L.iga_assemble_batch.argtypes = [ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int, vp,
+                                         ctypes.POINTER(H)]
+        L.iga_batch_info.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_float)]
         L.iga_apply.argtypes = [H, vp, vp, vp]
         L.iga_apply_host.argtypes = [H, vp, vp, vp]
         L.iga_matrix_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
@@ -373,3 +382,37 @@ def stiffness_apply(ctrl, x, prob, M: int = 0, q: int = 3):
     if _STIFFNESS_APPLY is None:
         _STIFFNESS_APPLY = _stiffness_apply_function()
     return _STIFFNESS_APPLY.apply(ctrl, x, prob, M, q)
+
+
+def assemble_batch(items, dtype="f32", stream=None, out=None):
+    """Assemble many patches as one CUDA graph (iga_assemble_batch).
+
+    items: sequence of (problem, M, q) or (problem, M, q, domains); M = 0 is the exact
+    matrix.  The first call (out=None) creates the matrices eagerly; passing the returned
+    list back as `out` replays a cached, autotuned graph of the whole batch."""
+    n = len(items)
+    arr = (BatchItem * n)()
+    keep = []
+    for k, it in enumerate(items):
+        prob, M, q = it[0], int(it[1]), int(it[2])
+        dom = it[3] if len(it) > 3 else "common"
+        pt, mp, kp = _structs(prob)
+        arr[k].patch, arr[k].p, arr[k].map, arr[k].kappa = pt, int(prob.p), mp, kp
+        arr[k].M, arr[k].q, arr[k].domains = M, q, DOMAINS[dom]
+        keep.append(kp)
+    H = ctypes.c_void_p * n
+    handles = H(*[(m.handle.value if out is not None else None) for m in (out or [None] * n)])
+    _check(load().iga_assemble_batch(n, arr, _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)), handles))
+    if out is not None:
+        return out
+    mats = [Matrix(h) for h in handles]
+    for m, kp in zip(mats, keep):
+        _keep(m, kp)
+    return mats
+
+
+def batch_info():
+    """(branches, kernels per replay, from cache, tuned replay ms) of this thread's last batch call."""
+    b, k, c, ms = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_float()
+    _check(load().iga_batch_info(ctypes.byref(b), ctypes.byref(k), ctypes.byref(c), ctypes.byref(ms)))
+    return b.value, k.value, bool(c.value), ms.value

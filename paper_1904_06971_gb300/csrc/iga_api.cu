@@ -55,6 +55,7 @@ struct Pending { int kid; cudaEvent_t a, b; };
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_events;
 thread_local cudaEvent_t t_begin = nullptr;
+thread_local bool t_capture = false;        // inside a graph capture: no profiling events
 
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
                              "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg",
@@ -464,7 +465,9 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         return cuda_fail(ce, "creating the memory pool");
     }
     double* scratch = nullptr;
-    ce = cudaMallocFromPoolAsync((void**)&scratch, (size_t)lay.total * sizeof(double), pool, st);
+    // inside a graph capture the allocation becomes a graph memory node (default pool)
+    ce = t_capture ? cudaMallocAsync((void**)&scratch, (size_t)lay.total * sizeof(double), st)
+                   : cudaMallocFromPoolAsync((void**)&scratch, (size_t)lay.total * sizeof(double), pool, st);
     if (ce != cudaSuccess) {
         if (created) { cudaFree(A->values); delete A; }
         return cuda_fail(ce, "allocating scratch");
@@ -524,7 +527,7 @@ void launch_begin(int kid, cudaStream_t s)
 {
     (void)kid;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (g_profile.load(std::memory_order_relaxed)) {
+    if (g_profile.load(std::memory_order_relaxed) && !t_capture) {
         t_begin = take_event();
         if (t_begin) cudaEventRecord(t_begin, s);
     } else {
@@ -563,6 +566,18 @@ int report_error(int code, const char* msg)
 {
     t_err = msg ? msg : "";
     return code;
+}
+
+void set_capture(bool on) { t_capture = on; }
+
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int64_t launch_count() { return g_launches.load(); }
+
+int assemble_patch(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
+                   int M, int q, int domains, int dtype, void* stream, iga_matrix_t* out)
+{
+    return assemble(patch, p, map, kappa, surrogate, M, q, domains, dtype, stream, out);
 }
 
 void launch_end(int kid, cudaStream_t s)

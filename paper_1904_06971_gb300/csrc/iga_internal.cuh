@@ -133,6 +133,15 @@ void launch_end(int kid, cudaStream_t s);
 // Sets the calling thread's iga_last_error() message; returns code.
 int report_error(int code, const char* msg);
 
+// Graph capture support (iga_batch.cu): no profiling events while capturing,
+// and replays of a captured graph add its kernel count to the launch counter.
+void set_capture(bool on);
+void add_launches(int64_t n);
+int64_t launch_count();
+// One patch through the exact (surrogate = false) or surrogate pipeline on `stream`.
+int assemble_patch(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
+                   int M, int q, int domains, int dtype, void* stream, iga_matrix_t* out);
+
 // Contraction arithmetic (arith.cuh kind) chosen for matrices of value type dtype.
 int current_arith(int dtype);
 

@@ -126,3 +126,17 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["unit"] == "nnz/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"] == W.CFG_2D_P2.name
+
+
+def test_batch_workload_recipe():
+    items = W.batch_items()
+    assert len(items) == 256
+    d2 = [p for p, M, q in items if p.dim == 2]
+    d3 = [p for p, M, q in items if p.dim == 3]
+    assert len(d2) == 192 and len(d3) == 64
+    assert all(2 <= p.p <= 5 and all(16 <= n <= 256 for n in p.n_el) for p in d2)
+    assert all(2 <= p.p <= 4 and all(8 <= n <= 48 for n in p.n_el) for p in d3)
+    assert all(0.0 <= p.map_amp <= 0.05 for p in d2 + d3)
+    assert {M for _, M, _ in items} == {4, 8} and {q for _, _, q in items} == {3}
+    again = W.batch_items()
+    assert again == items
