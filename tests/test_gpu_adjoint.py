@@ -138,3 +138,36 @@ def test_autograd_function(iga):
     S = oracle.surrogate_matrix(prob, M, q)
     ref_x = oracle.apply(S, prob, w.cpu().numpy())              # A~^T w = A~ w
     assert np.abs(gx.cpu().numpy() - ref_x).max() <= 1e-12 * np.abs(S).max() * np.abs(w.cpu().numpy()).max() * prob.S
+
+
+@pytest.mark.parametrize("M", [8, 0])
+def test_autograd_half_norm_loss_directional_fd(iga, M):
+    """L = 0.5 y^T y with y = A~(c) x through the autograd wrapper, on the 48^3 p = 3
+    workload with 16^3 control values: the gradient agrees with central differences
+    (h = 1e-6, FP64) along 32 random directions in (c, x) to 1e-6 relative, plus the
+    rounding of the difference quotient itself, 8 eps |L| / (2h) (L is a quartic
+    polynomial along the line, so the truncation error is O(h^2) and negligible)."""
+    wl = W.CFG_3D_P3_BSPLINE
+    prob = wl.problem
+    rng = np.random.default_rng(31)
+    c0 = torch.tensor(prob.kappa_ctrl, dtype=torch.float64, device="cuda")
+    x0 = torch.from_numpy(rng.standard_normal(prob.N)).cuda()
+    c = c0.clone().requires_grad_(True)
+    x = x0.clone().requires_grad_(True)
+    y = iga.stiffness_apply(c, x, prob, M, wl.q)
+    L = 0.5 * torch.dot(y, y)
+    gc, gx = torch.autograd.grad(L, (c, x))
+
+    def loss(cc, xx):
+        with torch.no_grad():
+            yy = iga.stiffness_apply(cc, xx, prob, M, wl.q)
+            return 0.5 * torch.dot(yy, yy).item()
+
+    h = 1e-6
+    fd_round = 8 * np.finfo(np.float64).eps * abs(L.item()) / (2 * h)
+    for _ in range(32):
+        dc = torch.from_numpy(rng.standard_normal(c0.numel())).cuda()
+        dx = torch.from_numpy(rng.standard_normal(prob.N)).cuda()
+        fd = (loss(c0 + h * dc, x0 + h * dx) - loss(c0 - h * dc, x0 - h * dx)) / (2 * h)
+        an = (torch.dot(gc, dc) + torch.dot(gx, dx)).item()
+        assert abs(fd - an) <= 1e-6 * abs(an) + fd_round, (fd, an, fd_round)
