@@ -626,8 +626,12 @@ def run_gpu(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_s_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": wl.dtype, "arith": {"contractions": arith, "coefficients": "fp64",
-                                                         "fill": "df64", "spmv": wl.dtype},
+        "vs_baseline": None, "dtype": wl.dtype,
+        "arith": {"contractions": arith,
+                  "coefficients": (arith if prob.map_kind == "sinprod" and prob.kappa_kind in ("const", "sin2d", "expsin3d")
+                                   else "fp64"),
+                  "fill": "df64" if wl.dtype == "f64" else "fp32", "diagonal": "fp64" if wl.dtype == "f64" else
+                  "compensated fp32", "spmv": wl.dtype},
         "data": "synthetic (seeded map/coefficient family, x ~ N(0,1))",
         "config": config_of(wl, world, primary),
         "exact": {"value": exact_value, "unit": UNIT, "ms_per_step": ms_e_max,

@@ -109,7 +109,14 @@ CFG_3D_P3_BSPLINE = Workload(
             kappa_kind="bspline3", kappa_nctrl=(16, 16, 16), kappa_ctrl=lognormal_ctrl((16, 16, 16), seed=0)),
     M=8, q=3, dtype="f64")
 
-WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4, CFG_3D_P3_40, CFG_3D_P3_BSPLINE)}
+# Smaller member of the p = 4 FP32 family for profiler captures (values 410 MB > L2).
+CFG_3D_P4_48 = Workload(
+    "3d_p4_48cube_M8_q3_f32",
+    Problem(dim=3, p=4, n_el=(48, 48, 48), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="expsin3d", kappa_b=0.5),
+    M=8, q=3, dtype="f32")
+
+WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4, CFG_3D_P3_40, CFG_3D_P3_BSPLINE, CFG_3D_P4_48)}
 
 
 def scaled(w: Workload, n_el: Tuple[int, ...], M: Optional[int] = None, p: Optional[int] = None) -> Workload:

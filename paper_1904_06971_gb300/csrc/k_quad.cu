@@ -73,7 +73,7 @@ __device__ __forceinline__ void load_run(const S* p, S* v)
 // keep the accumulators of one thread small enough for two blocks per SM).
 // ---------------------------------------------------------------------------
 template <class Pol, int P, int HALF>
-__global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, double* scratch)
+__device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
@@ -102,6 +102,32 @@ __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, 
     for (int a = 0; a <= P; ++a) {
         const int e3 = i3 - P + a;
         if (e3 < b.elo[2] || e3 >= b.elo[2] + b.E[2]) continue;
+        if constexpr (Pol::kind == kArithF32) {
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            const int t = a * Q + r;
+            const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + r) * plane + pp;
+            S c0, c1, c2, c3;
+            if (HALF == 0) { c0 = C[o]; c1 = C[fs + o]; c2 = C[3 * fs + o]; c3 = C[2 * fs + o]; }
+            else { c0 = C[2 * fs + o]; c1 = C[4 * fs + o]; c2 = C[5 * fs + o]; c3 = c0; }
+#pragma unroll
+            for (int dd = a; dd <= a + P; ++dd) {
+                S x00, x01, x10, x11;
+                load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+                if (HALF == 0) {
+                    Pol::mac(acc[dd][0], x00, c0);   // (K00, 00)
+                    Pol::mac(acc[dd][1], x00, c1);   // (K01, 00)
+                    Pol::mac(acc[dd][2], x00, c2);   // (K11, 00)
+                    Pol::mac(acc[dd][3], x01, c3);   // (K02, 01)
+                } else {
+                    Pol::mac(acc[dd][0], x10, c0);   // (K02, 10)
+                    Pol::mac(acc[dd][1], x01, c1);   // (K12, 01)
+                    Pol::mac(acc[dd][2], x10, c1);   // (K12, 10)
+                    Pol::mac(acc[dd][3], x11, c2);   // (K22, 11)
+                }
+            }
+        }
+        } else {
 #pragma unroll 1
         for (int r = 0; r < Q; ++r) {
             const int t = a * Q + r;
@@ -126,6 +152,7 @@ __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, 
                 }
             }
         }
+        }
     }
     S* T1 = reinterpret_cast<S*>(scratch + b.t1_off);
     const int64_t P3 = (int64_t)b.R[2] * W;
@@ -136,11 +163,26 @@ __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, 
             T1[((int64_t)(4 * HALF + k) * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
 }
 
+// FP32 contractions get their own entry points: the Gauss-point loop unrolled
+// (short bodies, several points' loads in flight) and three resident blocks per
+// SM; the double-float and FP64 bodies are long and keep the rolled loop and the
+// compiler's register choice.
+template <class Pol, int P, int HALF>
+__global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, double* scratch)
+{
+    stage_z_body<Pol, P, HALF>(g, T, bs, scratch);
+}
+template <int P, int HALF>
+__global__ void __launch_bounds__(kBlock, 3) k_stage_z_f32(Geo g, Tables T, BoxSet bs, double* scratch)
+{
+    stage_z_body<PolF32, P, HALF>(g, T, bs, scratch);
+}
+
 // ---------------------------------------------------------------------------
 // stage Y: contract direction 1
 // ---------------------------------------------------------------------------
 template <class Pol, int P, int DIM>
-__global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, double* scratch)
+__device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
@@ -180,6 +222,37 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
     for (int a = 0; a <= P; ++a) {
         const int e2 = i2 - P + a;
         if (e2 < b.elo[1] || e2 >= b.elo[1] + b.E[1]) continue;
+        if constexpr (Pol::kind == kArithF32) {
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            const int t = a * Q + r;
+            const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + r) * G0;
+            S v[NIN];
+#pragma unroll
+            for (int f = 0; f < NIN; ++f) v[f] = in[f * fstride + o];
+#pragma unroll
+            for (int dd = a; dd <= a + P; ++dd) {
+                S x00, x01, x10, x11;
+                load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+                if (DIM == 3) {
+                    Pol::mac(acc[dd][0], x00, v[0]);   // A^00 -> group 0 (11 left in direction 0)
+                    Pol::mac(acc[dd][1], x01, v[1]);   // A^01 -> group 1 (10)
+                    Pol::mac(acc[dd][1], x00, v[3]);   // A^02 -> group 1
+                    Pol::mac(acc[dd][2], x10, v[1]);   // A^10 -> group 2 (01)
+                    Pol::mac(acc[dd][2], x00, v[4]);   // A^20 -> group 2
+                    Pol::mac(acc[dd][3], x11, v[2]);   // A^11 -> group 3 (00)
+                    Pol::mac(acc[dd][3], x10, v[5]);   // A^12 -> group 3
+                    Pol::mac(acc[dd][3], x01, v[6]);   // A^21 -> group 3
+                    Pol::mac(acc[dd][3], x00, v[7]);   // A^22 -> group 3
+                } else {
+                    Pol::mac(acc[dd][0], x00, v[0]);   // A^00: K00, 00
+                    Pol::mac(acc[dd][1], x01, v[1]);   // A^01: K01, 01
+                    Pol::mac(acc[dd][2], x10, v[1]);   // A^10: K01, 10
+                    Pol::mac(acc[dd][3], x11, v[2]);   // A^11: K11, 11
+                }
+            }
+        }
+        } else {
 #pragma unroll 1
         for (int r = 0; r < Q; ++r) {
             const int t = a * Q + r;
@@ -209,6 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
                 }
             }
         }
+        }
     }
     S* T2 = reinterpret_cast<S*>(scratch + b.t2_off);
     const int64_t P2 = (int64_t)R2 * W;
@@ -217,6 +291,17 @@ __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, 
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
             T2[(((int64_t)k * P3 + pair3) * P2 + (int64_t)i2l * W + dd) * G0 + g0] = Pol::to_store(acc[dd][k]);
+}
+
+template <class Pol, int P, int DIM>
+__global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, double* scratch)
+{
+    stage_y_body<Pol, P, DIM>(g, T, bs, scratch);
+}
+template <int P, int DIM>
+__global__ void __launch_bounds__(kBlock, 3) k_stage_y_f32(Geo g, Tables T, BoxSet bs, double* scratch)
+{
+    stage_y_body<PolF32, P, DIM>(g, T, bs, scratch);
 }
 
 // ---------------------------------------------------------------------------
@@ -334,15 +419,18 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
     if (g.dim == 3) {
         if (nb[1] > 0) {
             launch_begin(K_STAGE_Z, s);
-            k_stage_z<Pol, P, 0><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            if constexpr (Pol::kind == kArithF32) k_stage_z_f32<P, 0><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            else k_stage_z<Pol, P, 0><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Z, s);
             launch_begin(K_STAGE_Z, s);
-            k_stage_z<Pol, P, 1><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            if constexpr (Pol::kind == kArithF32) k_stage_z_f32<P, 1><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
+            else k_stage_z<Pol, P, 1><<<(unsigned)nb[1], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Z, s);
         }
         if (nb[2] > 0) {
             launch_begin(K_STAGE_Y, s);
-            k_stage_y<Pol, P, 3><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
+            if constexpr (Pol::kind == kArithF32) k_stage_y_f32<P, 3><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
+            else k_stage_y<Pol, P, 3><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Y, s);
         }
         if (nb[3] > 0) {
@@ -353,7 +441,8 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
     } else {
         if (nb[2] > 0) {
             launch_begin(K_STAGE_Y, s);
-            k_stage_y<Pol, P, 2><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
+            if constexpr (Pol::kind == kArithF32) k_stage_y_f32<P, 2><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
+            else k_stage_y<Pol, P, 2><<<(unsigned)nb[2], kBlock, 0, s>>>(g, T, bs, scratch);
             launch_end(K_STAGE_Y, s);
         }
         if (nb[3] > 0) {

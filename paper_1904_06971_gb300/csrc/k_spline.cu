@@ -346,9 +346,17 @@ __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, SplineBuf
             const float2* Pp = sb.partial + (((int64_t)u * L2x + x2) * L1x + x1) * nu0 + sb.espan[0][v0][x0];
             const float2* E = sb.eval0[v0] + x0;
             const int L0v = sp.L[0][v0];
-            DFAcc acc = PolDF::zero();
-            for (int k = 0; k <= sp.qe[0][v0]; ++k) PolDF::mac(acc, E[(int64_t)k * L0v], Pp[k]);
-            out = from_df<T>(acc);
+            if constexpr (sizeof(T) == 4) {
+                // FP32 values: the hi parts in FP32 (the B-spline weights are a partition of
+                // unity, so the sum has no cancellation beyond the FP32 rounding of the value)
+                float acc = 0.f;
+                for (int k = 0; k <= sp.qe[0][v0]; ++k) acc = __fmaf_rn(E[(int64_t)k * L0v].x, Pp[k].x, acc);
+                out = acc;
+            } else {
+                DFAcc acc = PolDF::zero();
+                for (int k = 0; k <= sp.qe[0][v0]; ++k) PolDF::mac(acc, E[(int64_t)k * L0v], Pp[k]);
+                out = from_df<T>(acc);
+            }
         } else {
             const int64_t jrow = j0 + (int64_t)m0 * (j1 + (int64_t)m1 * j2);
             out = vals[(int64_t)(S - 1 - s) * N + jrow];
@@ -357,10 +365,100 @@ __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, SplineBuf
     }
 }
 
+// Pass 1 for the common domain Omega~, where every variant shares the tables of
+// variant P: the same mapping as k_fill with those tables held in registers, the
+// direction-0 evaluation row of the upper slots loaded once per thread, and the
+// Q1 = q_eff + 1 <= 4 terms of the evaluation unrolled.
+template <int P, int DIM, typename T, int Q1>
+__global__ void __launch_bounds__(kBlock) k_fill_common(Geo g, SplinePlan sp, SplineBufs sb, T* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    constexpr int NPAIR = (DIM == 3) ? W * W : W;
+    const int R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
+    const int R2 = (DIM == 3) ? sp.r1[2] - sp.r0[2] + 1 : 1;
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= (int64_t)R0 * R1 * R2 * NPAIR) return;
+    const int x0 = (int)(item % R0);
+    int64_t rest = item / R0;
+    const int pr = (int)(rest % NPAIR);
+    rest /= NPAIR;
+    const int x1 = (int)(rest % R1);
+    const int x2 = (int)(rest / R1);
+    const int d1 = pr % W, d2 = (DIM == 3) ? pr / W : P;
+    const int m0 = g.m[0], m1 = g.m[1];
+    const int64_t N = (int64_t)m0 * m1 * ((DIM == 3) ? g.m[2] : 1);
+    const int i0 = sp.r0[0] + x0, i1 = sp.r0[1] + x1, i2 = (DIM == 3) ? sp.r0[2] + x2 : 0;
+    const int64_t i = i0 + (int64_t)m0 * (i1 + (int64_t)m1 * i2);
+    const int y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;        // box indices of j in directions 1, 2
+    const bool in12 = (y1 >= 0 && y1 < R1) && (y2 >= 0 && y2 < R2);
+    const int L0 = sp.L[0][P], L1x = sp.Lmax[1], L2x = (DIM == 3) ? sp.Lmax[2] : 1, nu0 = sp.nu[0];
+    const int* esp0 = sb.espan[0][P];
+    const float2* ev0 = sb.eval0[P];
+    float2 Eu[Q1];
+#pragma unroll
+    for (int k = 0; k < Q1; ++k) Eu[k] = ev0[(int64_t)k * L0 + x0];
+    const int su = esp0[x0];
+    const int sbase = W * (d1 + W * ((DIM == 3) ? d2 : 0));
+    const int64_t up_row = ((int64_t)x2 * L1x + x1) * nu0 + su;      // within one slot's partial field
+    const int64_t lo_row = ((int64_t)y2 * L1x + y1) * nu0;
+    const int64_t slot_stride = (int64_t)L2x * L1x * nu0;
+#pragma unroll
+    for (int d0 = 0; d0 < W; ++d0) {
+        const int s = sbase + d0;
+        if (s == C) continue;
+        const int y0 = x0 + d0 - P;
+        T out;
+        if (in12 && y0 >= 0 && y0 < R0) {
+            const float2* Pp;
+            float2 E[Q1];
+            if (s > C) {            // Phi~_delta at x~_i
+                Pp = sb.partial + (int64_t)(s - C - 1) * slot_stride + up_row;
+#pragma unroll
+                for (int k = 0; k < Q1; ++k) E[k] = Eu[k];
+            } else {                // Phi~_{-delta} at x~_j
+                Pp = sb.partial + (int64_t)(S - 1 - s - C - 1) * slot_stride + lo_row + esp0[y0];
+#pragma unroll
+                for (int k = 0; k < Q1; ++k) E[k] = ev0[(int64_t)k * L0 + y0];
+            }
+            if constexpr (sizeof(T) == 4) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < Q1; ++k) acc = __fmaf_rn(E[k].x, Pp[k].x, acc);
+                out = acc;
+            } else {
+                DFAcc acc = PolDF::zero();
+#pragma unroll
+                for (int k = 0; k < Q1; ++k) PolDF::mac(acc, E[k], Pp[k]);
+                out = from_df<T>(acc);
+            }
+        } else {
+            const int64_t jrow = (i0 + d0 - P) + (int64_t)m0 * ((i1 + d1 - P) + (int64_t)m1 * (i2 + d2 - P));
+            out = vals[(int64_t)(S - 1 - s) * N + jrow];
+        }
+        vals[(int64_t)s * N + i] = out;
+    }
+}
+
+template <int P, int DIM, typename T>
+static bool fill_common_q(const Geo& g, const SplinePlan& sp, const SplineBufs& sb, T* vals, unsigned grid,
+                          cudaStream_t s)
+{
+    switch (sp.qe[0][P] + 1) {
+    case 1: k_fill_common<P, DIM, T, 1><<<grid, kBlock, 0, s>>>(g, sp, sb, vals); return true;
+    case 2: k_fill_common<P, DIM, T, 2><<<grid, kBlock, 0, s>>>(g, sp, sb, vals); return true;
+    case 3: k_fill_common<P, DIM, T, 3><<<grid, kBlock, 0, s>>>(g, sp, sb, vals); return true;
+    case 4: k_fill_common<P, DIM, T, 4><<<grid, kBlock, 0, s>>>(g, sp, sb, vals); return true;
+    default: return false;      // q > 3: the general kernel
+    }
+}
+
 // Pass 2 (every row): the kernel-preserving diagonal, minus the sum of the
-// row's stored off-diagonal values.  The sum is FP64, whose rounding stays
-// ~1e-15 of the row's mass even for 1330 terms (a double-float sum would lose
-// ~1e-12).
+// row's stored off-diagonal values.  For FP64 values the sum is FP64, whose
+// rounding stays ~1e-15 of the row's mass even for 1330 terms (a double-float sum
+// with the contractions' cheap accumulation lost ~1e-12); for FP32 values a
+// compensated FP32 sum is far more accurate than the FP32 result.
 template <int P, int DIM, typename T>
 __global__ void __launch_bounds__(kBlock) k_diag(int64_t N, T* vals)
 {
@@ -369,12 +467,30 @@ __global__ void __launch_bounds__(kBlock) k_diag(int64_t N, T* vals)
     constexpr int C = (S - 1) / 2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    // four interleaved partial sums keep more loads in flight; combined in a fixed order
-    double part[4] = {0.0, 0.0, 0.0, 0.0};
+    if constexpr (sizeof(T) == 4) {
+        // FP32 values: two compensated FP32 sums (Knuth two-sum per term; the error
+        // terms collected in a second float) on the FP32 pipe; far below the rounding
+        // of the FP32 result
+        float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
 #pragma unroll 4
-    for (int s = 0; s < S; ++s)
-        if (s != C) part[s & 3] += (double)vals[(int64_t)s * N + i];
-    vals[(int64_t)C * N + i] = (T)(-((part[0] + part[1]) + (part[2] + part[3])));
+        for (int s = 0; s < S; ++s) {
+            if (s == C) continue;
+            const float v = (float)vals[(int64_t)s * N + i];
+            const int k = s & 1;
+            const float t = __fadd_rn(hi[k], v);
+            const float z = __fsub_rn(t, hi[k]);
+            lo[k] = __fadd_rn(lo[k], __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(v, z)));
+            hi[k] = t;
+        }
+        vals[(int64_t)C * N + i] = (T)(-((double)hi[0] + (double)hi[1] + ((double)lo[0] + (double)lo[1])));
+    } else {
+        // four interleaved partial sums keep more loads in flight; combined in a fixed order
+        double part[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int s = 0; s < S; ++s)
+            if (s != C) part[s & 3] += (double)vals[(int64_t)s * N + i];
+        vals[(int64_t)C * N + i] = (T)(-((part[0] + part[1]) + (part[2] + part[3])));
+    }
 }
 
 template <int P>
@@ -389,12 +505,21 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
         const int64_t total = R0 * R1 * (g.dim == 3 ? (int64_t)(sp.r1[2] - sp.r0[2] + 1) * W * W : W);
         const unsigned gfill = (unsigned)((total + kBlock - 1) / kBlock);
         launch_begin(K_FILL, s);
-        if (g.dim == 3) {
-            if (f32) k_fill<P, 3, float><<<gfill, kBlock, 0, s>>>(g, sp, sb, (float*)ell);
-            else k_fill<P, 3, double><<<gfill, kBlock, 0, s>>>(g, sp, sb, (double*)ell);
-        } else {
-            if (f32) k_fill<P, 2, float><<<gfill, kBlock, 0, s>>>(g, sp, sb, (float*)ell);
-            else k_fill<P, 2, double><<<gfill, kBlock, 0, s>>>(g, sp, sb, (double*)ell);
+        bool done = false;
+        if (sp.all) {
+            if (g.dim == 3) done = f32 ? fill_common_q<P, 3, float>(g, sp, sb, (float*)ell, gfill, s)
+                                       : fill_common_q<P, 3, double>(g, sp, sb, (double*)ell, gfill, s);
+            else done = f32 ? fill_common_q<P, 2, float>(g, sp, sb, (float*)ell, gfill, s)
+                            : fill_common_q<P, 2, double>(g, sp, sb, (double*)ell, gfill, s);
+        }
+        if (!done) {
+            if (g.dim == 3) {
+                if (f32) k_fill<P, 3, float><<<gfill, kBlock, 0, s>>>(g, sp, sb, (float*)ell);
+                else k_fill<P, 3, double><<<gfill, kBlock, 0, s>>>(g, sp, sb, (double*)ell);
+            } else {
+                if (f32) k_fill<P, 2, float><<<gfill, kBlock, 0, s>>>(g, sp, sb, (float*)ell);
+                else k_fill<P, 2, double><<<gfill, kBlock, 0, s>>>(g, sp, sb, (double*)ell);
+            }
         }
         launch_end(K_FILL, s);
     }

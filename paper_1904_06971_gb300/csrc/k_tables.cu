@@ -293,6 +293,57 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
         xi[d] = T.gx[d][gg[d]];
     }
     typename Pol::store* out = reinterpret_cast<typename Pol::store*>(scratch + b.c_off);
+    if (Pol::kind == kArithF32 && g.coef_df) {
+        // FP32 contractions: the same formulas in FP32 (the hi parts of the
+        // double-float tables), whose rounding is of the order of the FP32
+        // contractions' own.
+        float sv[3], pcv[3], S2[3], C2[3];
+        for (int d = 0; d < DIM; ++d) {
+            const float2* t4 = T.tdf[d] + 4 * gg[d];
+            sv[d] = t4[0].x; pcv[d] = t4[1].x; S2[d] = t4[2].x; C2[d] = t4[3].x;
+        }
+        float gr[3], P;
+        if (DIM == 3) {
+            gr[0] = pcv[0] * (sv[1] * sv[2]);
+            gr[1] = pcv[1] * (sv[0] * sv[2]);
+            gr[2] = pcv[2] * (sv[0] * sv[1]);
+            P = sv[0] * (sv[1] * sv[2]);
+        } else {
+            gr[0] = pcv[0] * sv[1];
+            gr[1] = pcv[1] * sv[0];
+            gr[2] = 0.f;
+            P = sv[0] * sv[1];
+        }
+        float gsum = 0.f, gg2 = 0.f;
+        for (int d = 0; d < DIM; ++d) { gsum += gr[d]; gg2 = fmaf(gr[d], gr[d], gg2); }
+        const float amp = g.amp_df[0];
+        const float det = fmaf(amp, gsum, 1.f);
+        const float cc = amp / det;
+        const float c2g = cc * cc * gg2;
+        float kap = g.ka_df[0];
+        if (g.kappa_kind == IGA_KAPPA_SIN2D || g.kappa_kind == IGA_KAPPA_EXPSIN3D) {
+            float st, ct;
+            sincospif(2.f * amp * P, &st, &ct);
+            const float kb = g.kb_df[0];
+            const float sin0 = fmaf(S2[0], ct, C2[0] * st);
+            if (g.kappa_kind == IGA_KAPPA_SIN2D) {
+                kap = fmaf(kb, sin0 * fmaf(S2[1], ct, C2[1] * st), kap);
+            } else {
+                const float cos1 = C2[1] * ct - S2[1] * st;
+                const float sin2 = fmaf(S2[2], ct, C2[2] * st);
+                kap = expf(kb * sin0 * cos1 * sin2);
+            }
+        }
+        const float f = kap * fabsf(det);
+        int k = 0;
+        for (int a = 0; a < DIM; ++a)
+            for (int bdir = a; bdir < DIM; ++bdir, ++k) {
+                float m = c2g - cc * (gr[a] + gr[bdir]);
+                if (a == bdir) m += 1.f;
+                reinterpret_cast<float*>(out)[k * npts + item] = f * m;
+            }
+        return;
+    }
     if (Pol::kind != kArithF64 && g.coef_df) {
         // Same formulas as the FP64 branch below, in double-float arithmetic on
         // the FP32 pipe (dfmath.cuh): the result is stored in double-float (or
