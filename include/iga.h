@@ -228,7 +228,8 @@ int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* st
  * cache, and the tuned replay time in ms (0 unless a graph was tuned). */
 int iga_batch_info(int* branches, int64_t* kernels, int* cached, float* tuned_ms);
 
-/* Destroys every cached batch graph. */
+/* Destroys every cached batch graph (iga_matrix_destroy already drops the graphs
+ * that write into the destroyed matrix). */
 int iga_batch_release(void);
 
 /*

@@ -803,6 +803,7 @@ int iga_matrix_destroy(iga_matrix_t A)
 {
     t_err.clear();
     if (!A) return IGA_OK;
+    batch_forget(A);                 // cached batch graphs write into this matrix: drop them
     cudaError_t e = cudaFree(A->values);
     delete A;
     if (e != cudaSuccess) return cuda_fail(e, "freeing matrix values");

@@ -26,6 +26,7 @@ struct GraphEntry {
     int64_t kernels = 0;
     int branches = 0;
     float ms = 0.f;
+    std::vector<iga_matrix_t> mats;      // the matrices the graph writes into
 };
 
 std::mutex g_batch_mu;
@@ -127,6 +128,23 @@ int capture(Streams& S, int n, const iga_batch_item_t* items, int dtype, iga_mat
 }
 
 }  // namespace
+
+void batch_forget(iga_matrix_t A)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        const auto& m = it->second.mats;
+        if (std::find(m.begin(), m.end(), A) != m.end()) {
+            // a graph that may still run on some stream: wait for the device before destroying it
+            cudaDeviceSynchronize();
+            if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 }  // namespace iga
 
 using namespace iga;
@@ -222,6 +240,7 @@ int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* st
     // the caller's stream follows the replays
     if ((e = cudaEventRecord(in_ev, S->cap)) != cudaSuccess || (e = cudaStreamWaitEvent(st, in_ev, 0)) != cudaSuccess)
         return report_error(IGA_ECUDA, cudaGetErrorString(e));
+    best.mats.assign(A, A + n);
     g_graphs[key] = best;
     t_branches = best.branches;
     t_kernels = best.kernels;

@@ -138,6 +138,8 @@ int report_error(int code, const char* msg);
 void set_capture(bool on);
 void add_launches(int64_t n);
 int64_t launch_count();
+// Drop every cached batch graph that writes into matrix A (iga_batch.cu).
+void batch_forget(iga_matrix_t A);
 // One patch through the exact (surrogate = false) or surrogate pipeline on `stream`.
 int assemble_patch(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
                    int M, int q, int domains, int dtype, void* stream, iga_matrix_t* out);
