@@ -77,6 +77,7 @@ def lib():
         L.orc_num_dofs.restype = ctypes.c_int64
         L.orc_num_slots.argtypes = [P]
         L.orc_exact_rows.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp]
+        L.orc_mass_rows.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp]
         L.orc_elementwise_dense.argtypes = [P, dp]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L

@@ -439,6 +439,71 @@ static void exact_row(const orc_problem* P, const tab1d* T, int64_t row, double*
     }
 }
 
+/* |det Dphi(xi)|: the weight of the mass form m(u,v) = int_Omega u v dx pulled
+   back to the parameter domain (Sec. 8, proof of the mass-matrix corollary). */
+static double jac_det_abs(const orc_problem* P, const double* xi)
+{
+    double x[3], J[9];
+    orc_map(P, xi, x, J);
+    double det;
+    if (P->dim == 2) {
+        det = J[0] * J[4] - J[1] * J[3];
+    } else {
+        det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+              J[2] * (J[3] * J[7] - J[4] * J[6]);
+    }
+    return fabs(det);
+}
+
+/* Mass row i: M_ij = sum_g w_g |det Dphi(g)| B_i(g) B_j(g) over the elements of
+   supp(B_i), the same Gauss rule and slot order as exact_row. */
+static void mass_row(const orc_problem* P, const tab1d* T, int64_t row, double* out)
+{
+    int n = P->dim, p = P->p, w = 2 * p + 1;
+    int S = orc_num_slots(P);
+    int m[3] = {1, 1, 1}, ii[3] = {0, 0, 0};
+    for (int d = 0; d < n; ++d) m[d] = P->n_el[d] + p;
+    int64_t rem = row;
+    for (int d = 0; d < n; ++d) { ii[d] = (int)(rem % m[d]); rem /= m[d]; }
+    for (int s = 0; s < S; ++s) out[s] = 0.0;
+    int elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+    for (int d = 0; d < n; ++d) {
+        elo[d] = ii[d] - p < 0 ? 0 : ii[d] - p;
+        ehi[d] = ii[d] > P->n_el[d] - 1 ? P->n_el[d] - 1 : ii[d];
+    }
+    int e[3] = {0, 0, 0}, r[3] = {0, 0, 0};
+    for (e[2] = (n == 3 ? elo[2] : 0); e[2] <= (n == 3 ? ehi[2] : 0); ++e[2])
+    for (e[1] = elo[1]; e[1] <= ehi[1]; ++e[1])
+    for (e[0] = elo[0]; e[0] <= ehi[0]; ++e[0])
+    for (r[2] = 0; r[2] <= (n == 3 ? p : 0); ++r[2])
+    for (r[1] = 0; r[1] <= p; ++r[1])
+    for (r[0] = 0; r[0] <= p; ++r[0]) {
+        int g[3] = {0, 0, 0};
+        double xi[3] = {0, 0, 0}, wgt = 1.0;
+        for (int d = 0; d < n; ++d) {
+            g[d] = e[d] * (p + 1) + r[d];
+            xi[d] = T[d].xi[g[d]];
+            wgt *= T[d].wq[g[d]];
+        }
+        wgt *= jac_det_abs(P, xi);
+        double bi = 1.0;
+        for (int d = 0; d < n; ++d) bi *= tab_get(&T[d], g[d], ii[d], 0);
+        for (int s = 0; s < S; ++s) {
+            int jj[3] = {0, 0, 0}, ok = 1, rs = s;
+            for (int d = 0; d < n; ++d) {
+                int delta = rs % w - p; rs /= w;
+                jj[d] = ii[d] + delta;
+                if (jj[d] < 0 || jj[d] >= m[d]) ok = 0;
+                else if (jj[d] < e[d] || jj[d] > e[d] + p) ok = 0;
+            }
+            if (!ok) continue;
+            double bj = 1.0;
+            for (int d = 0; d < n; ++d) bj *= tab_get(&T[d], g[d], jj[d], 0);
+            out[s] += wgt * bi * bj;
+        }
+    }
+}
+
 static int build_tables(const orc_problem* P, tab1d* T)
 {
     for (int d = 0; d < P->dim; ++d)
@@ -458,6 +523,22 @@ int orc_exact_rows(const orc_problem* P, int64_t nrows, const int64_t* rows, dou
     int S = orc_num_slots(P);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t r = 0; r < nrows; ++r) exact_row(P, T, rows[r], out + r * S);
+    for (int d = 0; d < P->dim; ++d) tab_free(&T[d]);
+    return 0;
+}
+
+/* Mass rows (mass_row) for an explicit list of row indices; out is [nrows][S]. */
+int orc_mass_rows(const orc_problem* P, int64_t nrows, const int64_t* rows, double* out)
+{
+    if (!problem_ok(P)) return -1;
+    int64_t N = orc_num_dofs(P);
+    for (int64_t r = 0; r < nrows; ++r) if (rows[r] < 0 || rows[r] >= N) return -1;
+    tab1d T[3];
+    memset(T, 0, sizeof(T));
+    if (build_tables(P, T)) return -2;
+    int S = orc_num_slots(P);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) mass_row(P, T, rows[r], out + r * S);
     for (int d = 0; d < P->dim; ++d) tab_free(&T[d]);
     return 0;
 }

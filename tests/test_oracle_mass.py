@@ -1,0 +1,125 @@
+"""Pins of the oracle's mass matrix and its symmetric surrogate (no GPU).
+
+* Identity map: the mass matrix is the tensor product of 1-D B-spline mass
+  matrices, computed here independently with scipy's BSpline and numpy's
+  Gauss-Legendre rule.
+* Affine map x = A xi + b: M = |det A| M(identity) (change of variables).
+* Partition of unity: the sum of all entries is the quadrature of the measure of
+  Omega, 1 for the sine-product maps of the unit square / cube (they fix its
+  boundary) and |det A| for an affine map.
+* Symmetric positive definite.
+* Surrogate (eq. DefinitionOfSurrogateMatrixSymmetric): M = 1 reproduces M;
+  the mass-matrix corollary (polynomial map of degree p_phi, q >= n p_phi - 1)
+  gives M~ = M for affine maps; symmetric; frame rows and the upper entries
+  (diagonal included) of the sample rows exact; the H^{q+1} entry-error rate.
+"""
+import numpy as np
+import pytest
+from scipy.interpolate import BSpline
+
+import iga_workloads as W
+import oracle
+from oracle import mass
+
+
+def _mass_1d(p, n_el):
+    """1-D mass matrix of the open uniform B-splines by scipy + numpy Gauss (p+1 points)."""
+    t = np.concatenate([np.zeros(p), np.linspace(0, 1, n_el + 1), np.ones(p)])
+    m = n_el + p
+    xg, wg = np.polynomial.legendre.leggauss(p + 1)
+    Mx = np.zeros((m, m))
+    basis = BSpline(t, np.eye(m), p)
+    for e in range(n_el):
+        a, b = e / n_el, (e + 1) / n_el
+        x = a + (b - a) * 0.5 * (xg + 1)
+        B = basis(x)                                   # [points, m]
+        Mx += (B * (0.5 * (b - a) * wg)[:, None]).T @ B
+    return Mx
+
+
+@pytest.mark.parametrize("dim,p,n_el", [(2, 2, (7, 6)), (2, 3, (5, 8)), (3, 2, (4, 5, 3)), (3, 1, (5, 4, 6))])
+def test_identity_map_is_tensor_product_of_1d_mass(dim, p, n_el):
+    prob = W.Problem(dim=dim, p=p, n_el=n_el)
+    D = oracle.ell_to_dense(mass.mass_matrix(prob), prob)
+    ref = _mass_1d(p, n_el[0])
+    for d in range(1, dim):
+        ref = np.kron(_mass_1d(p, n_el[d]), ref)      # colexicographic: direction 0 fastest
+    assert np.abs(D - ref).max() < 1e-15 * 10 * np.abs(ref).max()
+
+
+def test_affine_map_scales_by_det():
+    A = np.array([[1.2, 0.3, 0.0], [-0.1, 0.9, 0.2], [0.05, 0.1, 1.1]])
+    aff = tuple(A.ravel()) + (0.1, -0.2, 0.3)
+    for dim in (2, 3):
+        n_el = (5, 6, 4)[:dim]
+        prob = W.Problem(dim=dim, p=2, n_el=n_el, map_kind="affine", affine=aff)
+        ref = W.Problem(dim=dim, p=2, n_el=n_el)
+        det = abs(np.linalg.det(A[:dim, :dim]))
+        M1, M0 = mass.mass_matrix(prob), mass.mass_matrix(ref)
+        assert np.abs(M1 - det * M0).max() < 1e-14 * np.abs(M1).max()
+        assert abs(M1.sum() - det) < 1e-13
+
+
+@pytest.mark.parametrize("dim,p,n_el,amp", [(2, 2, (12, 14), 0.05), (3, 2, (8, 7, 9), 0.03), (3, 3, (6, 6, 7), 0.03)])
+def test_total_mass_is_the_measure(dim, p, n_el, amp):
+    prob = W.Problem(dim=dim, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp)
+    M = mass.mass_matrix(prob)
+    assert abs(M.sum() - 1.0) < 1e-6
+    D = oracle.ell_to_dense(M, prob)
+    assert np.abs(D - D.T).max() < 1e-16 * 10
+    if prob.N <= 600:
+        assert np.linalg.eigvalsh(0.5 * (D + D.T)).min() > 0
+
+
+SURR = [
+    (W.Problem(dim=2, p=2, n_el=(20, 23), map_kind="sinprod", map_amp=0.05), 3, 3),
+    (W.Problem(dim=2, p=3, n_el=(25, 22), map_kind="sinprod", map_amp=0.05), 4, 2),
+    (W.Problem(dim=3, p=2, n_el=(13, 12, 14), map_kind="sinprod", map_amp=0.03), 3, 3),
+]
+
+
+def test_M1_is_exact():
+    for prob, _, q in SURR:
+        ref = mass.mass_matrix(prob)
+        assert oracle.relative_entry_error(mass.mass_surrogate_matrix(prob, 1, q), ref) < 1e-13
+
+
+@pytest.mark.parametrize("dim,q", [(2, 1), (3, 2), (2, 3)])
+def test_affine_reproduction(dim, q):
+    """Mass-matrix corollary: polynomial map of degree 1, q >= n - 1 => M~ = M."""
+    A = np.array([[1.1, 0.2, -0.1], [0.05, 0.9, 0.3], [-0.2, 0.1, 1.2]])
+    prob = W.Problem(dim=dim, p=2, n_el=(14, 13, 15)[:dim], map_kind="affine", affine=tuple(A.ravel()) + (0, 0, 0))
+    ref = mass.mass_matrix(prob)
+    assert oracle.relative_entry_error(mass.mass_surrogate_matrix(prob, 3, q), ref) < 1e-12
+
+
+@pytest.mark.parametrize("prob,M,q", SURR, ids=["2d_p2", "2d_p3", "3d_p2"])
+def test_symmetric_surrogate_structure(prob, M, q):
+    Ms = mass.mass_surrogate_matrix(prob, M, q)
+    ref = mass.mass_matrix(prob)
+    D = oracle.ell_to_dense(Ms, prob)
+    scale = np.abs(D).max()
+    assert np.abs(D - D.T).max() < 1e-15 * 10 * scale
+    err = oracle.relative_entry_error(Ms, ref)
+    assert 1e-9 < err < 0.1
+    setup = mass.mass_surrogate_setup(prob, M, q)
+    mi = oracle.multi_index(np.arange(prob.N), prob.m)
+    k0, k1 = np.array(setup.k0), np.array(setup.k1)
+    frame = ~np.all((mi >= k0) & (mi <= k1), axis=1)
+    assert np.abs(Ms[:, frame] - ref[:, frame]).max() < 1e-15 * 10 * scale
+    samp = np.ones(prob.N, dtype=bool)
+    for d in range(prob.dim):
+        samp &= np.isin(mi[:, d], setup.samples[d])
+    c = oracle.center_slot(prob.dim, prob.p)
+    assert np.abs(Ms[c:, samp] - ref[c:, samp]).max() < 1e-13 * scale
+
+
+@pytest.mark.slow
+def test_entry_error_rate():
+    """|M - M~|_max ~ H^{q+1} at fixed h (eq. SurrogateMassBound, q = 3)."""
+    prob = W.Problem(dim=2, p=2, n_el=(135, 135), map_kind="sinprod", map_amp=0.05)
+    ref = mass.mass_matrix(prob)
+    Ms = [4, 8, 16]
+    errs = [np.abs(mass.mass_surrogate_matrix(prob, M, 3) - ref).max() for M in Ms]
+    slopes = np.diff(np.log(errs)) / np.diff(np.log(Ms))
+    assert np.all(slopes > 4 - 0.6) and np.all(slopes < 4 + 1.5), (errs, slopes)
