@@ -177,6 +177,31 @@ int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_ma
                                    int dtype, void* stream, iga_matrix_t* A);
 
 /*
+ * Mass matrix M_ij = int_Omega B_i B_j dx = int B_i B_j |det Dphi| dxi (Sec. 8,
+ * proof of the mass-matrix corollary), by the same (p+1)-point Gauss rule and
+ * sum-factorised quadrature as iga_assemble_exact, with |det Dphi| as the
+ * only coefficient field.  Same stencil-ELL layout; no kappa.  Other arguments
+ * as for iga_assemble_exact (the handle is interchangeable with a stiffness
+ * matrix of the same patch, p and dtype).
+ */
+int iga_assemble_mass(const iga_patch_t* patch, int p, const iga_map_t* map, int dtype, void* stream,
+                      iga_matrix_t* A);
+
+/*
+ * Surrogate mass matrix, eq. DefinitionOfSurrogateMatrixSymmetric (Sec. 5.2):
+ * the mass matrix has no kernel, so no row-sum diagonal.  On the common domain
+ * Omega~ = [2p, m-2p-1] (Sec. 4) and the samples of iga_assemble_surrogate,
+ * the (S+1)/2 stencil functions of the offsets delta >= 0 (colexicographic,
+ * the centre included) are interpolated; for i, j in Omega~, M~_ij is
+ * Phi~_delta(x~_i) when i <= j (the diagonal included) and the copy M~_ji when
+ * i > j; every other entry is exact.  M = 1 reproduces iga_assemble_mass; for
+ * an affine map and q >= dim - 1 the surrogate is exact (mass-matrix corollary
+ * of Sec. 8).  Arguments as for iga_assemble_surrogate without kappa.
+ */
+int iga_assemble_mass_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map, int M, int q, int dtype,
+                                void* stream, iga_matrix_t* A);
+
+/*
  * Gradient with respect to the B-spline control values of kappa
  * (IGA_KAPPA_BSPLINE3) of L = ybar^T A x, A the exact matrix (M = 0) or the
  * surrogate with the common domain Omega~ (M >= 1, interpolation degree q), as

@@ -13,6 +13,7 @@ kappa_poly``.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 import threading
 from typing import Optional
@@ -78,6 +79,10 @@ def load():
         L.iga_assemble_surrogate_domains.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                                      ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, vp, ctypes.POINTER(H)]
+        L.iga_assemble_mass.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map), ctypes.c_int, vp,
+                                        ctypes.POINTER(H)]
+        L.iga_assemble_mass_surrogate.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(H)]
         L.iga_kappa_gradient.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                          ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.iga_assemble_batch.argtypes = [ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int, vp,
@@ -287,6 +292,25 @@ def assemble_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Opti
                                                      ctypes.byref(kp), int(M), int(q), DOMAINS[domains],
                                                      _dtype_code(dtype), st, ctypes.byref(h)))
     return _keep(out if out is not None else Matrix(h.value), kp)
+
+
+def assemble_mass(prob, dtype="f64", stream=None, out: Optional[Matrix] = None) -> Matrix:
+    """Exact Gauss-quadrature mass matrix on the GPU (iga_assemble_mass); the problem's kappa is not used."""
+    pt, mp, _ = _structs(dataclasses.replace(prob, kappa_kind="const"))     # the mass form has no kappa
+    h = ctypes.c_void_p(out.handle.value if out is not None else None)
+    _check(load().iga_assemble_mass(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), _dtype_code(dtype),
+                                    ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return out if out is not None else Matrix(h.value)
+
+
+def assemble_mass_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out: Optional[Matrix] = None) -> Matrix:
+    """Symmetric surrogate mass matrix on the common domain (iga_assemble_mass_surrogate)."""
+    pt, mp, _ = _structs(dataclasses.replace(prob, kappa_kind="const"))     # the mass form has no kappa
+    h = ctypes.c_void_p(out.handle.value if out is not None else None)
+    _check(load().iga_assemble_mass_surrogate(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), int(M), int(q),
+                                              _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)),
+                                              ctypes.byref(h)))
+    return out if out is not None else Matrix(h.value)
 
 
 def set_arithmetic(dtype, arith: str):

@@ -220,6 +220,9 @@ int plan_spline(const Geo& g, int p, int M, int q, int domains, SplinePlan& sp, 
     const int S = (dim == 3) ? W * W * W : W * W;
     memset(&sp, 0, sizeof(sp));
     sp.dim = dim; sp.q = q; sp.S = S; sp.c = (S - 1) / 2; sp.nv = W;
+    // kernel-preserving surrogate (stiffness): upper offsets only, the diagonal is
+    // minus the row sum; symmetric surrogate (mass): the diagonal is interpolated too
+    sp.first = (g.form == kFormMass) ? sp.c : sp.c + 1;
     sp.all = (domains == IGA_DOMAINS_COMMON);
     empty = 0;
     const bool per_offset = (domains == IGA_DOMAINS_PER_OFFSET);
@@ -307,12 +310,15 @@ void spline_bufs(double* scratch, const SplinePlan& sp, const SplineLayout& o, S
 }
 
 int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
-             int M, int q, int domains, int dtype, void* stream_v, iga_matrix_t* out)
+             int M, int q, int domains, int dtype, void* stream_v, iga_matrix_t* out, int form = kFormStiffness)
 {
     t_err.clear();
     Geo g;
     int rc = check_geometry(patch, p, map, kappa, g);
     if (rc) return rc;
+    g.form = form;
+    if (form == kFormMass && domains != IGA_DOMAINS_COMMON)
+        return fail(IGA_EUNSUPPORTED, "the mass surrogate uses the common domain Omega~");
     if (dtype != IGA_F64 && dtype != IGA_F32) return fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
     if (!out) return fail(IGA_EINVAL, "output handle pointer is null");
     if (surrogate) {
@@ -438,7 +444,7 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         }
         o_samples = lay.take((int64_t)S * sp.n_samples);
         spline_layout(lay, sp, slo);
-        const int64_t S_up = S - 1 - sp.c;
+        const int64_t S_up = S - sp.first;
         o_mid = lay.take(dim == 3 ? S_up * sp.Lmax[2] * (int64_t)sp.nu[1] * sp.nu[0] : 1);
         o_partial = lay.take(S_up * (dim == 3 ? sp.Lmax[2] : 1) * (int64_t)sp.Lmax[1] * sp.nu[0]);
     }
@@ -495,7 +501,8 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     double* samples = do_spline ? P(o_samples) : nullptr;
     if (ce == cudaSuccess) {
         stage = "quadrature stages";
-        ce = launch_stages(g, T, bs, nblk, scratch, A->values, dtype == IGA_F32, samples, st);
+        ce = (form == kFormMass) ? launch_mass_stages(g, T, bs, nblk, scratch, A->values, dtype == IGA_F32, samples, st)
+                                 : launch_stages(g, T, bs, nblk, scratch, A->values, dtype == IGA_F32, samples, st);
     }
     SplineBufs sb;
     memset(&sb, 0, sizeof(sb));
@@ -607,6 +614,25 @@ int iga_assemble_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map
     return assemble(patch, p, map, kappa, true, M, q, IGA_DOMAINS_COMMON, dtype, stream, A);
 }
 
+int iga_assemble_mass(const iga_patch_t* patch, int p, const iga_map_t* map, int dtype, void* stream, iga_matrix_t* A)
+{
+    iga_kappa_t unit;
+    memset(&unit, 0, sizeof(unit));
+    unit.kind = IGA_KAPPA_CONST;
+    unit.a = 1.0;
+    return assemble(patch, p, map, &unit, false, 1, 0, IGA_DOMAINS_COMMON, dtype, stream, A, kFormMass);
+}
+
+int iga_assemble_mass_surrogate(const iga_patch_t* patch, int p, const iga_map_t* map, int M, int q, int dtype,
+                                void* stream, iga_matrix_t* A)
+{
+    iga_kappa_t unit;
+    memset(&unit, 0, sizeof(unit));
+    unit.kind = IGA_KAPPA_CONST;
+    unit.a = 1.0;
+    return assemble(patch, p, map, &unit, true, M, q, IGA_DOMAINS_COMMON, dtype, stream, A, kFormMass);
+}
+
 int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, int M,
                        int q, const double* ybar, const double* x, double* grad, void* stream_v)
 {
@@ -663,7 +689,7 @@ int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, co
     if (sur) {
         spline_layout(lay, sp, slo);
         const int P = p;
-        const int64_t S_up = sp.S - 1 - sp.c;
+        const int64_t S_up = sp.S - sp.first;
         const int64_t L1 = sp.L[1][P], L2 = (dim == 3) ? sp.L[2][P] : 1;
         o_C0 = lay.take(S_up * L2 * L1 * sp.nu[0]);
         o_C1 = lay.take(dim == 3 ? S_up * L2 * (int64_t)sp.nu[1] * sp.nu[0] : 1);

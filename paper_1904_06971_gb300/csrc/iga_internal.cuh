@@ -28,7 +28,11 @@ struct Geo {
     // double-float copies (hi, lo) of amp, ka, kb for the double-float coefficient path
     float amp_df[2], ka_df[2], kb_df[2];
     int coef_df;              // evaluate the coefficient tensor in double-float arithmetic
+    int form;                 // kFormStiffness or kFormMass
 };
+
+// Bilinear forms: the diffusion stiffness (Sec. 3.2) and the mass form of Sec. 8.
+enum Form { kFormStiffness = 0, kFormMass = 1 };
 
 // A rectangular block of rows whose full stencil rows are computed by the
 // sum-factorised quadrature, with the Gauss points it needs.
@@ -161,6 +165,10 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
                         double* scratch, cudaStream_t s);
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
                           double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
+// The same three stages for the mass form: one scalar field (|det Dphi| at the
+// Gauss points) and the value-value pair weights only (k_mass.cu).
+cudaError_t launch_mass_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
+                               double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
 
 // Whether the sample index t of a direction is a sample of the variant with
 // domain [k0, k1]: every sample in the domain (all != 0, the common domain),
@@ -182,6 +190,7 @@ __host__ __device__ __forceinline__ bool variant_sample(const SampleAxis& ax, in
 constexpr int kMaxSamplesPerDir = 2048;
 struct SplinePlan {
     int dim, q, S, c, nv;     // nv = 2p + 1 variants per direction
+    int first;                // first interpolated slot: c + 1 (kernel-preserving), c (symmetric, diagonal included)
     int all;                  // every variant uses every sample (common domain)
     int64_t n_samples;        // prod nu
     SampleAxis ax[3];

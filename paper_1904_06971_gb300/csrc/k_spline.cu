@@ -47,11 +47,11 @@ __device__ void spline_basis(const double* kn, int mu, int q, double x, double* 
     }
 }
 
-// variant (v_0, v_1, v_2) of upper slot u: v_d = delta_d + p of slot c + 1 + u
+// variant (v_0, v_1, v_2) of interpolated slot u: v_d = delta_d + p of slot first + u
 __device__ __forceinline__ void slot_variants(const SplinePlan& sp, int64_t u, int v[3])
 {
     const int W = sp.nv;
-    int s = sp.c + 1 + (int)u;
+    int s = sp.first + (int)u;
     for (int d = 0; d < 3; ++d) {
         v[d] = (d < sp.dim) ? s % W : 0;
         s /= W;
@@ -145,7 +145,7 @@ __global__ void k_spline_setup(SplinePlan sp, SplineBufs sb)
 __global__ void k_spline_solve(SplinePlan sp, int d, SplineBufs sb, double* samples)
 {
     const int64_t lines = sp.n_samples / sp.nu[d];
-    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t S_up = sp.S - sp.first;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= S_up * lines) return;
     const int64_t u = idx / lines;
@@ -163,7 +163,7 @@ __global__ void k_spline_solve(SplinePlan sp, int d, SplineBufs sb, double* samp
     }
     const int ns = sp.ns[d][v[d]];
     if (ns <= 0) return;
-    double* x = samples + (sp.c + 1 + u) * sp.n_samples + base;
+    double* x = samples + (sp.first + u) * sp.n_samples + base;
     const int* ps = sb.pos[d][v[d]];
     const double* B = sb.lu[d][v[d]];
     const int bl = sb.band[2 * (d * kMaxV + v[d])], bu = sb.band[2 * (d * kMaxV + v[d]) + 1];
@@ -188,7 +188,7 @@ __global__ void k_spline_solve(SplinePlan sp, int d, SplineBufs sb, double* samp
 __global__ void k_spline_mid(SplinePlan sp, SplineBufs sb, const double* samples, double* mid)
 {
     const int nu0 = sp.nu[0], nu1 = sp.nu[1], L2 = sp.Lmax[2];
-    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t S_up = sp.S - sp.first;
     const int64_t total = S_up * L2 * nu1 * nu0;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -199,7 +199,7 @@ __global__ void k_spline_mid(SplinePlan sp, SplineBufs sb, const double* samples
     int v[3];
     slot_variants(sp, u, v);
     if (a0 >= sp.ns[0][v[0]] || b1 >= sp.ns[1][v[1]] || j2 >= sp.L[2][v[2]]) return;
-    const double* coef = samples + (sp.c + 1 + u) * sp.n_samples;
+    const double* coef = samples + (sp.first + u) * sp.n_samples;
     const int q2 = sp.qe[2][v[2]];
     const int s2 = sb.espan[2][v[2]][j2];
     const int* p2 = sb.pos[2][v[2]];
@@ -215,7 +215,7 @@ __global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* sam
 {
     const int nu0 = sp.nu[0], nu1 = sp.nu[1];
     const int L1 = sp.Lmax[1], L2 = (sp.dim == 3) ? sp.Lmax[2] : 1;
-    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t S_up = sp.S - sp.first;
     const int64_t total = S_up * L2 * L1 * nu0;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -235,7 +235,7 @@ __global__ void k_spline_partial(SplinePlan sp, SplineBufs sb, const double* sam
         const double* src = mid + ((u * L2 + j2) * (int64_t)nu1) * nu0 + a0;
         for (int b = 0; b <= q1; ++b) acc += src[(int64_t)nu0 * (s1 + b)] * E1[b];
     } else {
-        const double* src = samples + (sp.c + 1 + u) * sp.n_samples + sb.pos[0][v[0]][a0];
+        const double* src = samples + (sp.first + u) * sp.n_samples + sb.pos[0][v[0]][a0];
         const int* p1 = sb.pos[1][v[1]];
         for (int b = 0; b <= q1; ++b) acc += src[(int64_t)nu0 * p1[s1 + b]] * E1[b];
     }
@@ -259,7 +259,7 @@ cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, double* samples,
     (void)g;
     cudaError_t err = launch_spline_setup(sp, sb, s);
     if (err != cudaSuccess) return err;
-    const int64_t S_up = sp.S - 1 - sp.c;
+    const int64_t S_up = sp.S - sp.first;
     for (int d = 0; d < sp.dim; ++d) {
         const int64_t n = S_up * (sp.n_samples / sp.nu[d]);
         launch_begin(K_SPLINE_SOLVE, s);
@@ -333,13 +333,14 @@ __global__ void __launch_bounds__(kBlock) k_fill(Geo g, SplinePlan sp, SplineBuf
 #pragma unroll
     for (int d0 = 0; d0 < W; ++d0) {
         const int s = sbase + d0;
-        if (s == C) continue;
+        if (s == C && sp.first > C) continue;     // kernel-preserving: the diagonal comes from pass 2
         const int j0 = i0 + d0 - P;
         T out;
         if (in12 && j0 >= sp.r0[0] && j0 <= sp.r1[0]) {
-            // upper: evaluate Phi~_delta at i; lower: Phi~_{-delta} at j
-            const bool upper = s > C;
-            const int u = upper ? s - C - 1 : (S - 1 - s) - C - 1;
+            // upper (diagonal included for the symmetric surrogate): Phi~_delta at i;
+            // lower: Phi~_{-delta} at j
+            const bool upper = s >= sp.first;
+            const int u = upper ? s - sp.first : (S - 1 - s) - sp.first;
             const int v0 = upper ? d0 : 2 * P - d0;
             const int x0 = (upper ? i0 : j0) - sp.k0[0][v0];
             const int x1 = upper ? up1 : lo1, x2 = upper ? up2 : lo2;
@@ -407,18 +408,18 @@ __global__ void __launch_bounds__(kBlock) k_fill_common(Geo g, SplinePlan sp, Sp
 #pragma unroll
     for (int d0 = 0; d0 < W; ++d0) {
         const int s = sbase + d0;
-        if (s == C) continue;
+        if (s == C && sp.first > C) continue;     // kernel-preserving: the diagonal comes from pass 2
         const int y0 = x0 + d0 - P;
         T out;
         if (in12 && y0 >= 0 && y0 < R0) {
             const float2* Pp;
             float2 E[Q1];
-            if (s > C) {            // Phi~_delta at x~_i
-                Pp = sb.partial + (int64_t)(s - C - 1) * slot_stride + up_row;
+            if (s >= sp.first) {    // Phi~_delta at x~_i (the diagonal too for the symmetric surrogate)
+                Pp = sb.partial + (int64_t)(s - sp.first) * slot_stride + up_row;
 #pragma unroll
                 for (int k = 0; k < Q1; ++k) E[k] = Eu[k];
             } else {                // Phi~_{-delta} at x~_j
-                Pp = sb.partial + (int64_t)(S - 1 - s - C - 1) * slot_stride + lo_row + esp0[y0];
+                Pp = sb.partial + (int64_t)(S - 1 - s - sp.first) * slot_stride + lo_row + esp0[y0];
 #pragma unroll
                 for (int k = 0; k < Q1; ++k) E[k] = ev0[(int64_t)k * L0 + y0];
             }
@@ -523,6 +524,8 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
         }
         launch_end(K_FILL, s);
     }
+    if (sp.first <= sp.c && !empty_box) return;      // symmetric surrogate: no kernel-preserving diagonal
+    if (g.form == kFormMass) return;                  // mass matrix with an empty Omega~: all rows exact
     launch_begin(K_DIAG, s);
     if (g.dim == 3) {
         if (f32) k_diag<P, 3, float><<<gdiag, kBlock, 0, s>>>(N, (float*)ell);

@@ -293,6 +293,28 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
         xi[d] = T.gx[d][gg[d]];
     }
     typename Pol::store* out = reinterpret_cast<typename Pol::store*>(scratch + b.c_off);
+    if (g.form == kFormMass) {
+        // the mass form's only field: |det Dphi| (Sec. 8), FP64
+        double det = 1.0;
+        if (g.map_kind == IGA_MAP_SINPROD) {
+            // Dphi = I + amp 1 gr^T, gr_b = dP/dxi_b: det = 1 + amp sum_b gr_b
+            double sv[3], cv[3], gsum = 0.0;
+            for (int d = 0; d < DIM; ++d) { sv[d] = T.sx[d][gg[d]]; cv[d] = T.cx[d][gg[d]]; }
+            for (int bdir = 0; bdir < DIM; ++bdir) {
+                double dP = CUDART_PI * cv[bdir];
+                for (int j = 0; j < DIM; ++j) if (j != bdir) dP *= sv[j];
+                gsum += dP;
+            }
+            det = 1.0 + g.amp * gsum;
+        } else if (g.map_kind == IGA_MAP_AFFINE) {
+            const double* A = g.aff;
+            det = (DIM == 2) ? A[0] * A[4] - A[1] * A[3]
+                             : A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                                   A[2] * (A[3] * A[7] - A[4] * A[6]);
+        }
+        out[item] = Pol::from_double(fabs(det));
+        return;
+    }
     if (Pol::kind == kArithF32 && g.coef_df) {
         // FP32 contractions: the same formulas in FP32 (the hi parts of the
         // double-float tables), whose rounding is of the order of the FP32
