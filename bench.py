@@ -5,7 +5,9 @@ matrix (basis and pair tables, coefficient field, sum-factorised quadrature of
 the frame and sample rows, per-offset spline interpolation, surrogate fill
 with the kernel-preserving diagonal) followed by one stencil SpMV with it.
 The exact Gauss-quadrature assembly of the same patch is timed the same way
-and reported beside it.  Default workload: 3-D patch, p = 3, 64^3 elements,
+and reported beside it, and so are the mass matrix of the same patch (its
+symmetric surrogate and exact assembly), the kappa adjoint and the batch of
+256 patches (outside the timed region).  Default workload: 3-D patch, p = 3, 64^3 elements,
 M = 8, q = 3, FP64 values (x_i = xi_i + 0.03 prod sin(pi xi_j),
 kappa = exp(0.5 sin(2 pi x) cos(2 pi y) sin(2 pi z))), synthetic and seeded.
 
@@ -405,6 +407,50 @@ def adjoint_report(iga, torch, dev, steps: int, warmup: int):
     return out
 
 
+def mass_report(iga, torch, wl, steps: int, warmup: int):
+    """Mass matrix of the bench workload's patch (Sec. 8): the symmetric surrogate
+    (eq. DefinitionOfSurrogateMatrixSymmetric, same M and q) against the exact
+    assembly, CUDA events, matrices resident; entry error of the surrogate."""
+    prob = wl.problem
+    stream = torch.cuda.current_stream()
+    out = {"workload": wl.name, "unit": "nnz/s"}
+    mats = {}
+    for key in ("surrogate", "exact"):
+        A = iga.assemble_mass_surrogate(prob, wl.M, wl.q, dtype=wl.dtype) if key == "surrogate" \
+            else iga.assemble_mass(prob, dtype=wl.dtype)
+
+        def step():
+            if key == "surrogate":
+                iga.assemble_mass_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A)
+            else:
+                iga.assemble_mass(prob, dtype=wl.dtype, out=A)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        iga.profile_read()
+        iga.profile_enable(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        iga.profile_enable(False)
+        prof = iga.profile_read()
+        ms = a.elapsed_time(b) / steps
+        out[key] = {"value": prob.nnz / (ms * 1e-3), "ms_per_step": ms,
+                    "kernels": {k: round(v[1] / steps, 4) for k, v in prof.items() if v[0]}}
+        mats[key] = A
+    vs, ve = mats["surrogate"].values(), mats["exact"].values()
+    out["entry_error"] = ((vs.double() - ve.double()).abs().max() / ve.double().abs().max()).item()
+    out["speedup_vs_exact"] = out["exact"]["ms_per_step"] / out["surrogate"]["ms_per_step"]
+    del vs, ve
+    for A in mats.values():
+        A.destroy()
+    return out
+
+
 def batch_report(iga, torch, steps: int, warmup: int):
     """The 256-patch batching workload (FP32 values): eager per-patch assembly on one
     stream against the autotuned graph replay (one graph launch per step)."""
@@ -651,6 +697,7 @@ def run_gpu(args, wl):
                 "h2d_bytes_per_step": prob.N * esz, "d2h_bytes_per_step": prob.N * esz},
         "adjoint": adjoint_report(iga, torch, dev, steps=5, warmup=3) if not args.no_adjoint else None,
         "batch": batch_report(iga, torch, steps=5, warmup=3) if not args.no_batch else None,
+        "mass": mass_report(iga, torch, wl, steps=5, warmup=3) if not args.no_mass else None,
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -673,6 +720,7 @@ def main(argv=None):
     ap.add_argument("--no-solve", action="store_true", help="skip the CG solution-error report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the kappa-gradient timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-patch batch timing")
+    ap.add_argument("--no-mass", action="store_true", help="skip the mass-matrix timing")
     ap.add_argument("--cg-tol", type=float, default=1e-10)
     ap.add_argument("--cg-maxit", type=int, default=20000)
     ap.add_argument("--domains", choices=["common", "per_offset"], default="common",

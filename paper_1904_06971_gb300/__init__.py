@@ -22,7 +22,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "load", "launch_count",
+__all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "assemble_mass", "assemble_mass_surrogate",
+           "kappa_gradient", "stiffness_apply", "assemble_batch", "batch_info", "load", "launch_count",
            "profile_enable", "profile_read", "kernel_names", "set_arithmetic", "get_arithmetic",
            "F64", "F32", "ARITH"]
 

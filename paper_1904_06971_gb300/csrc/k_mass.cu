@@ -12,6 +12,23 @@
 
 namespace iga {
 
+// Q consecutive values from an offset that is a multiple of Q (the T2 lines of
+// a box start on 16-byte boundaries): 16-byte loads when Q values fill whole
+// 16-byte words, else scalar loads.
+template <class S, int Q>
+__device__ __forceinline__ void load_run_m(const S* p, S* v)
+{
+    if constexpr ((Q * sizeof(S)) % 16 == 0) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        float4* v4 = reinterpret_cast<float4*>(v);
+#pragma unroll
+        for (int k = 0; k < (int)(Q * sizeof(S) / 16); ++k) v4[k] = p4[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v[k] = p[k];
+    }
+}
+
 template <class Pol, int P>
 __global__ void __launch_bounds__(kBlock) k_mass_z(Geo g, Tables T, BoxSet bs, double* scratch)
 {
@@ -91,6 +108,9 @@ __global__ void __launch_bounds__(kBlock) k_mass_y(Geo g, Tables T, BoxSet bs, d
 }
 
 // Stage X: same item mapping as k_stage_x (kLinesX lines of one row per thread).
+// Rows whose stencil stays among cardinal B-splines share one pair-weight table
+// (translation invariance, Sec. 2.2), staged in shared memory: the loads of a
+// warp become broadcasts instead of one cache line per thread.
 template <class Pol, int P, int DIM>
 __global__ void __launch_bounds__(kBlock) k_mass_x(Geo g, Tables T, BoxSet bs, double* scratch, void* ell,
                                                    int ell_f32, int64_t N, double* samples)
@@ -98,6 +118,12 @@ __global__ void __launch_bounds__(kBlock) k_mass_x(Geo g, Tables T, BoxSet bs, d
     using S = typename Pol::store;
     using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q, LINES = kLinesX;
+    __shared__ S sX[W * TT];
+    const bool has_card = g.m[0] >= 4 * P + 1;
+    const S* X0 = reinterpret_cast<const S*>(T.Xs[0]);
+    if (has_card)
+        for (int k = threadIdx.x; k < W * TT; k += blockDim.x) sX[k] = X0[((int64_t)(2 * P) * W * TT + k) * 4];
+    __syncthreads();
     Box b;
     get_box(bs, DIM, P, 3, blockIdx.x, b);
     const int64_t G0 = (int64_t)b.E[0] * Q;
@@ -113,10 +139,16 @@ __global__ void __launch_bounds__(kBlock) k_mass_x(Geo g, Tables T, BoxSet bs, d
     const int i1 = b.rlo[0] + i1l;
     const int i3 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
     const int d3 = (DIM == 3) ? (int)(pair3 % W) : 0;
-    const S* Xi = reinterpret_cast<const S*>(T.Xs[0]) + (int64_t)i1 * W * TT * 4;
+    const bool card = has_card && i1 >= 2 * P && i1 <= g.m[0] - 2 * P - 1;
+    // pattern-00 weight of (delta, t): sX[dd * TT + t], or every fourth entry of the global table
+    const S* Xi = card ? sX : X0 + (int64_t)i1 * W * TT * 4;
+    const int xs = card ? 1 : 4;
     int nl = (int)(P2 - lg * LINES);
     if (nl > LINES) nl = LINES;
-    const S* T2 = reinterpret_cast<const S*>(scratch + b.t2_off);
+    const S* T2[LINES];
+#pragma unroll
+    for (int l = 0; l < LINES; ++l)
+        T2[l] = reinterpret_cast<const S*>(scratch + b.t2_off) + (pair3 * P2 + lg * LINES + (l < nl ? l : 0)) * G0;
     A acc[LINES][W];
 #pragma unroll
     for (int l = 0; l < LINES; ++l)
@@ -127,18 +159,17 @@ __global__ void __launch_bounds__(kBlock) k_mass_x(Geo g, Tables T, BoxSet bs, d
         const int e1 = i1 - P + a;
         if (e1 < b.elo[0] || e1 >= b.elo[0] + b.E[0]) continue;
         const int64_t o = (int64_t)(e1 - b.elo[0]) * Q;
+        __align__(16) S v[LINES][Q];
+#pragma unroll
+        for (int l = 0; l < LINES; ++l) load_run_m<S, Q>(T2[l] + o, v[l]);
 #pragma unroll
         for (int r = 0; r < Q; ++r) {
             const int t = a * Q + r;
-            S v[LINES];
-#pragma unroll
-            for (int l = 0; l < LINES; ++l)
-                v[l] = T2[(pair3 * P2 + lg * LINES + (l < nl ? l : 0)) * G0 + o + r];
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
-                const S x = Xi[(dd * TT + t) * 4];
+                const S x = Xi[(dd * TT + t) * xs];
 #pragma unroll
-                for (int l = 0; l < LINES; ++l) Pol::mac(acc[l][dd], x, v[l]);
+                for (int l = 0; l < LINES; ++l) Pol::mac(acc[l][dd], x, v[l][r]);
             }
         }
     }

@@ -294,7 +294,34 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
     }
     typename Pol::store* out = reinterpret_cast<typename Pol::store*>(scratch + b.c_off);
     if (g.form == kFormMass) {
-        // the mass form's only field: |det Dphi| (Sec. 8), FP64
+        // the mass form's only field: |det Dphi| (Sec. 8), det = 1 + amp sum_b gr_b
+        // for the sine-product map.  FP32 contractions take it in FP32, double-float
+        // ones in double-float arithmetic (FP32 pipe), FP64 ones in FP64.
+        if (Pol::kind != kArithF64 && g.coef_df && g.map_kind == IGA_MAP_SINPROD) {
+            df2 sv[3], pcv[3];
+            for (int d = 0; d < DIM; ++d) {
+                const float2* t4 = T.tdf[d] + 4 * gg[d];
+                sv[d] = df2{t4[0].x, t4[0].y};
+                pcv[d] = df2{t4[1].x, t4[1].y};
+            }
+            if (Pol::kind == kArithF32) {
+                float gsum = (DIM == 3) ? pcv[0].h * (sv[1].h * sv[2].h) + pcv[1].h * (sv[0].h * sv[2].h) +
+                                              pcv[2].h * (sv[0].h * sv[1].h)
+                                        : pcv[0].h * sv[1].h + pcv[1].h * sv[0].h;
+                reinterpret_cast<float*>(out)[item] = fabsf(fmaf(g.amp_df[0], gsum, 1.f));
+                return;
+            }
+            df2 gsum;
+            if (DIM == 3) {
+                gsum = df_add(df_add(df_mul(pcv[0], df_mul(sv[1], sv[2])), df_mul(pcv[1], df_mul(sv[0], sv[2]))),
+                              df_mul(pcv[2], df_mul(sv[0], sv[1])));
+            } else {
+                gsum = df_add(df_mul(pcv[0], sv[1]), df_mul(pcv[1], sv[0]));
+            }
+            const df2 det = df_abs(df_fma(df2{g.amp_df[0], g.amp_df[1]}, gsum, df2{1.f, 0.f}));
+            reinterpret_cast<float2*>(out)[item] = make_float2(det.h, det.l);
+            return;
+        }
         double det = 1.0;
         if (g.map_kind == IGA_MAP_SINPROD) {
             // Dphi = I + amp 1 gr^T, gr_b = dP/dxi_b: det = 1 + amp sum_b gr_b
