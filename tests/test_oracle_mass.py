@@ -2,7 +2,8 @@
 
 * Identity map: the mass matrix is the tensor product of 1-D B-spline mass
   matrices, computed here independently with scipy's BSpline and numpy's
-  Gauss-Legendre rule.
+  Gauss-Legendre rule; an interior row is the tensor product of the closed-form
+  cardinal stencils h N_{2p+1}(k) (B-spline convolution identity).
 * Affine map x = A xi + b: M = |det A| M(identity) (change of variables).
 * Partition of unity: the sum of all entries is the quadrature of the measure of
   Omega, 1 for the sine-product maps of the unit square / cube (they fix its
@@ -45,6 +46,29 @@ def test_identity_map_is_tensor_product_of_1d_mass(dim, p, n_el):
     for d in range(1, dim):
         ref = np.kron(_mass_1d(p, n_el[d]), ref)      # colexicographic: direction 0 fastest
     assert np.abs(D - ref).max() < 1e-15 * 10 * np.abs(ref).max()
+
+
+# Centred cardinal B-spline of degree 2p+1 at the integers 0, 1, ..., p (the
+# autocorrelation of the degree-p cardinal B-spline), times (2p+1)!.
+_CARDINAL = {2: ([66, 26, 1], 120), 3: ([2416, 1191, 120, 1], 5040), 4: ([156190, 88234, 14608, 502, 1], 362880)}
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_interior_stencil_closed_form(p):
+    """Identity map: an interior row's entry for offset delta is prod_d h_d N_{2p+1}(delta_d)."""
+    num, den = _CARDINAL[p]
+    k = np.arange(-p, p + 1)
+    n1 = np.array([num[abs(j)] for j in k], dtype=np.float64) / den
+    assert abs(n1.sum() - 1.0) < 1e-15                       # each 1-D stencil sums to h
+    for dim, n_el in ((2, (4 * p + 3, 4 * p + 5)), (3, (4 * p + 2, 4 * p + 3, 4 * p + 1))):
+        prob = W.Problem(dim=dim, p=p, n_el=n_el)
+        m = np.array(prob.m)
+        row = int(oracle.flat_index(m[None, :] // 2, m)[0])
+        got = mass.mass_rows(prob, [row])[0]
+        ref = np.ones(1)
+        for d in range(dim):                                     # colexicographic slots: direction 0 fastest
+            ref = np.kron(n1 / n_el[d], ref)
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()      # rounding of (p+1)^n-point sums
 
 
 def test_affine_map_scales_by_det():
