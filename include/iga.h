@@ -52,7 +52,7 @@ extern "C" {
 #define IGA_ENOMEM       (-2)   /* device allocation failed */
 #define IGA_ECUDA        (-3)   /* a CUDA runtime call or launch failed */
 #define IGA_EUNSUPPORTED (-4)   /* valid request outside what is built (p, n, q range) */
-#define IGA_ETIMEOUT     (-5)   /* a bounded device wait gave up */
+#define IGA_ETIMEOUT     (-5)   /* reserved for a bounded device wait that gave up; no call waits on the device today */
 
 /* storage type of matrix values and of the SpMV vectors */
 #define IGA_F64 0
