@@ -1,7 +1,7 @@
 /*
  * iga.h -- C ABI of libiga: GPU (sm_103a) assembly of exact and surrogate
- * stiffness matrices for isogeometric analysis on one mapped tensor-product
- * B-spline patch, and the stencil SpMV with the result.
+ * stiffness (and mass) matrices for isogeometric analysis on one mapped
+ * tensor-product B-spline patch, and the stencil SpMV with the result.
  *
  * The operator is the variable-coefficient diffusion form pulled back to the
  * parametric domain (0,1)^n (Drzisga, Keith & Wohlmuth, "The surrogate matrix
@@ -74,8 +74,11 @@ extern "C" {
 
 /*
  * Arithmetic of the sum-factorised quadrature contractions (process-wide,
- * chosen per value dtype).  The basis tables, the coefficient tensor and all
- * accumulation into stored values are FP64 in every mode.
+ * chosen per value dtype).  The basis tables and pair weights are FP64 in
+ * every mode.  The coefficient tensor (and the mass form's |det Dphi|) is FP64
+ * too, except on the sine-product map with |amp| <= 0.07 and a constant,
+ * SIN2D or EXPSIN3D (|b| <= 1) kappa: there DF64 mode evaluates it in
+ * double-float arithmetic and FP32 mode in FP32.
  *   IGA_ARITH_FP64: native FP64 FMAs.
  *   IGA_ARITH_DF64: double-float arithmetic on the FP32 units -- each value is
  *     an unevaluated sum of two floats (about 48 significand bits), products
