@@ -5,6 +5,8 @@
   Gauss-Legendre rule; an interior row is the tensor product of the closed-form
   cardinal stencils h N_{2p+1}(k) (B-spline convolution identity).
 * Affine map x = A xi + b: M = |det A| M(identity) (change of variables).
+* Sine-product map: brute-force element-by-element assembly with a
+  finite-difference Jacobian.
 * Partition of unity: the sum of all entries is the quadrature of the measure of
   Omega, 1 for the sine-product maps of the unit square / cube (they fix its
   boundary) and |det A| for an affine map.
@@ -46,6 +48,46 @@ def test_identity_map_is_tensor_product_of_1d_mass(dim, p, n_el):
     for d in range(1, dim):
         ref = np.kron(_mass_1d(p, n_el[d]), ref)      # colexicographic: direction 0 fastest
     assert np.abs(D - ref).max() < 1e-15 * 10 * np.abs(ref).max()
+
+
+def _phi_sinprod(xi, amp):
+    """x_a = xi_a + amp prod_j sin(pi xi_j) (the map of the sine-product workloads)."""
+    return xi + amp * np.prod(np.sin(np.pi * xi), axis=-1, keepdims=True)
+
+
+@pytest.mark.parametrize("dim,p,n_el", [(2, 2, (5, 4)), (3, 1, (3, 4, 3)), (3, 2, (3, 3, 2))])
+def test_brute_force_sinprod(dim, p, n_el):
+    """Element-by-element assembly with scipy's B-splines, numpy's Gauss rule and a
+    central-difference Jacobian of the map (no formula shared with the oracle)."""
+    amp = 0.05
+    prob = W.Problem(dim=dim, p=p, n_el=n_el, map_kind="sinprod", map_amp=amp)
+    xg, wg = np.polynomial.legendre.leggauss(p + 1)
+    knots = [np.concatenate([np.zeros(p), np.linspace(0, 1, ne + 1), np.ones(p)]) for ne in n_el]
+    ms = [ne + p for ne in n_el]
+    D = np.zeros((prob.N, prob.N))
+    h = 1e-5
+    for e in np.ndindex(*n_el):
+        pts1, w1, B1 = [], [], []
+        for d in range(dim):
+            a, b = e[d] / n_el[d], (e[d] + 1) / n_el[d]
+            x = a + (b - a) * 0.5 * (xg + 1)
+            pts1.append(x)
+            w1.append(0.5 * (b - a) * wg)
+            B1.append(BSpline(knots[d], np.eye(ms[d]), p)(x))          # [points, m_d]
+        for g in np.ndindex(*([p + 1] * dim)):
+            xi = np.array([pts1[d][g[d]] for d in range(dim)])
+            J = np.empty((dim, dim))
+            for d in range(dim):
+                dx = np.zeros(dim)
+                dx[d] = h
+                J[:, d] = (_phi_sinprod(xi + dx, amp) - _phi_sinprod(xi - dx, amp)) / (2 * h)
+            w = np.prod([w1[d][g[d]] for d in range(dim)]) * abs(np.linalg.det(J))
+            B = B1[0][g[0]]
+            for d in range(1, dim):
+                B = np.kron(B1[d][g[d]], B)                                 # colexicographic
+            D += w * np.outer(B, B)
+    got = oracle.ell_to_dense(mass.mass_matrix(prob), prob)
+    assert np.abs(got - D).max() < 1e-9 * np.abs(D).max()
 
 
 # Centred cardinal B-spline of degree 2p+1 at the integers 0, 1, ..., p (the
