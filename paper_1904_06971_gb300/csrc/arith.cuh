@@ -16,6 +16,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 namespace iga {
 
 enum Arith { kArithF64 = 0, kArithDF = 1, kArithF32 = 2 };
@@ -27,6 +29,7 @@ struct PolF64 {
     __device__ __forceinline__ static acc zero() { return 0.0; }
     __device__ __forceinline__ static void mac(acc& a, store x, store v) { a = fma(x, v, a); }
     __device__ __forceinline__ static double to_double(const acc& a) { return a; }
+    __device__ __forceinline__ static float to_float(const acc& a) { return __double2float_rn(a); }
     __device__ __forceinline__ static store to_store(const acc& a) { return a; }
     __device__ __forceinline__ static store from_double(double v) { return v; }
 };
@@ -35,19 +38,53 @@ struct DFAcc {
     float h, l;
 };
 
-// Exact float -> double conversion by integer operations (sign, rebiased
-// exponent, widened significand), so it stays off GB300's slow FP64 pipe where
-// the F2F conversion instruction runs.  Zero, subnormal, infinite and NaN
-// inputs take the hardware conversion.
-__device__ __forceinline__ double f2d_exact(float f)
+// Exact float -> double conversion by integer operations only (sign, rebiased
+// exponent, widened significand; subnormals normalised with a leading-zero
+// count; infinities and NaNs keep their payload), so it stays off GB300's
+// slow FP64 pipe where the hardware conversion instruction runs.  Every case
+// is integer arithmetic and selects: no branch that could fall back on the
+// hardware conversion.  Host-callable for testing.
+__host__ __device__ __forceinline__ unsigned int f2d_bits_of(float f)
 {
-    const unsigned int u = __float_as_uint(f);
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    unsigned int u;
+    memcpy(&u, &f, sizeof(u));
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ int f2d_clz(unsigned int x)
+{
+#ifdef __CUDA_ARCH__
+    return __clz(x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+__host__ __device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned int u = f2d_bits_of(f);
     const unsigned int e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + (1023u - 127u)) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    const unsigned int m = u & 0x7fffffu;
+    // normal: exponent e - 127 + 1023; infinity / NaN: 0x7ff
+    unsigned long long ed = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e + 896u);
+    unsigned long long md = (unsigned long long)m << 29;
+    if (e == 0u) {
+        // m 2^-149 with the leading one of m at bit 31 - lz: exponent 905 - lz,
+        // the bits below it left-aligned in the 52-bit field (zero: m = 0)
+        const int lz = f2d_clz(m);
+        ed = m ? (unsigned long long)(905 - lz) : 0ull;
+        md = m ? (((unsigned long long)m << (21 + lz)) & 0xfffffffffffffull) : 0ull;
+    }
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) | (ed << 52) | md;
+#ifdef __CUDA_ARCH__
     return __longlong_as_double((long long)d);
+#else
+    double r;
+    memcpy(&r, &d, sizeof(r));
+    return r;
+#endif
 }
 
 struct PolDF {
@@ -70,6 +107,8 @@ struct PolDF {
         a.l = __fadd_rn(a.l, __fadd_rn(t, pe));
     }
     __device__ __forceinline__ static double to_double(const acc& a) { return f2d_exact(a.h) + f2d_exact(a.l); }
+    // the float nearest to hi + lo: one rounding of the exact sum
+    __device__ __forceinline__ static float to_float(const acc& a) { return __fadd_rn(a.h, a.l); }
     __device__ __forceinline__ static store to_store(const acc& a)
     {
         const float s = __fadd_rn(a.h, a.l);
@@ -89,6 +128,7 @@ struct PolF32 {
     __device__ __forceinline__ static acc zero() { return 0.f; }
     __device__ __forceinline__ static void mac(acc& a, store x, store v) { a = __fmaf_rn(x, v, a); }
     __device__ __forceinline__ static double to_double(const acc& a) { return (double)a; }
+    __device__ __forceinline__ static float to_float(const acc& a) { return a; }
     __device__ __forceinline__ static store to_store(const acc& a) { return a; }
     __device__ __forceinline__ static store from_double(double v) { return __double2float_rn(v); }
 };

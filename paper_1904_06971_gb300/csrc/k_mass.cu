@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_mass_x(Geo g, Tables T, BoxSet bs, d
             const int64_t row = i1 + (int64_t)g.m[0] * (i2 + (int64_t)g.m[1] * i3);
 #pragma unroll
             for (int dd = 0; dd < W; ++dd) {
-                if (ell_f32) ((float*)ell)[(int64_t)(slot0 + dd) * N + row] = (float)Pol::to_double(acc[l][dd]);
+                if (ell_f32) ((float*)ell)[(int64_t)(slot0 + dd) * N + row] = Pol::to_float(acc[l][dd]);
                 else ((double*)ell)[(int64_t)(slot0 + dd) * N + row] = Pol::to_double(acc[l][dd]);
             }
         } else {
