@@ -54,7 +54,9 @@ def stencils_1d(p):
 
 
 def test_stencils_1d_known_values():
-    """The survey's quoted p=2,3 values and the sum rules (mass sums to h, stiffness to 0)."""
+    """Cardinal B-spline values at the integers for p = 2 (mass h [66, 26, 1]/120, stiffness
+    [1, -1/3, -1/6]/h, from the B-spline convolution identity) and the sum rules
+    (mass sums to h, stiffness to 0)."""
     F, F1, F2 = stencils_1d(2)
     assert [F[k] for k in (0, 1, 2)] == [Fraction(66, 120), Fraction(26, 120), Fraction(1, 120)]
     assert [-F2[k] for k in (0, 1, 2)] == [Fraction(1), Fraction(-2, 6), Fraction(-1, 6)]
