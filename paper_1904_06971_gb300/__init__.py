@@ -91,6 +91,8 @@ def load():
         L.iga_batch_info.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_float)]
         L.iga_apply.argtypes = [H, vp, vp, vp]
+        L.iga_cg.argtypes = [H, vp, vp, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_double)]
         L.iga_apply_host.argtypes = [H, vp, vp, vp]
         L.iga_matrix_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64),
                                       ctypes.POINTER(i32)]
@@ -231,10 +233,7 @@ class Matrix:
         u = torch.empty_like(f)
         it = ctypes.c_int()
         rel = ctypes.c_double()
-        L = load()
-        L.iga_cg.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
-                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
-        _check(L.iga_cg(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()), float(tol), int(maxit),
+        _check(load().iga_cg(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()), float(tol), int(maxit),
                         ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(it), ctypes.byref(rel)))
         return u, it.value, rel.value
 
