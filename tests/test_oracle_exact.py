@@ -174,6 +174,49 @@ def test_coefficient_from_inverse_jacobian():
                                    rtol=1e-13, atol=1e-15)
 
 
+def _kappa_at(prob, x):
+    """kappa at the physical point x, written out from the workload definitions."""
+    if prob.kappa_kind == "const":
+        return prob.kappa_a
+    if prob.kappa_kind == "sin2d":
+        return prob.kappa_a + prob.kappa_b * np.sin(2 * np.pi * x[0]) * np.sin(2 * np.pi * x[1])
+    if prob.kappa_kind == "poly":
+        d = prob.kappa_deg
+        xs = list(x) + [0.0] * (3 - len(x))
+        return sum(prob.kappa_poly[a + (d + 1) * (b + (d + 1) * c)] * xs[0] ** a * xs[1] ** b * xs[2] ** c
+                   for a in range(d + 1) for b in range(d + 1) for c in range(d + 1))
+    raise ValueError(prob.kappa_kind)
+
+
+_POLY = tuple(np.random.default_rng(11).uniform(-0.2, 0.2, 27) + np.eye(1, 27).ravel())
+
+
+@pytest.mark.parametrize("prob", [
+    W.CFG_2D_P2.problem,
+    W.Problem(dim=3, p=2, n_el=(4, 4, 4), map_kind="sinprod", map_amp=0.03, kappa_kind="poly", kappa_deg=2,
+              kappa_poly=_POLY),
+    W.Problem(dim=2, p=2, n_el=(4, 4), map_kind="affine", affine=(1.3, 0.2, 0, -0.4, 0.8, 0, 0, 0, 1, 0.5, -1.0, 0),
+              kappa_kind="sin2d", kappa_a=2.0, kappa_b=0.7),
+    W.Problem(dim=3, p=1, n_el=(3, 3, 3), map_kind="affine",
+              affine=(1.1, 0.2, -0.1, 0.05, 0.9, 0.3, -0.2, 0.1, 1.2, 0.1, -0.2, 0.3), kappa_kind="poly", kappa_deg=2,
+              kappa_poly=_POLY),
+], ids=["2d_sin2d", "3d_poly_sinprod", "2d_sin2d_affine", "3d_poly_affine"])
+def test_coefficient_kappa_at_physical_point(prob):
+    """K = kappa(phi(xi)) |det J| J^{-1} J^{-T} for the other kappa kinds and maps, with kappa
+    evaluated independently at the physical point and numpy's inverse."""
+    rng = np.random.default_rng(6)
+    for _ in range(5):
+        xi = rng.uniform(0, 1, prob.dim)
+        x, J = oracle.geometry_map(prob, xi)
+        if prob.map_kind == "affine":
+            A = np.array(prob.affine[:9]).reshape(3, 3)[:prob.dim, :prob.dim]
+            np.testing.assert_allclose(x, A @ xi + np.array(prob.affine[9:9 + prob.dim]), rtol=1e-15, atol=1e-15)
+            np.testing.assert_allclose(J, A, rtol=0, atol=0)
+        Ji = np.linalg.inv(J)
+        np.testing.assert_allclose(oracle.coefficient(prob, xi), _kappa_at(prob, x) * abs(np.linalg.det(J)) * Ji @ Ji.T,
+                                   rtol=1e-13, atol=1e-15)
+
+
 PROBLEMS_SMALL = [
     W.Problem(dim=2, p=1, n_el=(6, 5), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.5),
     W.Problem(dim=2, p=2, n_el=(5, 7), map_kind="sinprod", map_amp=0.04, kappa_kind="sin2d", kappa_a=1.0, kappa_b=0.4),
