@@ -180,6 +180,30 @@ int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_ma
                                    int dtype, void* stream, iga_matrix_t* A);
 
 /*
+ * Sampling plan of a surrogate assembly, computed on the host only (no device
+ * call; usable without a GPU): the sample rows of Sec. 6 per direction and,
+ * per direction and offset component delta_d = -p..p, the interpolation domain
+ * and the samples inside it, exactly as iga_assemble_surrogate_domains (and,
+ * with IGA_DOMAINS_COMMON, iga_assemble_mass_surrogate) uses them.
+ *   patch, p, M, q, domains: as for iga_assemble_surrogate_domains.
+ *   cap: capacity per direction of `samples`.
+ *   samples: host int32 [3][cap]; direction d's sample indices, increasing, at samples[d * cap].
+ *   n_samples: host int32 [3]; the count per direction (1, with sample index 0, beyond dim).
+ *   dom_lo, dom_hi, dom_ns, dom_q: host int32 [3][2p+1], or all NULL; entry d (2p+1) + (delta_d + p):
+ *     the domain's first and last index (Omega~ = [2p, m-2p-1] for every component with
+ *     IGA_DOMAINS_COMMON; Omega~_delta's factor [p + max(0,-delta_d), m-p-1-max(0,delta_d)] with
+ *     IGA_DOMAINS_PER_OFFSET; an empty domain has hi = lo - 1 and no sample), the number of samples
+ *     in it, and the interpolation degree used (q lowered to that number - 1; 0 for an empty domain).
+ *   empty: host int; 1 when the region of interpolated rows has no row (every row exact), and
+ *     then nothing else is written.
+ * Errors: IGA_EINVAL / IGA_EUNSUPPORTED for arguments the assembly rejects, IGA_EINVAL when a
+ * direction has more than cap samples.
+ */
+int iga_surrogate_plan(const iga_patch_t* patch, int p, int M, int q, int domains, int cap, int32_t* samples,
+                       int32_t* n_samples, int32_t* dom_lo, int32_t* dom_hi, int32_t* dom_ns, int32_t* dom_q,
+                       int* empty);
+
+/*
  * Mass matrix M_ij = int_Omega B_i B_j dx = int B_i B_j |det Dphi| dxi (Sec. 8,
  * proof of the mass-matrix corollary), by the same (p+1)-point Gauss rule and
  * sum-factorised quadrature as iga_assemble_exact, with |det Dphi| as the

@@ -23,6 +23,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "assemble_mass", "assemble_mass_surrogate",
+           "surrogate_plan",
            "kappa_gradient", "stiffness_apply", "assemble_batch", "batch_info", "load", "launch_count",
            "profile_enable", "profile_read", "kernel_names", "set_arithmetic", "get_arithmetic",
            "F64", "F32", "ARITH"]
@@ -84,6 +85,9 @@ def load():
                                         ctypes.POINTER(H)]
         L.iga_assemble_mass_surrogate.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(H)]
+        P32 = ctypes.POINTER(i32)
+        L.iga_surrogate_plan.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, P32, P32, P32, P32, P32, P32, ctypes.POINTER(ctypes.c_int)]
         L.iga_kappa_gradient.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                          ctypes.POINTER(Kappa), ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.iga_assemble_batch.argtypes = [ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int, vp,
@@ -311,6 +315,30 @@ def assemble_mass_surrogate(prob, M: int, q: int, dtype="f64", stream=None, out:
                                               _dtype_code(dtype), ctypes.c_void_p(_stream_ptr(stream)),
                                               ctypes.byref(h)))
     return out if out is not None else Matrix(h.value)
+
+
+def surrogate_plan(prob, M: int, q: int, domains: str = "common") -> dict:
+    """Sampling plan of a surrogate assembly, computed on the host (iga_surrogate_plan; no GPU needed).
+
+    Returns {"empty": bool, "samples": [per-direction index arrays],
+    "domains": [per direction: [(lo, hi, n_samples, q_used) for delta_d = -p..p]]}."""
+    pt, _, _ = _structs(dataclasses.replace(prob, kappa_kind="const"))
+    p, W = int(prob.p), 2 * int(prob.p) + 1
+    cap = max(prob.m) + 1
+    samples = np.zeros((3, cap), dtype=np.int32)
+    ns = np.zeros(3, dtype=np.int32)
+    lo, hi, dns, dq = (np.zeros((3, W), dtype=np.int32) for _ in range(4))
+    empty = ctypes.c_int()
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    ptr = lambda a: a.ctypes.data_as(P32)                                      # noqa: E731
+    _check(load().iga_surrogate_plan(ctypes.byref(pt), p, int(M), int(q), DOMAINS[domains], cap, ptr(samples), ptr(ns),
+                                     ptr(lo), ptr(hi), ptr(dns), ptr(dq), ctypes.byref(empty)))
+    if empty.value:
+        return {"empty": True, "samples": [], "domains": []}
+    return {"empty": False,
+            "samples": [samples[d, :ns[d]].copy() for d in range(prob.dim)],
+            "domains": [[(int(lo[d, v]), int(hi[d, v]), int(dns[d, v]), int(dq[d, v])) for v in range(W)]
+                        for d in range(prob.dim)]}
 
 
 def set_arithmetic(dtype, arith: str):

@@ -633,6 +633,56 @@ int iga_assemble_mass_surrogate(const iga_patch_t* patch, int p, const iga_map_t
     return assemble(patch, p, map, &unit, true, M, q, IGA_DOMAINS_COMMON, dtype, stream, A, kFormMass);
 }
 
+int iga_surrogate_plan(const iga_patch_t* patch, int p, int M, int q, int domains, int cap, int32_t* samples,
+                       int32_t* n_samples, int32_t* dom_lo, int32_t* dom_hi, int32_t* dom_ns, int32_t* dom_q,
+                       int* empty)
+{
+    t_err.clear();
+    iga_map_t map;
+    memset(&map, 0, sizeof(map));
+    map.kind = IGA_MAP_IDENTITY;
+    iga_kappa_t unit;
+    memset(&unit, 0, sizeof(unit));
+    unit.kind = IGA_KAPPA_CONST;
+    unit.a = 1.0;
+    Geo g;
+    int rc = check_geometry(patch, p, &map, &unit, g);       // the patch and degree checks of the assembly
+    if (rc) return rc;
+    if (M < 1) return fail(IGA_EINVAL, "sampling parameter M must be >= 1 (got %d)", M);
+    if (q < 0 || q > kMaxQ) return fail(IGA_EUNSUPPORTED, "interpolation degree q must be in 0..%d (got %d)", kMaxQ, q);
+    if (domains != IGA_DOMAINS_COMMON && domains != IGA_DOMAINS_PER_OFFSET)
+        return fail(IGA_EINVAL, "domains must be IGA_DOMAINS_COMMON or IGA_DOMAINS_PER_OFFSET (got %d)", domains);
+    if (!samples || !n_samples || !empty || cap < 1) return fail(IGA_EINVAL, "samples, n_samples and empty must be non-null, cap >= 1");
+    const bool doms = dom_lo || dom_hi || dom_ns || dom_q;
+    if (doms && !(dom_lo && dom_hi && dom_ns && dom_q)) return fail(IGA_EINVAL, "dom_lo, dom_hi, dom_ns, dom_q: all or none");
+    g.form = kFormStiffness;
+    SplinePlan sp;
+    int emp = 0, k1[3] = {0, 0, 0};
+    rc = plan_spline(g, p, M, q, domains, sp, emp, k1);
+    if (rc) return rc;
+    *empty = emp;
+    if (emp) return IGA_OK;
+    for (int d = 0; d < 3; ++d)
+        if (sp.nu[d] > cap) return fail(IGA_EINVAL, "direction %d has %d samples, more than cap = %d", d, sp.nu[d], cap);
+    for (int d = 0; d < 3; ++d) {
+        n_samples[d] = sp.nu[d];
+        for (int a = 0; a < sp.nu[d]; ++a) samples[(int64_t)d * cap + a] = axis_sample(sp.ax[d], a);
+    }
+    if (doms) {
+        const int W = 2 * p + 1;
+        for (int d = 0; d < 3; ++d)
+            for (int v = 0; v < W; ++v) {
+                const int k = d * W + v;
+                const bool real = d < g.dim;
+                dom_lo[k] = real ? sp.k0[d][v] : 0;
+                dom_hi[k] = real ? sp.k0[d][v] + sp.L[d][v] - 1 : 0;
+                dom_ns[k] = real ? sp.ns[d][v] : 1;
+                dom_q[k] = (real && sp.ns[d][v] > 0) ? sp.qe[d][v] : 0;
+            }
+    }
+    return IGA_OK;
+}
+
 int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, int M,
                        int q, const double* ybar, const double* x, double* grad, void* stream_v)
 {
