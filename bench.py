@@ -7,9 +7,10 @@ with the kernel-preserving diagonal) followed by one stencil SpMV with it.
 The exact Gauss-quadrature assembly of the same patch is timed the same way
 and reported beside it, and so are the mass matrix of the same patch (its
 symmetric surrogate and exact assembly), the kappa adjoint and the batch of
-256 patches (outside the timed region).  Default workload: 3-D patch, p = 3, 64^3 elements,
-M = 8, q = 3, FP64 values (x_i = xi_i + 0.03 prod sin(pi xi_j),
-kappa = exp(0.5 sin(2 pi x) cos(2 pi y) sin(2 pi z))), synthetic and seeded.
+256 patches (outside the timed region).  Default workload: 3-D patch, p = 4, 96^3 elements
+(10^6 DoFs, 6.8e8 nonzeros), M = 8, q = 3, FP64 values (x_i = xi_i + 0.03 prod sin(pi xi_j),
+kappa = exp(0.5 sin(2 pi x) cos(2 pi y) sin(2 pi z))), synthetic and seeded.  Beside it the line
+reports the FP32-value precision tier of the same patch and the 64^3 p = 3 FP64 patch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
@@ -322,15 +323,25 @@ def cpu_baseline(wl, domains, target_s: float = 15.0):
             "seconds": timer.t_setup + t_rows}
 
 
+def reference_rows(timer, steps_total: int, budget_s: float = 150.0, cap_s: float = 15.0) -> int:
+    """Rows per reference step: calibrated like the cpu_baseline leg (a timed pilot of 64 rows) so that
+    one step costs min(cap_s, budget_s / steps_total) seconds of row work; the per-call overhead is then
+    amortised as in the baseline leg and the whole run stays within a few minutes."""
+    _, t64, _ = timer.step(64, seed=10 ** 6)
+    per_step = min(cap_s, max(1.0, budget_s / max(1, steps_total)))
+    return int(min(timer.wl.problem.N, max(64, per_step / max(t64 / 64, 1e-6))))
+
+
 def run_reference(args, wl):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     timer = OracleTimer(wl, args.domains)
+    rows = args.ref_rows or reference_rows(timer, args.warmup + args.steps)
     vals = []
     sample = ""
     for k in range(args.warmup + args.steps):
-        v, _, sample = timer.step(args.ref_rows, seed=k)
+        v, _, sample = timer.step(rows, seed=k)
         if k >= args.warmup:
             vals.append(v)
     value = float(np.mean(vals))
@@ -340,7 +351,8 @@ def run_reference(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded); FP64 CPU oracle on the host cores",
         "config": config_of(wl, world, args.domains),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": timer.cores, "kind": "oracle", "sample": sample,
+                         "rows_per_step": rows},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -501,6 +513,120 @@ def batch_report(iga, torch, steps: int, warmup: int):
             "create_s": t_create, "capture_and_tune_s": t_tune, "tuned_replay_ms": tuned_ms}
 
 
+def _time_steps(torch, step, steps: int, warmup: int, stream, profile_iga=None):
+    """Mean CUDA-event time (ms) of `step` on `stream`, 256 MiB L2 flush between steps."""
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if profile_iga is not None:
+        profile_iga.profile_read()
+        profile_iga.profile_enable(True)
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    prof = None
+    if profile_iga is not None:
+        profile_iga.profile_enable(False)
+        prof = {k: round(v[1] / steps, 4) for k, v in profile_iga.profile_read().items() if v[0]}
+    del flush
+    return float(np.mean([a.elapsed_time(b) for a, b in evs])), prof
+
+
+def fp32_tier_report(iga, torch, wl, A64, E64, exact_solution, args, steps: int = 10, warmup: int = 3):
+    """The FP32-value precision tier of the same patch: surrogate (+ SpMV) and exact steps, the entry
+    error of the FP32 matrices against the FP64 matrices of the same method (the FP64 values are parity-
+    tested against the FP64 oracle at 1e-12; the FP32 ones at 1e-5), and the discrete-solution error of
+    the FP32 surrogate's CG with FP64-residual iterative refinement against u_h of the exact FP64 matrix."""
+    prob = wl.problem
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype="f32")
+    E = iga.assemble_exact(prob, dtype="f32")
+
+    def s_step():
+        iga.assemble_surrogate(prob, wl.M, wl.q, dtype="f32", out=A)
+        A.apply(x, y)
+
+    def e_step():
+        iga.assemble_exact(prob, dtype="f32", out=E)
+        E.apply(x, y)
+
+    ms_s, prof_s = _time_steps(torch, s_step, steps, warmup, stream, iga)
+    ms_e, _ = _time_steps(torch, e_step, max(3, steps // 2), warmup, stream)
+    out = {"workload": wl.name.replace("_M8_q3", "_M8_q3_f32"), "values": "f32",
+           "arith": {"contractions": iga.get_arithmetic("f32"), "fill": "fp32", "diagonal": "compensated fp32",
+                     "spmv": "f32"},
+           "unit": UNIT, "surrogate": {"value": prob.nnz / (ms_s * 1e-3), "ms_per_step": ms_s, "kernels": prof_s},
+           "exact": {"value": prob.nnz / (ms_e * 1e-3), "ms_per_step": ms_e},
+           "speedup_surrogate_vs_exact": ms_e / ms_s}
+    vs32, vs64 = A.values().double(), A64.values()
+    scale = vs64.abs().max().item()
+    out["entry_error_vs_fp64_surrogate"] = float((vs32 - vs64).abs().max().item() / scale)
+    del vs32
+    ve32, ve64 = E.values().double(), E64.values()
+    out["exact_entry_error_vs_fp64_exact"] = float((ve32 - ve64).abs().max().item() / ve64.abs().max().item())
+    del ve32
+    vs32 = A.values().double()
+    out["surrogate_vs_exact_fp64_max_rel"] = float((vs32 - ve64).abs().max().item() / ve64.abs().max().item())
+    del vs32, vs64, ve64
+    if not args.no_solve:
+        f = torch.from_numpy(W.rhs_vector(prob.N, seed=wl.seed)).to("cuda")
+        u_e, _, _ = exact_solution(f)
+        u_s, it_s, res_s = A.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+        err = u_s - u_e
+        Ee = E64.apply(err).double()
+        Eu = E64.apply(u_e).double()
+        out["solution_error"] = {"rel_l2": float(err.norm() / u_e.norm()),
+                                 "rel_energy": float(torch.sqrt(torch.dot(err, Ee) / torch.dot(u_e, Eu))),
+                                 "cg_iters": it_s, "cg_rel_residual": res_s,
+                                 "solver": "FP32 CG inner solves, FP64 residuals (iterative refinement)",
+                                 "reference": "u_h of the exact FP64 matrix"}
+    A.destroy()
+    E.destroy()
+    return out
+
+
+def side_report(iga, torch, wl, steps: int, warmup: int):
+    """Surrogate (+ SpMV) and exact steps of another workload, with the surrogate's entry error."""
+    prob = wl.problem
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    tdt = torch.float64 if wl.dtype == "f64" else torch.float32
+    x = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dtype=tdt, device="cuda")
+    y = torch.empty_like(x)
+    A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype)
+    E = iga.assemble_exact(prob, dtype=wl.dtype)
+
+    def s_step():
+        iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype, out=A)
+        A.apply(x, y)
+
+    def e_step():
+        iga.assemble_exact(prob, dtype=wl.dtype, out=E)
+        E.apply(x, y)
+
+    ms_s, prof_s = _time_steps(torch, s_step, steps, warmup, stream, iga)
+    ms_e, prof_e = _time_steps(torch, e_step, steps, warmup, stream, iga)
+    vs, ve = A.values().double(), E.values().double()
+    err = float((vs - ve).abs().max().item() / ve.abs().max().item())
+    del vs, ve
+    A.destroy()
+    E.destroy()
+    return {"workload": wl.name, "values": wl.dtype, "unit": UNIT, "nnz": prob.nnz,
+            "surrogate": {"value": prob.nnz / (ms_s * 1e-3), "ms_per_step": ms_s, "kernels": prof_s},
+            "exact": {"value": prob.nnz / (ms_e * 1e-3), "ms_per_step": ms_e, "kernels": prof_e},
+            "speedup_surrogate_vs_exact": ms_e / ms_s, "surrogate_vs_exact_max_rel": err}
+
+
 def run_gpu(args, wl):
     import torch
     world, rank, local = dist_env()
@@ -605,17 +731,27 @@ def run_gpu(args, wl):
     t_e2e = (time.perf_counter() - t0) / K2
     t_e2e = max_over_ranks(dist, t_e2e, dev)
 
-    def accuracy(mat):
+    ref_solution = {}
+
+    def exact_solution(f):
+        """u_h of the exact FP64-quadrature matrix for the seeded load (one CG solve, reused)."""
+        if "u" not in ref_solution:
+            ref_solution["u"] = E.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+        return ref_solution["u"]
+
+    def accuracy(mat, exact=None):
         """Stated entry error max |A~ - A| / max |A| over all stored entries (GPU copies), the
         row sums, and the discrete-solution error of CG on both matrices with one load vector."""
-        vs, ve = mat.values(), E.values()
+        exact = E if exact is None else exact
+        vs, ve = mat.values(), exact.values()
         entry_err = float((vs.double() - ve.double()).abs().max().item() / ve.double().abs().max().item())
         del vs, ve
-        rowsum = float(mat.apply(torch.ones_like(x)).double().abs().max().item())
+        ones = torch.ones(prob.N, dtype=mat.torch_dtype, device=dev)
+        rowsum = float(mat.apply(ones).double().abs().max().item())
         solution = None
         if not args.no_solve:
             f = torch.from_numpy(W.rhs_vector(prob.N, seed=wl.seed)).to(dev)
-            u_e, it_e, res_e = E.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
+            u_e, it_e, res_e = exact_solution(f)
             u_s, it_s, res_s = mat.cg(f, tol=args.cg_tol, maxit=args.cg_maxit)
             err = u_s - u_e
             Ee = E.apply(err.to(tdt)).double()
@@ -623,11 +759,18 @@ def run_gpu(args, wl):
             solution = {"rel_l2": float(err.norm() / u_e.norm()),
                         "rel_energy": float(torch.sqrt(torch.dot(err, Ee) / torch.dot(u_e, Eu))),
                         "cg_iters": {"exact": it_e, "surrogate": it_s}, "cg_rel_residual": max(res_e, res_s),
-                        "load": "f_i ~ U[-1,1] (seeded), homogeneous Dirichlet"}
+                        "load": "f_i ~ U[-1,1] (seeded), homogeneous Dirichlet",
+                        "reference": "u_h of the exact FP64 matrix"}
         return {"surrogate_vs_exact_max_rel": entry_err, "row_sum_max_abs": rowsum}, solution
 
     entry, solution = accuracy(A)
     entry_o, solution_o = accuracy(B)
+    B.destroy()
+    extra = {}
+    if not args.no_extra and wl.name == W.CFG_3D_P4_F64.name:
+        extra["fp32_tier"] = fp32_tier_report(iga, torch, wl, A, E, exact_solution, args)
+    if not args.no_extra:
+        extra["p3_64cube"] = side_report(iga, torch, W.CFG_3D_P3, steps=8, warmup=3)
 
     if rank != 0:
         return 0
@@ -698,6 +841,7 @@ def run_gpu(args, wl):
         "cpu_baseline": base,
         "e2e": {"value": aggregate_value(prob.nnz, world, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": prob.N * esz, "d2h_bytes_per_step": prob.N * esz},
+        **extra,
         "adjoint": adjoint_report(iga, torch, dev, steps=5, warmup=3) if not args.no_adjoint else None,
         "batch": batch_report(iga, torch, steps=5, warmup=3) if not args.no_batch else None,
         "mass": mass_report(iga, torch, wl, steps=5, warmup=3) if not args.no_mass else None,
@@ -716,14 +860,17 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default=W.CFG_3D_P3.name, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default=W.CFG_3D_P4_F64.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the oracle baseline")
-    ap.add_argument("--ref-rows", type=int, default=48, help="rows per step of the reference (oracle) arm")
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="rows per step of the reference (oracle) arm (0: calibrated like the cpu_baseline leg)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the CG solution-error report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the kappa-gradient timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-patch batch timing")
     ap.add_argument("--no-mass", action="store_true", help="skip the mass-matrix timing")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the FP32-tier and 64^3 p = 3 reports beside the headline")
     ap.add_argument("--cg-tol", type=float, default=1e-10)
     ap.add_argument("--cg-maxit", type=int, default=20000)
     ap.add_argument("--domains", choices=["common", "per_offset"], default="common",

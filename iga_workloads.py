@@ -81,6 +81,14 @@ CFG_3D_P3 = Workload(
             kappa_kind="expsin3d", kappa_b=0.5),
     M=8, q=3, dtype="f64")
 
+# 3D, p = 4, 96^3 elements (10^6 DoFs, 729-point stencils, 6.8e8 nnz), same map family;
+# M = 8, q = 3; FP64 values: the largest single-patch workload, timed at the paper's precision.
+CFG_3D_P4_F64 = Workload(
+    "3d_p4_96cube_M8_q3",
+    Problem(dim=3, p=4, n_el=(96, 96, 96), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="expsin3d", kappa_b=0.5),
+    M=8, q=3, dtype="f64")
+
 # 3D precision case: same map family, p = 4, 96^3 elements; M = 8, q = 3; FP32 values.
 CFG_3D_P4 = Workload(
     "3d_p4_96cube_M8_q3_f32",
@@ -116,7 +124,15 @@ CFG_3D_P4_48 = Workload(
             kappa_kind="expsin3d", kappa_b=0.5),
     M=8, q=3, dtype="f32")
 
-WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4, CFG_3D_P3_40, CFG_3D_P3_BSPLINE, CFG_3D_P4_48)}
+# Smaller member of the p = 4 FP64 family for profiler captures (values 820 MB > L2).
+CFG_3D_P4_48_F64 = Workload(
+    "3d_p4_48cube_M8_q3",
+    Problem(dim=3, p=4, n_el=(48, 48, 48), map_kind="sinprod", map_amp=0.03,
+            kappa_kind="expsin3d", kappa_b=0.5),
+    M=8, q=3, dtype="f64")
+
+WORKLOADS = {w.name: w for w in (CFG_2D_P2, CFG_3D_P3, CFG_3D_P4_F64, CFG_3D_P4, CFG_3D_P3_40, CFG_3D_P3_BSPLINE,
+                                  CFG_3D_P4_48, CFG_3D_P4_48_F64)}
 
 
 def scaled(w: Workload, n_el: Tuple[int, ...], M: Optional[int] = None, p: Optional[int] = None) -> Workload:

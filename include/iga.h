@@ -352,14 +352,18 @@ const char* iga_kernel_name(int k);
  * stall, or applications whose own allocator owns the GPU's memory).
  *   values: caller-owned DEVICE buffer of S * N elements of dtype (double or
  *   float), written with the stencil-ELL layout above; the other arguments
- *   are those of iga_assemble_exact, and the result equals its values.
+ *   are those of iga_assemble_exact and are checked the same way (every map
+ *   and coefficient kind, IGA_KAPPA_BSPLINE3 included: its control values are
+ *   the caller's device memory), and the result equals its values.
  * Scratch: one file-scope device array of 64 MiB that every GPU which loads
  * this library reserves until the process exits.  A patch whose quadrature
  * scratch exceeds 64 MiB is rejected with IGA_EUNSUPPORTED before any work
  * (e.g. 3-D p = 3 fits up to about 12^3 elements, p = 2 up to 16^3; 2-D p = 2
  * up to several hundred elements per direction).
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture.  The kept address is not valid after
+ * cudaDeviceReset() or another teardown of the device's primary context.
  * Every call uses the same array, so calls whose work overlaps on the GPU
  * (other streams, other host threads) race and must be serialised by the
  * caller.  No part of the array needs to start at zero: every word a call

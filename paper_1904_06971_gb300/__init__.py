@@ -94,6 +94,8 @@ def load():
                                          ctypes.POINTER(H)]
         L.iga_batch_info.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_float)]
+        L.iga_assemble_exact_noalloc.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                                 ctypes.POINTER(Kappa), ctypes.c_int, vp, vp]
         L.iga_apply.argtypes = [H, vp, vp, vp]
         L.iga_cg.argtypes = [H, vp, vp, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_double)]

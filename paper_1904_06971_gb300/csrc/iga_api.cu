@@ -577,6 +577,11 @@ int report_error(int code, const char* msg)
 
 void set_capture(bool on) { t_capture = on; }
 
+int validate_geometry(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, Geo& g)
+{
+    return check_geometry(patch, p, map, kappa, g);
+}
+
 void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int64_t launch_count() { return g_launches.load(); }

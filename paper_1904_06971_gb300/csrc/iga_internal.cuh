@@ -137,6 +137,11 @@ void launch_end(int kid, cudaStream_t s);
 // Sets the calling thread's iga_last_error() message; returns code.
 int report_error(int code, const char* msg);
 
+// The argument checks of every assembly entry point (patch, degree, map,
+// coefficient) and the Geo they describe; sets iga_last_error() and returns
+// its status on failure (iga_api.cu).
+int validate_geometry(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, Geo& g);
+
 // Graph capture support (iga_batch.cu): no profiling events while capturing,
 // and replays of a captured graph add its kernel count to the launch counter.
 void set_capture(bool on);

@@ -38,7 +38,10 @@ int noalloc_fail(int code, const char* fmt, ...)
 }
 
 // Device address of g_noalloc_scratch per device, looked up once per device
-// (with that device current) by the first call on it.
+// (with that device current) by the first call on it.  The cached address
+// belongs to the device's primary context: it is not valid after
+// cudaDeviceReset() or any other teardown of that context, and calls made
+// after one would launch against a stale address.
 std::mutex g_sym_mu;
 double* g_sym_addr[128] = {};
 
@@ -68,39 +71,13 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
                                           const iga_kappa_t* kappa, int dtype, void* values, void* stream)
 {
     iga::report_error(IGA_OK, "");
-    if (!patch || !map || !kappa || !values) return noalloc_fail(IGA_EINVAL, "null argument");
-    if (patch->dim != 2 && patch->dim != 3) return noalloc_fail(IGA_EUNSUPPORTED, "dim must be 2 or 3");
-    if (p < 1 || p > kMaxP) return noalloc_fail(IGA_EUNSUPPORTED, "degree p must be in 1..%d", kMaxP);
-    if (dtype != IGA_F64 && dtype != IGA_F32) return noalloc_fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
-    if (map->kind < IGA_MAP_IDENTITY || map->kind > IGA_MAP_SINPROD) return noalloc_fail(IGA_EINVAL, "unknown map kind");
-    if (kappa->kind < IGA_KAPPA_CONST || kappa->kind > IGA_KAPPA_POLY) return noalloc_fail(IGA_EINVAL, "unknown kappa kind");
-    if (kappa->kind == IGA_KAPPA_EXPSIN3D && patch->dim != 3) return noalloc_fail(IGA_EINVAL, "IGA_KAPPA_EXPSIN3D needs dim 3");
-    if (kappa->kind == IGA_KAPPA_POLY && (kappa->deg < 0 || kappa->deg > 3))
-        return noalloc_fail(IGA_EINVAL, "polynomial kappa degree must be 0..3");
-
+    // the argument checks of iga_assemble_exact (every map and coefficient kind,
+    // B-spline coefficients included: their control values are the caller's)
     Geo g;
-    memset(&g, 0, sizeof(g));
-    g.dim = patch->dim;
-    g.p = p;
-    for (int d = 0; d < 3; ++d) {
-        if (d < g.dim) {
-            if (patch->n_el[d] < p + 1 || patch->n_el[d] > (1 << 22))
-                return noalloc_fail(IGA_EINVAL, "n_el[%d] = %d out of range (need >= p + 1)", d, patch->n_el[d]);
-            g.n_el[d] = patch->n_el[d];
-            g.m[d] = patch->n_el[d] + p;
-        } else {
-            g.n_el[d] = 1;
-            g.m[d] = 1;
-        }
-    }
-    g.map_kind = map->kind;
-    g.amp = map->amp;
-    for (int k = 0; k < 12; ++k) g.aff[k] = map->affine[k];
-    g.kappa_kind = kappa->kind;
-    g.kappa_deg = kappa->deg;
-    g.ka = kappa->a;
-    g.kb = kappa->b;
-    for (int k = 0; k < 64; ++k) g.poly[k] = kappa->poly[k];
+    int rc = validate_geometry(patch, p, map, kappa, g);
+    if (rc) return rc;
+    if (!values) return noalloc_fail(IGA_EINVAL, "values must be a non-null device pointer");
+    if (dtype != IGA_F64 && dtype != IGA_F32) return noalloc_fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
 
     // one box: every row of the patch
     const int Q = p + 1, W = 2 * p + 1, TT = Q * Q;
@@ -154,7 +131,7 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(IGA_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     double* scratch = nullptr;
-    int rc = scratch_address(dev, &scratch);
+    rc = scratch_address(dev, &scratch);
     if (rc) return rc;
 
     cudaStream_t st = (cudaStream_t)stream;

@@ -193,7 +193,7 @@ def _sampled_rows(prob, k, seed):
     return np.unique(np.array(rows, dtype=np.int64))
 
 
-@pytest.mark.parametrize("wl", [W.CFG_3D_P3, W.CFG_3D_P4], ids=lambda w: w.name)
+@pytest.mark.parametrize("wl", [W.CFG_3D_P3, W.CFG_3D_P4_F64, W.CFG_3D_P4], ids=lambda w: w.name)
 def test_full_size_surrogate_sampled_rows(iga, wl):
     prob = wl.problem
     tol = TOL64 if wl.dtype == "f64" else TOL32
@@ -226,15 +226,30 @@ def test_full_size_surrogate_sampled_rows(iga, wl):
     A.destroy()
 
 
-def test_full_size_exact_sampled_rows(iga):
-    wl = W.CFG_3D_P3
+@pytest.mark.parametrize("wl", [W.CFG_3D_P3, W.CFG_3D_P4_F64], ids=lambda w: w.name)
+def test_full_size_exact_sampled_rows(iga, wl):
     prob = wl.problem
     A = iga.assemble_exact(prob, dtype="f64")
     vals = A.values()
     rows = _sampled_rows(prob, 32, seed=2)
     got = vals[:, torch.from_numpy(rows).cuda()].cpu().numpy().T
     ref = oracle.exact_rows(prob, rows)
-    assert np.abs(got - ref).max() <= TOL64 * np.abs(ref).max()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= TOL64 * scale
+    # zero row sums and symmetry of the whole exact matrix at full size (Sec. 3.4, Sec. 5.3)
+    ones = torch.ones(prob.N, dtype=torch.float64, device="cuda")
+    assert A.apply(ones).abs().max().item() <= TOL64 * scale
+    offs = oracle.offsets(prob.dim, prob.p)
+    m = np.array(prob.m)
+    mi = oracle.multi_index(np.arange(prob.N), m)
+    worst = 0.0
+    for s in range(prob.S // 2 + 1, prob.S, max(1, prob.S // 40)):
+        mj = mi + offs[s]
+        ok = np.all((mj >= 0) & (mj < m), axis=1)
+        i = torch.from_numpy(np.nonzero(ok)[0]).cuda()
+        j = torch.from_numpy(oracle.surrogate.flat_index(mj[ok], m)).cuda()
+        worst = max(worst, (vals[s, i] - vals[prob.S - 1 - s, j]).abs().max().item())
+    assert worst <= TOL64 * scale
     A.destroy()
 
 

@@ -6,8 +6,11 @@ and writes into a caller-owned buffer.
 
 Checked through the C ABI against iga_assemble_exact, within the FP64 / FP32
 parity tolerances of the other GPU tests, on consecutive calls that reuse the
-same scratch array (its contents left by the previous call must not matter),
-and for the clear rejection of patches whose scratch exceeds the array.
+same scratch array (its contents left by the previous call must not matter);
+that calls after the first one change neither the device's free memory nor
+the library's or torch's pools; that B-spline coefficients (control values in
+caller memory) go through the same checks and give the same matrix; and the
+clear rejection of patches whose scratch exceeds the array.
 """
 import ctypes
 
@@ -31,17 +34,15 @@ def iga():
     return m
 
 
-def call_noalloc(iga, prob, out, dtype):
+def call_noalloc(iga, prob, out, dtype, ctrl=None, sync=True):
     L = iga.load()
-    f = L.iga_assemble_exact_noalloc
-    f.argtypes = [ctypes.POINTER(iga.Patch), ctypes.c_int, ctypes.POINTER(iga.Map), ctypes.POINTER(iga.Kappa),
-                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
-    f.restype = ctypes.c_int
-    pt, mp, kp = iga._structs(prob)
+    pt, mp, kp = iga._structs(prob, ctrl)
     stream = torch.cuda.current_stream().cuda_stream
-    rc = f(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp), 0 if dtype == "f64" else 1,
-           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
-    torch.cuda.synchronize()
+    rc = L.iga_assemble_exact_noalloc(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
+                                      0 if dtype == "f64" else 1, ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(stream))
+    if sync:
+        torch.cuda.synchronize()
     return rc
 
 
@@ -58,8 +59,8 @@ CASES = [
 ]
 
 
-def _reference(iga, prob, dtype):
-    A = iga.assemble_exact(prob, dtype=dtype)
+def _reference(iga, prob, dtype, ctrl=None):
+    A = iga.assemble_exact(prob, dtype=dtype, kappa_ctrl=ctrl)
     v = A.values_host()
     A.destroy()
     return v
@@ -96,3 +97,32 @@ def test_noalloc_rejects_patches_beyond_its_scratch(iga):
     msg = iga.load().iga_last_error().decode()
     assert "64 MiB" in msg
     assert torch.isnan(out).all().item()          # nothing was launched
+
+
+def test_noalloc_bspline_kappa(iga):
+    """B-spline coefficient (control values in caller memory): same checks and result as iga_assemble_exact."""
+    prob = W.Problem(dim=3, p=3, n_el=(9, 10, 8), map_kind="sinprod", map_amp=0.03, kappa_kind="bspline3",
+                     kappa_nctrl=(6, 5, 7), kappa_ctrl=W.lognormal_ctrl((6, 5, 7), seed=3))
+    ctrl = torch.tensor(prob.kappa_ctrl, dtype=torch.float64, device="cuda")
+    ref = _reference(iga, prob, "f64", ctrl)
+    for _ in range(2):
+        out = torch.full((prob.S, prob.N), float("nan"), dtype=torch.float64, device="cuda")
+        assert call_noalloc(iga, prob, out, "f64", ctrl) == 0, iga.load().iga_last_error().decode()
+        assert rel(out.cpu().numpy(), ref) <= TOL["f64"]
+
+
+def test_noalloc_allocates_nothing(iga):
+    """After a first call (which looks up the scratch address), further calls leave the device's free memory,
+    torch's caching allocator and the library's own pool untouched."""
+    prob, dt = CASES[1]
+    out = torch.empty((prob.S, prob.N), dtype=torch.float64, device="cuda")
+    assert call_noalloc(iga, prob, out, dt) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        assert call_noalloc(iga, prob, out, dt, sync=False) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
