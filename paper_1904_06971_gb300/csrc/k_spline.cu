@@ -442,6 +442,233 @@ __global__ void __launch_bounds__(kBlock) k_fill_common(Geo g, SplinePlan sp, Sp
     }
 }
 
+// Pass 1 and the kernel-preserving diagonal together for the common domain
+// Omega~: one block per line (x1, x2) of Omega~ rows along direction 0.  The
+// block stages in shared memory the partially evaluated field of every
+// interpolated slot at its own line (upper entries, Phi~_delta at x~_i) and at
+// the neighbouring line of each lower slot (Phi~_{-delta} at x~_j), plus the
+// direction-0 evaluation table; thread (ty, x0) then writes slots
+// s = ty, ty + Y, ... of row x0 (consecutive rows of one slot are contiguous),
+// gathers the frame columns, and sums the row for the diagonal.  FP64 values:
+// the interpolant in double-float, converted by integer operations (df2d_exact),
+// the row sum in renormalised double-float (interpolated entries) and FP64
+// (frame entries, a minority), the Y partial sums of a row added in FP64.
+// FP32 values: FP32 evaluation and a compensated FP32 row sum.
+constexpr int kFillLineThreads = 256;
+
+struct FillLineSmem {
+    int U, nu0, R0, XR, Y;
+    size_t bytes;
+};
+__host__ __device__ inline FillLineSmem fill_line_smem(int S, int first, int nu0, int R0, int Q1)
+{
+    FillLineSmem f;
+    f.U = S - first;
+    f.nu0 = nu0;
+    f.R0 = R0;
+    f.XR = R0 < kFillLineThreads ? R0 : kFillLineThreads;
+    f.Y = kFillLineThreads / f.XR;
+    // partial rows (upper, lower), evaluation table, spans (padded to 16 bytes), two doubles per thread
+    f.bytes = ((size_t)2 * f.U * nu0 + (size_t)Q1 * R0) * sizeof(float2) + (size_t)((R0 + 3) / 4) * 16 +
+              (size_t)kFillLineThreads * 2 * sizeof(double);
+    return f;
+}
+
+// renormalised double-float accumulation a += (bh, bl)
+__device__ __forceinline__ void df_add2(float& ah, float& al, float bh, float bl)
+{
+    const float s = __fadd_rn(ah, bh);
+    const float z = __fsub_rn(s, ah);
+    float t = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, z)), __fsub_rn(bh, z));
+    t = __fadd_rn(t, __fadd_rn(al, bl));
+    ah = __fadd_rn(s, t);
+    al = __fsub_rn(t, __fsub_rn(ah, s));
+}
+
+template <int P, int DIM, typename T, int Q1>
+__global__ void __launch_bounds__(kFillLineThreads) k_fill_line(Geo g, SplinePlan sp, SplineBufs sb, T* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    extern __shared__ __align__(16) unsigned char fl_smem[];
+    const int R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
+    const int R2 = (DIM == 3) ? sp.r1[2] - sp.r0[2] + 1 : 1;
+    const int first = sp.first;
+    const bool kp = first > C;                     // kernel-preserving: the diagonal is minus the row sum
+    const FillLineSmem f = fill_line_smem(S, first, sp.nu[0], R0, Q1);
+    const int nu0 = f.nu0, U = f.U;
+    float2* sPu = reinterpret_cast<float2*>(fl_smem);
+    float2* sPl = sPu + (size_t)U * nu0;
+    float2* sE = sPl + (size_t)U * nu0;
+    int* sSp = reinterpret_cast<int*>(sE + (size_t)Q1 * R0);
+    double* sD = reinterpret_cast<double*>(fl_smem + (f.bytes - (size_t)kFillLineThreads * 2 * sizeof(double)));
+    const int x1 = (int)(blockIdx.x % (unsigned)R1), x2 = (int)(blockIdx.x / (unsigned)R1);
+    const int tid = threadIdx.x;
+    const int L0 = sp.L[0][P], L1x = sp.Lmax[1], L2x = (DIM == 3) ? sp.Lmax[2] : 1;
+    const int64_t slot_stride = (int64_t)L2x * L1x * nu0;
+    // stage the partial-field rows, the evaluation table and the spans
+    for (int idx = tid; idx < U * nu0; idx += kFillLineThreads) {
+        const int u = idx / nu0, a = idx - u * nu0;
+        sPu[idx] = sb.partial[(int64_t)u * slot_stride + ((int64_t)x2 * L1x + x1) * nu0 + a];
+        const int sl = S - 1 - first - u;          // lower slot whose mirror is u
+        const int d1 = (sl / W) % W, d2 = (DIM == 3) ? sl / (W * W) : P;
+        const int y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;
+        if (y1 >= 0 && y1 < R1 && y2 >= 0 && y2 < R2)
+            sPl[idx] = sb.partial[(int64_t)u * slot_stride + ((int64_t)y2 * L1x + y1) * nu0 + a];
+    }
+    for (int idx = tid; idx < Q1 * R0; idx += kFillLineThreads) {
+        const int k = idx / R0, x0 = idx - k * R0;
+        sE[idx] = sb.eval0[P][(int64_t)k * L0 + x0];
+    }
+    for (int x0 = tid; x0 < R0; x0 += kFillLineThreads) sSp[x0] = sb.espan[0][P][x0];
+    __syncthreads();
+
+    const int m0 = g.m[0], m1 = g.m[1];
+    const int64_t N = (int64_t)m0 * m1 * ((DIM == 3) ? g.m[2] : 1);
+    const int i1 = sp.r0[1] + x1, i2 = (DIM == 3) ? sp.r0[2] + x2 : 0;
+    const int XR = f.XR, Y = f.Y;
+    const int ty = tid / XR, tx = tid - ty * XR;
+    for (int xb = 0; xb < R0; xb += XR) {
+        const int x0 = xb + tx;
+        const bool active = ty < Y && x0 < R0;
+        const int i0 = sp.r0[0] + x0;
+        const int64_t i = i0 + (int64_t)m0 * (i1 + (int64_t)m1 * i2);
+        float dh = 0.f, dl = 0.f;             // double-float / compensated FP32 row sum
+        double dframe = 0.0;                  // FP64 sum of gathered frame entries (FP64 values)
+        if (active) {
+            const int sp0 = sSp[x0];
+            for (int s = ty; s < S; s += Y) {
+                if (kp && s == C) continue;
+                const int d0 = s % W, d1 = (s / W) % W, d2 = (DIM == 3) ? s / (W * W) : P;
+                const int y0 = x0 + d0 - P, y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;
+                T out;
+                if (y0 >= 0 && y0 < R0 && y1 >= 0 && y1 < R1 && y2 >= 0 && y2 < R2) {
+                    const float2* row;
+                    int xe;
+                    if (s >= first) { row = sPu + (size_t)(s - first) * nu0 + sp0; xe = x0; }
+                    else { row = sPl + (size_t)(S - 1 - s - first) * nu0 + sSp[y0]; xe = y0; }
+                    if constexpr (sizeof(T) == 4) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int k = 0; k < Q1; ++k) acc = __fmaf_rn(sE[k * R0 + xe].x, row[k].x, acc);
+                        out = acc;
+                        // compensated row sum (two-sum, errors collected in dl)
+                        const float t = __fadd_rn(dh, acc);
+                        const float z = __fsub_rn(t, dh);
+                        dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(acc, z)));
+                        dh = t;
+                    } else {
+                        DFAcc acc = PolDF::zero();
+#pragma unroll
+                        for (int k = 0; k < Q1; ++k) PolDF::mac(acc, sE[k * R0 + xe], row[k]);
+                        out = df2d_exact(acc.h, acc.l);
+                        if (kp) df_add2(dh, dl, acc.h, acc.l);
+                    }
+                } else {
+                    const int64_t jrow = i + (d0 - P) + (int64_t)m0 * ((d1 - P) + (int64_t)m1 * (d2 - P));
+                    out = vals[(int64_t)(S - 1 - s) * N + jrow];
+                    if constexpr (sizeof(T) == 4) {
+                        const float v = (float)out;
+                        const float t = __fadd_rn(dh, v);
+                        const float z = __fsub_rn(t, dh);
+                        dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(v, z)));
+                        dh = t;
+                    } else {
+                        dframe += (double)out;
+                    }
+                }
+                vals[(int64_t)s * N + i] = out;
+            }
+        }
+        if (kp) {
+            // the Y partial sums of each row, added in a fixed order by thread ty = 0
+            if (sizeof(T) == 4) { sD[2 * tid] = (double)dh; sD[2 * tid + 1] = (double)dl; }
+            else { sD[2 * tid] = df2d_exact(dh, dl); sD[2 * tid + 1] = dframe; }
+            __syncthreads();
+            if (active && ty == 0) {
+                double sum = 0.0, lo = 0.0;
+                for (int y = 0; y < Y; ++y) {
+                    sum += sD[2 * (y * XR + tx)];
+                    lo += sD[2 * (y * XR + tx) + 1];
+                }
+                vals[(int64_t)C * N + i] = (T)(-(sum + lo));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int P, int DIM, typename T, int Q1>
+static bool fill_line_launch(const Geo& g, const SplinePlan& sp, const SplineBufs& sb, T* vals, cudaStream_t s)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    const int R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
+    const int R2 = (DIM == 3) ? sp.r1[2] - sp.r0[2] + 1 : 1;
+    const FillLineSmem f = fill_line_smem(S, sp.first, sp.nu[0], R0, Q1);
+    if (f.bytes > (size_t)160 * 1024) return false;
+    static bool attr_set = false;          // the attribute is idempotent; setting it twice is harmless
+    if (!attr_set) {
+        // set once outside any stream capture (a capture then uses the fallback kernels until then)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+        if (cudaFuncSetAttribute(k_fill_line<P, DIM, T, Q1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 160 * 1024) != cudaSuccess)
+            return false;
+        attr_set = true;
+    }
+    k_fill_line<P, DIM, T, Q1><<<(unsigned)((int64_t)R1 * R2), kFillLineThreads, f.bytes, s>>>(g, sp, sb, vals);
+    return true;
+}
+
+template <int P, int DIM, typename T>
+static bool fill_line_q(const Geo& g, const SplinePlan& sp, const SplineBufs& sb, T* vals, cudaStream_t s)
+{
+    switch (sp.qe[0][P] + 1) {
+    case 1: return fill_line_launch<P, DIM, T, 1>(g, sp, sb, vals, s);
+    case 2: return fill_line_launch<P, DIM, T, 2>(g, sp, sb, vals, s);
+    case 3: return fill_line_launch<P, DIM, T, 3>(g, sp, sb, vals, s);
+    case 4: return fill_line_launch<P, DIM, T, 4>(g, sp, sb, vals, s);
+    default: return false;      // q > 3: the general kernels
+    }
+}
+
+// The kernel-preserving diagonal of the frame rows only (rows with an index
+// outside [r0, r1] in some direction), after k_fill_line wrote those of Omega~.
+template <int P, int DIM, typename T>
+__global__ void __launch_bounds__(kBlock) k_diag_frame(int m0, int m1, int64_t N, int r0_0, int r1_0, int r0_1,
+                                                       int r1_1, int r0_2, int r1_2, T* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
+    if (i0 >= r0_0 && i0 <= r1_0 && i1 >= r0_1 && i1 <= r1_1 && (DIM == 2 || (i2 >= r0_2 && i2 <= r1_2))) return;
+    if constexpr (sizeof(T) == 4) {
+        float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+#pragma unroll 4
+        for (int s = 0; s < S; ++s) {
+            if (s == C) continue;
+            const float v = (float)vals[(int64_t)s * N + i];
+            const int k = s & 1;
+            const float t = __fadd_rn(hi[k], v);
+            const float z = __fsub_rn(t, hi[k]);
+            lo[k] = __fadd_rn(lo[k], __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(v, z)));
+            hi[k] = t;
+        }
+        vals[(int64_t)C * N + i] = (T)(-((double)hi[0] + (double)hi[1] + ((double)lo[0] + (double)lo[1])));
+    } else {
+        double part[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int s = 0; s < S; ++s)
+            if (s != C) part[s & 3] += (double)vals[(int64_t)s * N + i];
+        vals[(int64_t)C * N + i] = (T)(-((part[0] + part[1]) + (part[2] + part[3])));
+    }
+}
+
 template <int P, int DIM, typename T>
 static bool fill_common_q(const Geo& g, const SplinePlan& sp, const SplineBufs& sb, T* vals, unsigned grid,
                           cudaStream_t s)
@@ -501,6 +728,7 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
     const int W = 2 * P + 1;
     const int64_t N = (int64_t)g.m[0] * g.m[1] * (g.dim == 3 ? g.m[2] : 1);
     const unsigned gdiag = (unsigned)((N + kBlock - 1) / kBlock);
+    bool line = false;          // k_fill_line wrote the Omega~ rows' diagonals
     if (!empty_box) {
         const int64_t R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
         const int64_t total = R0 * R1 * (g.dim == 3 ? (int64_t)(sp.r1[2] - sp.r0[2] + 1) * W * W : W);
@@ -508,10 +736,17 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
         launch_begin(K_FILL, s);
         bool done = false;
         if (sp.all) {
-            if (g.dim == 3) done = f32 ? fill_common_q<P, 3, float>(g, sp, sb, (float*)ell, gfill, s)
-                                       : fill_common_q<P, 3, double>(g, sp, sb, (double*)ell, gfill, s);
-            else done = f32 ? fill_common_q<P, 2, float>(g, sp, sb, (float*)ell, gfill, s)
-                            : fill_common_q<P, 2, double>(g, sp, sb, (double*)ell, gfill, s);
+            if (g.dim == 3) line = f32 ? fill_line_q<P, 3, float>(g, sp, sb, (float*)ell, s)
+                                       : fill_line_q<P, 3, double>(g, sp, sb, (double*)ell, s);
+            else line = f32 ? fill_line_q<P, 2, float>(g, sp, sb, (float*)ell, s)
+                            : fill_line_q<P, 2, double>(g, sp, sb, (double*)ell, s);
+            done = line;
+            if (!done) {
+                if (g.dim == 3) done = f32 ? fill_common_q<P, 3, float>(g, sp, sb, (float*)ell, gfill, s)
+                                           : fill_common_q<P, 3, double>(g, sp, sb, (double*)ell, gfill, s);
+                else done = f32 ? fill_common_q<P, 2, float>(g, sp, sb, (float*)ell, gfill, s)
+                                : fill_common_q<P, 2, double>(g, sp, sb, (double*)ell, gfill, s);
+            }
         }
         if (!done) {
             if (g.dim == 3) {
@@ -527,7 +762,16 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
     if (sp.first <= sp.c && !empty_box) return;      // symmetric surrogate: no kernel-preserving diagonal
     if (g.form == kFormMass) return;                  // mass matrix with an empty Omega~: all rows exact
     launch_begin(K_DIAG, s);
-    if (g.dim == 3) {
+    if (line) {
+        const int r02 = g.dim == 3 ? sp.r0[2] : 0, r12 = g.dim == 3 ? sp.r1[2] : 0;
+        if (g.dim == 3) {
+            if (f32) k_diag_frame<P, 3, float><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (float*)ell);
+            else k_diag_frame<P, 3, double><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (double*)ell);
+        } else {
+            if (f32) k_diag_frame<P, 2, float><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (float*)ell);
+            else k_diag_frame<P, 2, double><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (double*)ell);
+        }
+    } else if (g.dim == 3) {
         if (f32) k_diag<P, 3, float><<<gdiag, kBlock, 0, s>>>(N, (float*)ell);
         else k_diag<P, 3, double><<<gdiag, kBlock, 0, s>>>(N, (double*)ell);
     } else {
