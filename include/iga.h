@@ -87,10 +87,16 @@ extern "C" {
  *     IGA_F64 values; its results agree with FP64 to ~1e-14 relative to the
  *     largest entry.
  *   IGA_ARITH_FP32: FP32 FMAs (only for IGA_F32 values; the default there).
+ *   IGA_ARITH_BF16X3: IGA_ARITH_FP32, except that the last contraction (stage X,
+ *     direction 0) of the rows whose stencil stays among cardinal B-splines runs
+ *     on the tensor cores: each FP32 operand split into three BF16 parts, the six
+ *     partial products of order <= 2 accumulated in FP32 (FP32-level accuracy,
+ *     Sec. 6 sum factorisation).  Only for IGA_F32 values, degrees 2..5.
  */
 #define IGA_ARITH_FP64 0
 #define IGA_ARITH_DF64 1
 #define IGA_ARITH_FP32 2
+#define IGA_ARITH_BF16X3 3
 
 typedef struct {
     int32_t dim;        /* n: 2 or 3 */

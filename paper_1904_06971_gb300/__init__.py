@@ -29,7 +29,7 @@ __all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "assemb
            "F64", "F32", "ARITH"]
 
 F64, F32 = 0, 1
-ARITH = {"fp64": 0, "df64": 1, "fp32": 2}
+ARITH = {"fp64": 0, "df64": 1, "fp32": 2, "bf16x3": 3}
 _MAP = {"identity": 0, "affine": 1, "sinprod": 2}
 _KAPPA = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3, "bspline3": 4}
 _lock = threading.Lock()

@@ -46,6 +46,7 @@ int cuda_fail(cudaError_t e, const char* what)
 
 // ---- contraction arithmetic per value dtype (process-wide) ----
 std::atomic<int> g_arith[2] = {{kArithDF}, {kArithF32}};
+std::atomic<int> g_tc_f32{0};          // FP32 values: stage X of the cardinal rows on the tensor cores
 
 // ---- launch counting and optional per-kernel event timing ----
 std::atomic<int64_t> g_launches{0};
@@ -59,7 +60,7 @@ thread_local bool t_capture = false;        // inside a graph capture: no profil
 
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
                              "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg",
-                             "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter"};
+                             "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter", "stage_x_tc"};
 
 cudaEvent_t take_event()
 {
@@ -494,6 +495,7 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
     }
     T.arith = arith;
+    T.tc = current_tc(dtype);
     const char* stage = "basis tables";
     ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
     if (ce == cudaSuccess) { stage = "pair tables"; ce = launch_pairs(g, bv, bd, wq, X, Xs, arith, st); }
@@ -567,6 +569,11 @@ cudaError_t pool_alloc(size_t bytes, cudaStream_t s, void** out)
 int current_arith(int dtype)
 {
     return g_arith[dtype == IGA_F32 ? 1 : 0].load();
+}
+
+int current_tc(int dtype)
+{
+    return (dtype == IGA_F32 && g_arith[1].load() == kArithF32) ? g_tc_f32.load() : 0;
 }
 
 int report_error(int code, const char* msg)
@@ -895,22 +902,25 @@ int iga_set_arithmetic(int dtype, int arith)
 {
     t_err.clear();
     if (dtype != IGA_F64 && dtype != IGA_F32) return fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
-    int a;
+    int a, tc = 0;
     switch (arith) {
     case IGA_ARITH_FP64: a = kArithF64; break;
     case IGA_ARITH_DF64: a = kArithDF; break;
     case IGA_ARITH_FP32: a = kArithF32; break;
+    case IGA_ARITH_BF16X3: a = kArithF32; tc = 1; break;
     default: return fail(IGA_EINVAL, "unknown arithmetic %d", arith);
     }
     if (dtype == IGA_F64 && a == kArithF32)
         return fail(IGA_EINVAL, "FP32 contractions cannot meet FP64 accuracy; use IGA_ARITH_FP64 or IGA_ARITH_DF64");
     g_arith[dtype == IGA_F32 ? 1 : 0].store(a);
+    if (dtype == IGA_F32) g_tc_f32.store(tc);
     return IGA_OK;
 }
 
 int iga_get_arithmetic(int dtype)
 {
     const int a = current_arith(dtype);
+    if (current_tc(dtype)) return IGA_ARITH_BF16X3;
     return a == kArithF64 ? IGA_ARITH_FP64 : a == kArithDF ? IGA_ARITH_DF64 : IGA_ARITH_FP32;
 }
 

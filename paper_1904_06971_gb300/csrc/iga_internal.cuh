@@ -121,12 +121,13 @@ struct Tables {
     const void* Xs[3];        // the same in the store type of the contraction arithmetic
     const float2* tdf[3];     // [G][4] double-float sin(pi xi), pi cos(pi xi), sin(2 pi xi), cos(2 pi xi)
     int arith;                // contraction arithmetic (arith.cuh: kArithF64 / kArithDF / kArithF32)
+    int tc;                   // FP32 arithmetic: stage X of the cardinal rows on the tensor cores (k_quad_tc.cu)
 };
 
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
     K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE,
-    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_NUM
+    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
@@ -153,8 +154,10 @@ void batch_forget(iga_matrix_t A);
 int assemble_patch(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
                    int M, int q, int domains, int dtype, void* stream, iga_matrix_t* out);
 
-// Contraction arithmetic (arith.cuh kind) chosen for matrices of value type dtype.
+// Contraction arithmetic (arith.cuh kind) chosen for matrices of value type dtype,
+// and whether its stage X runs on the tensor cores (FP32 values, IGA_ARITH_BF16X3).
 int current_arith(int dtype);
+int current_tc(int dtype);
 
 // ---- launchers implemented in the kernel files; all return cudaError_t ----
 cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[3],
@@ -170,6 +173,10 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
                         double* scratch, cudaStream_t s);
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
                           double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
+// Stage X of the cardinal rows of the explicit boxes on the tensor cores (BF16
+// parts, FP32 accumulation; FP32 values, p = 2..5); *used = false when it did not run.
+cudaError_t launch_stage_x_tc(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, float* ell,
+                              int64_t N, cudaStream_t s, bool* used);
 // The same three stages for the mass form: one scalar field (|det Dphi| at the
 // Gauss points) and the value-value pair weights only (k_mass.cu).
 cudaError_t launch_mass_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],

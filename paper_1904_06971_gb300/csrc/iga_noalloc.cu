@@ -149,6 +149,7 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
         T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
     }
     T.arith = arith;
+    T.tc = current_tc(dtype);
     e = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
     if (e == cudaSuccess) e = launch_pairs(g, bv, bd, wq, X, Xs, arith, st);
     if (e == cudaSuccess) e = launch_coef(g, T, bs, nblk[0], scratch, st);

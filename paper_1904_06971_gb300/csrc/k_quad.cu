@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_stage_y_f32(Geo g, Tables T, BoxS
 // ---------------------------------------------------------------------------
 template <class Pol, int P, int DIM, int LINES>
 __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, double* scratch,
-                                                    void* ell, int ell_f32, int64_t N, double* samples)
+                                                    void* ell, int ell_f32, int64_t N, double* samples, int skip_card)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
     const int d3 = (DIM == 3) ? (int)(pair3 % W) : 0;
     const int m0 = g.m[0];
     const bool card = has_card && i1 >= 2 * P && i1 <= m0 - 2 * P - 1;
+    if (skip_card && card && b.out_kind == 0) return;      // written by the tensor-core stage X
     const S* Xi = card ? sX : X0 + (int64_t)i1 * W * TT * 4;
     const int64_t gs = P3 * P2 * G0;        // group stride
     int nl = (int)(P2 - lg * LINES);
@@ -434,8 +435,17 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
             launch_end(K_STAGE_Y, s);
         }
         if (nb[3] > 0) {
+            int skip = 0;
+            if constexpr (Pol::kind == kArithF32) {
+                if (T.tc && ell_f32 && P >= 2) {
+                    bool used = false;
+                    cudaError_t e = launch_stage_x_tc(g, T, bs, scratch, (float*)ell, N, s, &used);
+                    if (e != cudaSuccess) return e;
+                    skip = used ? 1 : 0;
+                }
+            }
             launch_begin(K_STAGE_X, s);
-            k_stage_x<Pol, P, 3, kLinesX><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
+            k_stage_x<Pol, P, 3, kLinesX><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples, skip);
             launch_end(K_STAGE_X, s);
         }
     } else {
@@ -446,8 +456,17 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
             launch_end(K_STAGE_Y, s);
         }
         if (nb[3] > 0) {
+            int skip = 0;
+            if constexpr (Pol::kind == kArithF32) {
+                if (T.tc && ell_f32 && P >= 2) {
+                    bool used = false;
+                    cudaError_t e = launch_stage_x_tc(g, T, bs, scratch, (float*)ell, N, s, &used);
+                    if (e != cudaSuccess) return e;
+                    skip = used ? 1 : 0;
+                }
+            }
             launch_begin(K_STAGE_X, s);
-            k_stage_x<Pol, P, 2, kLinesX><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples);
+            k_stage_x<Pol, P, 2, kLinesX><<<(unsigned)nb[3], kBlock, 0, s>>>(g, T, bs, scratch, ell, ell_f32, N, samples, skip);
             launch_end(K_STAGE_X, s);
         }
     }

@@ -1,0 +1,300 @@
+// K3 stage X on the tensor cores (tcgen05, sm_103a), for FP32 values.
+//
+// Stage X contracts direction 0 (k_quad.cu): for a line (pair3, pair2) of the
+// stage-Y output T2 and a row i0 whose stencil stays among cardinal B-splines,
+//     A_row[delta0] = sum_g sum_t T2[g][line][(i0 - p - elo) Q + t] X_card[delta0][t][pat(g)],
+// t = a Q + r over the (p+1)^2 Gauss points of supp(B_i0); the pair weights
+// X_card are the same for every cardinal row (translation invariance, Sec. 2.2).
+// For 128 lines at a time this is a product of an MN-major A (lines x Gauss
+// points, a sliding window per row i0) and a K-major B (Gauss points x offsets,
+// 2p+1 <= 16 columns): one tcgen05 MMA chain per row into its own 16 columns of
+// tensor memory.  The window of row i0 starts Q rows after that of row i0 - 1,
+// so one shared-memory tile of the Gauss points of a chunk of rows serves all
+// of them without copies (the descriptor start moves by whole 16-byte K rows).
+//
+// FP32 accuracy from BF16 operands: every FP32 value x is split into three
+// BF16 parts x0 + x1 + x2 (each the rounded remainder of the previous ones, 24
+// significand bits in all); the six partial products of total order <= 2
+// (a0 b0, a0 b1, a1 b0, a0 b2, a1 b1, a2 b0) accumulate in FP32 in tensor
+// memory.  The dropped products are below 2^-24 of the terms, the size of the
+// FP32 rounding of the CUDA-core kernel they replace.
+//
+// Rows outside the cardinal range, one-row sample boxes and every other
+// arithmetic stay on the CUDA-core kernel of k_quad.cu.
+#include <cuda_bf16.h>
+
+#include "arith.cuh"
+#include "iga_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace iga {
+
+namespace {
+
+constexpr int kTcThreads = 256;         // 8 warps: all load and split, warp 0 lane 0 issues the MMAs
+constexpr int kTcLines = 128;           // MMA M: lines per block
+constexpr int kTcN = 16;                // MMA N: offsets delta0 (2p + 1 <= 11 used)
+constexpr int kTcSlices = 3;            // BF16 parts per FP32 value
+constexpr int kTcWaitIter = 1 << 22;    // polls of an mbarrier before the kernel gives up
+
+template <int P>
+struct TcShape {
+    static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
+    static constexpr int KW = (TT + 15) / 16 * 16;           // K rows of one window (zero weights beyond TT)
+    static constexpr int KSTEPS = KW / 16;
+    static constexpr int C = (P >= 5) ? 12 : 16;             // rows i0 per chunk (one tensor-memory block each)
+    static constexpr int ROWS = (C - 1) * Q + KW;            // Gauss points of a chunk's tile
+    static constexpr int A_SLICE = 16 * ROWS * 16;           // bytes of one BF16 part of the A tile (16 line groups)
+    static constexpr int A_BUF = kTcSlices * A_SLICE;        // bytes of one A tile
+    static constexpr int B_PART = kTcN * KW * 2;             // bytes of one BF16 part of one pattern's B
+    static constexpr int B_BYTES = 4 * kTcSlices * B_PART;
+    static constexpr int SMEM = 2 * A_BUF + B_BYTES + 64;    // two A tiles, B, barriers and the TMEM address
+    static constexpr int TMEM_COLS = (C * kTcN <= 128) ? 128 : (C * kTcN <= 256 ? 256 : 512);
+};
+
+// The three BF16 parts of x (round to nearest at each step; the remainders are exact in FP32).
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a0, __nv_bfloat16& a1, __nv_bfloat16& a2)
+{
+    a0 = __float2bfloat16_rn(x);
+    const float r1 = __fsub_rn(x, __bfloat162float(a0));
+    a1 = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(a1));
+    a2 = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+}  // namespace
+
+// Set when a tensor-core stage gave up waiting for its MMAs (never expected);
+// the rows it did not finish are written as NaN.
+__device__ int g_tc_status = 0;
+
+// One block per 128 consecutive lines (pair3, pair2) of box b; the rows i0 in
+// [i0_lo, i0_hi] (all cardinal) in chunks of C rows.  Per chunk and T2 group
+// (pattern of direction 0) the block loads the chunk's Gauss points of its
+// lines into a shared tile as three BF16 parts (MN-major: 16 groups of 8 lines,
+// one 16-byte row per Gauss point), and one thread issues, for every row of
+// the chunk, the MMAs of its window against the cardinal weights of that
+// pattern (K-major, 16 offset columns).  Two tiles alternate, so loading group
+// g + 1 overlaps the MMAs of group g; an mbarrier per tile tracks when its MMAs
+// are done.  After the fourth group the rows are read from tensor memory and
+// written to the stencil-ELL values.
+template <int P, int DIM>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch, float* ell, int64_t N)
+{
+    using Sh = TcShape<P>;
+    constexpr int Q = Sh::Q, W = Sh::W, TT = Sh::TT, KW = Sh::KW, C = Sh::C, ROWS = Sh::ROWS;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;                                   // [tile 2][part 3][line group 16][ROWS][16 B]
+    unsigned char* sB = tc_smem + 2 * Sh::A_BUF;                   // [group 4][part 3][n group 2][K block][128 B]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + Sh::B_BYTES);   // [0..1] tile consumed, [2] drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int64_t G0 = (int64_t)b.E[0] * Q;
+    const int64_t P3 = (DIM == 3) ? (int64_t)b.R[2] * W : 1;
+    const int64_t P2 = (int64_t)b.R[1] * W;
+    const int64_t total = P3 * P2;                    // lines of the box
+    const int64_t line0 = (int64_t)blockIdx.x * kTcLines;
+    const float* T2 = reinterpret_cast<const float*>(scratch + b.t2_off);
+    const int64_t gs = total * G0;                    // group stride of T2
+
+    // B: cardinal pair weights of direction 0 in three BF16 parts, one K-major
+    // [16 offsets x KW Gauss points] matrix per pattern (zero beyond 2p+1 and TT)
+    const float* Xc = reinterpret_cast<const float*>(T.Xs[0]) + (int64_t)(2 * P) * W * TT * 4;
+    for (int idx = tid; idx < 4 * kTcN * KW; idx += kTcThreads) {
+        const int gq = idx / (kTcN * KW), n = (idx / KW) % kTcN, k = idx % KW;
+        const int pat = 3 - gq;                       // T2 group 0: pattern 11, 1: 10, 2: 01, 3: 00
+        const float x = (n < W && k < TT) ? Xc[((int64_t)n * TT + k) * 4 + pat] : 0.f;
+        __nv_bfloat16 x0, x1, x2;
+        split3(x, x0, x1, x2);
+        const int off = ((n >> 3) * (KW / 8) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(sB + (size_t)gq * kTcSlices * Sh::B_PART);
+        base[off] = x0;
+        base[Sh::B_PART / 2 + off] = x1;
+        base[Sh::B_PART + off] = x2;
+    }
+    if (tid == 0) {
+        tc::bar_init(&bars[0], 1);
+        tc::bar_init(&bars[1], 1);
+        tc::bar_init(&bars[2], 1);
+        tc::fence_bar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, Sh::TMEM_COLS);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    // this thread's output line (epilogue): warp w reads tensor-memory lanes 32 (w % 4) ..
+    const int q4 = warp & 3, half = warp >> 2;
+    const int64_t my_line = line0 + q4 * 32 + lane;
+    int64_t rowbase = 0;
+    int slot0 = 0;
+    if (my_line < total) {
+        const int64_t pair3 = my_line / P2, pair2 = my_line - pair3 * P2;
+        const int i1 = b.rlo[1] + (int)(pair2 / W), d1 = (int)(pair2 % W);
+        const int i2 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
+        const int d2 = (DIM == 3) ? (int)(pair3 % W) : 0;
+        rowbase = (int64_t)g.m[0] * (i1 + (int64_t)g.m[1] * i2);
+        slot0 = W * (d1 + W * d2);
+    }
+
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(kTcLines, kTcN, 1, 0);
+    const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+    int use = 0;                      // A tiles filled so far
+    bool ok = true;
+    int done_to = i0_lo - 1;          // rows written so far
+    for (int c0 = i0_lo; c0 <= i0_hi && ok; c0 += C) {
+        const int nc = min(C, i0_hi - c0 + 1);
+        const int64_t row0 = (int64_t)(c0 - P - b.elo[0]) * Q;    // first Gauss point of the chunk's tile
+        for (int gq = 0; gq < 4; ++gq, ++use) {
+            const int buf = use & 1;
+            bool wok = true;
+            if (use >= 2) wok = tc::bar_wait(&bars[buf], (uint32_t)(((use >> 1) - 1) & 1), kTcWaitIter);
+            ok = __syncthreads_and(wok) != 0;
+            if (!ok) break;
+            unsigned char* tile = sA + (size_t)buf * Sh::A_BUF;
+            const float* src = T2 + (int64_t)gq * gs;
+            for (int item = tid; item < 16 * ROWS; item += kTcThreads) {
+                const int lg = item / ROWS, r = item - lg * ROWS;
+                const int64_t gp = row0 + r;
+                uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+                for (int l = 0; l < 8; l += 2) {
+                    const int64_t la = line0 + lg * 8 + l;
+                    const float va = (la < total && gp < G0) ? src[la * G0 + gp] : 0.f;
+                    const float vb = (la + 1 < total && gp < G0) ? src[(la + 1) * G0 + gp] : 0.f;
+                    __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+                    split3(va, a0, a1, a2);
+                    split3(vb, b0, b1, b2);
+                    w0[l / 2] = pack2(a0, b0);
+                    w1[l / 2] = pack2(a1, b1);
+                    w2[l / 2] = pack2(a2, b2);
+                }
+                const size_t off = ((size_t)lg * ROWS + r) * 16;
+                *reinterpret_cast<uint4*>(tile + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4*>(tile + Sh::A_SLICE + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint4*>(tile + 2 * Sh::A_SLICE + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t a_base = sA_addr + (uint32_t)(buf * Sh::A_BUF);
+                const uint32_t b_base = sB_addr + (uint32_t)(gq * kTcSlices * Sh::B_PART);
+                for (int c = 0; c < nc; ++c) {
+#pragma unroll
+                    for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
+                        const uint32_t arow = (uint32_t)(c * Q + ks * 16) * 16;
+                        // partial products a_i b_j of total order i + j <= 2
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) {
+                            const int pi = (k == 2 || k == 4) ? 1 : (k == 5 ? 2 : 0);
+                            const int pj = (k == 1 || k == 4) ? 1 : (k == 3 ? 2 : 0);
+                            const uint64_t ad = tc::sdesc(a_base + (uint32_t)(pi * Sh::A_SLICE) + arow, 128, ROWS * 16);
+                            const uint64_t bd = tc::sdesc(b_base + (uint32_t)(pj * Sh::B_PART + ks * 256), 128,
+                                                          (KW / 8) * 128);
+                            tc::mma_bf16(tmem + (uint32_t)(c * kTcN), ad, bd, IDESC, (gq | ks | k) ? 1u : 0u);
+                        }
+                    }
+                }
+                tc::commit(&bars[buf]);
+            }
+        }
+        if (!ok) break;
+        // the chunk's last MMAs (tile use - 1) done: read the rows out of tensor memory
+        const int last = use - 1;
+        ok = __syncthreads_and(tc::bar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), kTcWaitIter)) != 0;
+        if (!ok) break;
+        tc::fence_after_sync();
+        for (int c = half; c < nc; c += 2) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(c * kTcN), v);
+            if (my_line < total) {
+                const int64_t row = c0 + c + rowbase;
+#pragma unroll
+                for (int dd = 0; dd < W; ++dd) ell[(int64_t)(slot0 + dd) * N + row] = v[dd];
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        done_to = c0 + nc - 1;
+    }
+    if (!ok) {
+        // give up: mark the status, NaN the rows not written, let every issued MMA drain before freeing
+        if (tid == 0) {
+            atomicOr(&g_tc_status, 1);
+            tc::commit(&bars[2]);
+        }
+        tc::bar_wait(&bars[2], 0u, kTcWaitIter);
+        if (half == 0 && my_line < total)
+            for (int i0 = done_to + 1; i0 <= i0_hi; ++i0)
+                for (int dd = 0; dd < W; ++dd) ell[(int64_t)(slot0 + dd) * N + rowbase + i0] = __int_as_float(0x7fc00000);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, Sh::TMEM_COLS);
+}
+
+template <int P, int DIM>
+static cudaError_t stage_x_tc_boxes(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, float* ell,
+                                    int64_t N, cudaStream_t s, bool* used)
+{
+    using Sh = TcShape<P>;
+    constexpr int W = 2 * P + 1;
+    *used = false;
+    const int card_lo = 2 * P, card_hi = g.m[0] - 2 * P - 1;
+    if (card_hi < card_lo) return cudaSuccess;
+    static bool attr_set = false;        // idempotent; set outside any stream capture
+    if (!attr_set) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(k_stage_x_tc<P, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    for (int k = 0; k < bs.nb; ++k) {
+        const Box& b = bs.box[k];
+        const int lo = max(card_lo, b.rlo[0]), hi = min(card_hi, b.rlo[0] + b.R[0] - 1);
+        if (hi < lo) continue;
+        const int64_t lines = ((DIM == 3) ? (int64_t)b.R[2] * W : 1) * b.R[1] * W;
+        const int64_t grid = (lines + kTcLines - 1) / kTcLines;
+        if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+        launch_begin(K_STAGE_X_TC, s);
+        k_stage_x_tc<P, DIM><<<(unsigned)grid, kTcThreads, Sh::SMEM, s>>>(g, T, b, lo, hi, scratch, ell, N);
+        launch_end(K_STAGE_X_TC, s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    *used = true;
+    return cudaSuccess;
+}
+
+// Tensor-core stage X for the cardinal rows of every explicit box (FP32 values,
+// degrees 2..5); *used tells whether it ran (the CUDA-core stage X then skips
+// those rows).
+cudaError_t launch_stage_x_tc(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, float* ell,
+                              int64_t N, cudaStream_t s, bool* used)
+{
+    *used = false;
+    switch (g.p * 4 + g.dim) {
+    case 2 * 4 + 2: return stage_x_tc_boxes<2, 2>(g, T, bs, scratch, ell, N, s, used);
+    case 2 * 4 + 3: return stage_x_tc_boxes<2, 3>(g, T, bs, scratch, ell, N, s, used);
+    case 3 * 4 + 2: return stage_x_tc_boxes<3, 2>(g, T, bs, scratch, ell, N, s, used);
+    case 3 * 4 + 3: return stage_x_tc_boxes<3, 3>(g, T, bs, scratch, ell, N, s, used);
+    case 4 * 4 + 2: return stage_x_tc_boxes<4, 2>(g, T, bs, scratch, ell, N, s, used);
+    case 4 * 4 + 3: return stage_x_tc_boxes<4, 3>(g, T, bs, scratch, ell, N, s, used);
+    case 5 * 4 + 2: return stage_x_tc_boxes<5, 2>(g, T, bs, scratch, ell, N, s, used);
+    case 5 * 4 + 3: return stage_x_tc_boxes<5, 3>(g, T, bs, scratch, ell, N, s, used);
+    default: return cudaSuccess;
+    }
+}
+
+}  // namespace iga

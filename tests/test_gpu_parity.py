@@ -91,6 +91,41 @@ def test_exact_f32(iga, idx, arith):
     assert rel(v, ref) <= TOL32
 
 
+# patches with rows whose stencil stays among cardinal B-splines in direction 0
+# (m_0 >= 4p + 1): the FP32-value stage X of those rows runs on the tensor cores
+# under IGA_ARITH_BF16X3; line counts from a partial 128-line tile to many tiles
+TC_EXACT = [
+    W.Problem(dim=3, p=4, n_el=(20, 6, 5), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=2, p=3, n_el=(40, 9), map_kind="sinprod", map_amp=0.05, kappa_kind="sin2d", kappa_a=1.0,
+              kappa_b=0.5),
+    W.Problem(dim=3, p=2, n_el=(14, 9, 8), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.4),
+    W.Problem(dim=3, p=5, n_el=(24, 6, 6), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=3, p=3, n_el=(30, 13, 11), map_kind="sinprod", map_amp=0.03, kappa_kind="expsin3d", kappa_b=0.5),
+    W.Problem(dim=3, p=4, n_el=(17, 7, 6), map_kind="affine",
+              affine=(1.1, 0.2, -0.1, 0.05, 0.9, 0.3, -0.2, 0.1, 1.2, 0.1, 0.2, 0.3), kappa_kind="const", kappa_a=2.0),
+]
+
+
+@pytest.mark.parametrize("arith", ["bf16x3"], indirect=True)
+@pytest.mark.parametrize("prob", TC_EXACT, ids=lambda q: f"{q.dim}d_p{q.p}_{'x'.join(map(str, q.n_el))}")
+def test_exact_f32_tensor_core_stage(iga, prob, arith):
+    """Tensor-core stage X (BF16 parts, FP32 accumulation) against the FP64 oracle at the FP32 tolerance,
+    and against the FP32 CUDA-core contraction of the same matrix."""
+    iga.set_arithmetic("f32", "fp32")
+    ref32 = gpu_exact(iga, prob, "f32")
+    use(iga, "f32", arith)
+    assert iga.get_arithmetic("f32") == "bf16x3"
+    iga.profile_read()
+    iga.profile_enable(True)
+    v = gpu_exact(iga, prob, "f32")
+    iga.profile_enable(False)
+    prof = iga.profile_read()
+    assert prof["stage_x_tc"][0] >= 1            # the tensor-core kernel ran
+    ref = oracle.exact_matrix(prob)
+    assert rel(v, ref) <= TOL32
+    assert rel(v, ref32.astype(np.float64)) <= 2e-6
+
+
 SMALL_SURR = [
     (W.CFG_2D_P2.problem, 4, 3),
     (W.CFG_2D_P2.problem, 3, 2),
@@ -126,7 +161,7 @@ def test_surrogate_full_matrix(iga, prob, M, q, arith):
     assert rel(got, ref) <= TOL64
 
 
-@pytest.mark.parametrize("arith", ["fp32", "df64"], indirect=True)
+@pytest.mark.parametrize("arith", ["fp32", "df64", "bf16x3"], indirect=True)
 @pytest.mark.parametrize("idx", [7, 9, 12])
 def test_surrogate_f32(iga, idx, arith):
     use(iga, "f32", arith)
@@ -193,8 +228,11 @@ def _sampled_rows(prob, k, seed):
     return np.unique(np.array(rows, dtype=np.int64))
 
 
-@pytest.mark.parametrize("wl", [W.CFG_3D_P3, W.CFG_3D_P4_F64, W.CFG_3D_P4], ids=lambda w: w.name)
-def test_full_size_surrogate_sampled_rows(iga, wl):
+@pytest.mark.parametrize("wl,arith", [(W.CFG_3D_P3, "df64"), (W.CFG_3D_P4_F64, "df64"), (W.CFG_3D_P4, "fp32"),
+                                     (W.CFG_3D_P4, "bf16x3")], ids=["p3_64", "p4_96_f64", "p4_96_f32", "p4_96_f32_tc"],
+                         indirect=["arith"])
+def test_full_size_surrogate_sampled_rows(iga, wl, arith):
+    use(iga, wl.dtype, arith)
     prob = wl.problem
     tol = TOL64 if wl.dtype == "f64" else TOL32
     A = iga.assemble_surrogate(prob, wl.M, wl.q, dtype=wl.dtype)
