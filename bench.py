@@ -590,6 +590,40 @@ def fp32_tier_report(iga, torch, wl, A64, E64, exact_solution, args, steps: int 
                                  "cg_iters": it_s, "cg_rel_residual": res_s,
                                  "solver": "FP32 CG inner solves, FP64 residuals (iterative refinement)",
                                  "reference": "u_h of the exact FP64 matrix"}
+    # the same steps with stage X of the cardinal rows on the tensor cores (BF16x3 parts, FP32 accumulation)
+    saved = iga.get_arithmetic("f32")
+    try:
+        iga.set_arithmetic("f32", "bf16x3")
+        At = iga.assemble_surrogate(prob, wl.M, wl.q, dtype="f32")
+        Et = iga.assemble_exact(prob, dtype="f32")
+
+        def s_step_tc():
+            iga.assemble_surrogate(prob, wl.M, wl.q, dtype="f32", out=At)
+            At.apply(x, y)
+
+        def e_step_tc():
+            iga.assemble_exact(prob, dtype="f32", out=Et)
+            Et.apply(x, y)
+
+        ms_st, prof_st = _time_steps(torch, s_step_tc, steps, warmup, stream, iga)
+        ms_et, prof_et = _time_steps(torch, e_step_tc, max(3, steps // 2), warmup, stream, iga)
+        tc = {"arith": "bf16x3 tensor-core stage X (cardinal rows), FP32 elsewhere",
+              "surrogate": {"value": prob.nnz / (ms_st * 1e-3), "ms_per_step": ms_st, "kernels": prof_st},
+              "exact": {"value": prob.nnz / (ms_et * 1e-3), "ms_per_step": ms_et, "kernels": prof_et},
+              "speedup_surrogate_vs_exact": ms_et / ms_st}
+        vt, v64 = At.values().double(), A64.values()
+        tc["entry_error_vs_fp64_surrogate"] = float((vt - v64).abs().max().item() / v64.abs().max().item())
+        vc = A.values().double()
+        tc["entry_error_vs_fp32_cuda_cores"] = float((vt - vc).abs().max().item() / vc.abs().max().item())
+        del vt, vc, v64
+        vt, v64 = Et.values().double(), E64.values()
+        tc["exact_entry_error_vs_fp64_exact"] = float((vt - v64).abs().max().item() / v64.abs().max().item())
+        del vt, v64
+        out["tensor_core"] = tc
+        At.destroy()
+        Et.destroy()
+    finally:
+        iga.set_arithmetic("f32", saved)
     A.destroy()
     E.destroy()
     return out

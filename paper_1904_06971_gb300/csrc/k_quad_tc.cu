@@ -31,25 +31,33 @@ namespace iga {
 
 namespace {
 
-constexpr int kTcThreads = 256;         // 8 warps: all load and split, warp 0 lane 0 issues the MMAs
+constexpr int kTcThreads = 256;         // 8 warps: all copy and split, thread 0 issues the MMAs
 constexpr int kTcLines = 128;           // MMA M: lines per block
 constexpr int kTcN = 16;                // MMA N: offsets delta0 (2p + 1 <= 11 used)
 constexpr int kTcSlices = 3;            // BF16 parts per FP32 value
 constexpr int kTcWaitIter = 1 << 22;    // polls of an mbarrier before the kernel gives up
 
+// Tile shapes per degree.  A "job" is one (chunk of C rows i0, T2 group) pair:
+// its Gauss points (ROWS per line) are copied asynchronously into a raw FP32
+// tile, split into the BF16 tile, and consumed by the MMAs of the chunk's rows.
+// Raw tiles, BF16 tiles and tensor-memory blocks are all double-buffered.
 template <int P>
 struct TcShape {
     static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     static constexpr int KW = (TT + 15) / 16 * 16;           // K rows of one window (zero weights beyond TT)
     static constexpr int KSTEPS = KW / 16;
-    static constexpr int C = (P >= 5) ? 12 : 16;             // rows i0 per chunk (one tensor-memory block each)
+    static constexpr int C = (P >= 5) ? 4 : (P == 4 ? 8 : 16);   // rows i0 per chunk
     static constexpr int ROWS = (C - 1) * Q + KW;            // Gauss points of a chunk's tile
     static constexpr int A_SLICE = 16 * ROWS * 16;           // bytes of one BF16 part of the A tile (16 line groups)
-    static constexpr int A_BUF = kTcSlices * A_SLICE;        // bytes of one A tile
+    static constexpr int A_BUF = kTcSlices * A_SLICE;        // bytes of one BF16 tile
+    static constexpr int RAW = kTcLines * ROWS * 4;          // bytes of one raw FP32 tile
     static constexpr int B_PART = kTcN * KW * 2;             // bytes of one BF16 part of one pattern's B
     static constexpr int B_BYTES = 4 * kTcSlices * B_PART;
-    static constexpr int SMEM = 2 * A_BUF + B_BYTES + 64;    // two A tiles, B, barriers and the TMEM address
-    static constexpr int TMEM_COLS = (C * kTcN <= 128) ? 128 : (C * kTcN <= 256 ? 256 : 512);
+    static constexpr int SMEM = 2 * A_BUF + 2 * RAW + B_BYTES + 64;
+    static constexpr int TBLOCK = C * kTcN;                  // tensor-memory columns of one chunk
+    static constexpr int TMEM_COLS = (2 * TBLOCK <= 128) ? 128 : (2 * TBLOCK <= 256 ? 256 : 512);
+    static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
+    static_assert(2 * TBLOCK <= 512, "chunk does not fit in tensor memory");
 };
 
 // The three BF16 parts of x (round to nearest at each step; the remainders are exact in FP32).
@@ -74,15 +82,17 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 __device__ int g_tc_status = 0;
 
 // One block per 128 consecutive lines (pair3, pair2) of box b; the rows i0 in
-// [i0_lo, i0_hi] (all cardinal) in chunks of C rows.  Per chunk and T2 group
-// (pattern of direction 0) the block loads the chunk's Gauss points of its
-// lines into a shared tile as three BF16 parts (MN-major: 16 groups of 8 lines,
-// one 16-byte row per Gauss point), and one thread issues, for every row of
-// the chunk, the MMAs of its window against the cardinal weights of that
-// pattern (K-major, 16 offset columns).  Two tiles alternate, so loading group
-// g + 1 overlaps the MMAs of group g; an mbarrier per tile tracks when its MMAs
-// are done.  After the fourth group the rows are read from tensor memory and
-// written to the stencil-ELL values.
+// [i0_lo, i0_hi] (all cardinal) in chunks of C rows, four jobs (T2 groups =
+// direction-0 patterns) per chunk.  Per job: the block's threads copy the
+// job's Gauss points of their lines asynchronously into a raw FP32 tile (the
+// copy of the next job is in flight while this one is processed), split them
+// into three BF16 parts in an MN-major tile (16 groups of 8 lines, one 16-byte
+// row per Gauss point), and thread 0 issues, for every row of the chunk, the
+// MMAs of its window against the cardinal weights of that pattern (K-major,
+// 16 offset columns) into the chunk's tensor-memory block.  mbarriers tell
+// when a BF16 tile's MMAs are done; after the first job of chunk k has been
+// issued, the rows of chunk k - 1 are read out of the other tensor-memory
+// block and written to the stencil-ELL values.
 template <int P, int DIM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch, float* ell, int64_t N)
@@ -90,9 +100,10 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     using Sh = TcShape<P>;
     constexpr int Q = Sh::Q, W = Sh::W, TT = Sh::TT, KW = Sh::KW, C = Sh::C, ROWS = Sh::ROWS;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char* sA = tc_smem;                                   // [tile 2][part 3][line group 16][ROWS][16 B]
-    unsigned char* sB = tc_smem + 2 * Sh::A_BUF;                   // [group 4][part 3][n group 2][K block][128 B]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + Sh::B_BYTES);   // [0..1] tile consumed, [2] drain
+    unsigned char* sA = tc_smem;                                         // [2][part 3][line group 16][ROWS][16 B]
+    float* sR = reinterpret_cast<float*>(tc_smem + 2 * Sh::A_BUF);       // [2][line 128][ROWS]
+    unsigned char* sB = tc_smem + 2 * Sh::A_BUF + 2 * Sh::RAW;           // [group 4][part 3][n group 2][K block][128 B]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + Sh::B_BYTES);      // [0..1] BF16 tile consumed, [2] drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -103,6 +114,24 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     const int64_t line0 = (int64_t)blockIdx.x * kTcLines;
     const float* T2 = reinterpret_cast<const float*>(scratch + b.t2_off);
     const int64_t gs = total * G0;                    // group stride of T2
+    const int nchunks = (i0_hi - i0_lo) / C + 1;
+    const int jobs = 4 * nchunks;
+
+    // asynchronous copy of job j's Gauss points into raw tile j & 1 (zeros beyond the box)
+    auto issue_copy = [&](int j) {
+        const int c0 = i0_lo + (j >> 2) * C, gq = j & 3;
+        const int64_t row0 = (int64_t)(c0 - P - b.elo[0]) * Q;
+        const float* src = T2 + (int64_t)gq * gs;
+        float* dst = sR + (size_t)(j & 1) * (kTcLines * ROWS);
+        for (int idx = tid; idx < kTcLines * ROWS; idx += kTcThreads) {
+            const int l = idx / ROWS, r = idx - l * ROWS;
+            const int64_t line = line0 + l, gp = row0 + r;
+            const bool valid = line < total && gp < G0;
+            tc::cp_async4(dst + idx, valid ? src + line * G0 + gp : T2, valid);
+        }
+        tc::cp_async_commit();
+    };
+    issue_copy(0);
 
     // B: cardinal pair weights of direction 0 in three BF16 parts, one K-major
     // [16 offsets x KW Gauss points] matrix per pattern (zero beyond 2p+1 and TT)
@@ -145,78 +174,17 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
         rowbase = (int64_t)g.m[0] * (i1 + (int64_t)g.m[1] * i2);
         slot0 = W * (d1 + W * d2);
     }
-
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(kTcLines, kTcN, 1, 0);
-    const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
-    int use = 0;                      // A tiles filled so far
-    bool ok = true;
-    int done_to = i0_lo - 1;          // rows written so far
-    for (int c0 = i0_lo; c0 <= i0_hi && ok; c0 += C) {
-        const int nc = min(C, i0_hi - c0 + 1);
-        const int64_t row0 = (int64_t)(c0 - P - b.elo[0]) * Q;    // first Gauss point of the chunk's tile
-        for (int gq = 0; gq < 4; ++gq, ++use) {
-            const int buf = use & 1;
-            bool wok = true;
-            if (use >= 2) wok = tc::bar_wait(&bars[buf], (uint32_t)(((use >> 1) - 1) & 1), kTcWaitIter);
-            ok = __syncthreads_and(wok) != 0;
-            if (!ok) break;
-            unsigned char* tile = sA + (size_t)buf * Sh::A_BUF;
-            const float* src = T2 + (int64_t)gq * gs;
-            for (int item = tid; item < 16 * ROWS; item += kTcThreads) {
-                const int lg = item / ROWS, r = item - lg * ROWS;
-                const int64_t gp = row0 + r;
-                uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-                for (int l = 0; l < 8; l += 2) {
-                    const int64_t la = line0 + lg * 8 + l;
-                    const float va = (la < total && gp < G0) ? src[la * G0 + gp] : 0.f;
-                    const float vb = (la + 1 < total && gp < G0) ? src[(la + 1) * G0 + gp] : 0.f;
-                    __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-                    split3(va, a0, a1, a2);
-                    split3(vb, b0, b1, b2);
-                    w0[l / 2] = pack2(a0, b0);
-                    w1[l / 2] = pack2(a1, b1);
-                    w2[l / 2] = pack2(a2, b2);
-                }
-                const size_t off = ((size_t)lg * ROWS + r) * 16;
-                *reinterpret_cast<uint4*>(tile + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4*>(tile + Sh::A_SLICE + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                *reinterpret_cast<uint4*>(tile + 2 * Sh::A_SLICE + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-            }
-            tc::fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t a_base = sA_addr + (uint32_t)(buf * Sh::A_BUF);
-                const uint32_t b_base = sB_addr + (uint32_t)(gq * kTcSlices * Sh::B_PART);
-                for (int c = 0; c < nc; ++c) {
-#pragma unroll
-                    for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
-                        const uint32_t arow = (uint32_t)(c * Q + ks * 16) * 16;
-                        // partial products a_i b_j of total order i + j <= 2
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) {
-                            const int pi = (k == 2 || k == 4) ? 1 : (k == 5 ? 2 : 0);
-                            const int pj = (k == 1 || k == 4) ? 1 : (k == 3 ? 2 : 0);
-                            const uint64_t ad = tc::sdesc(a_base + (uint32_t)(pi * Sh::A_SLICE) + arow, 128, ROWS * 16);
-                            const uint64_t bd = tc::sdesc(b_base + (uint32_t)(pj * Sh::B_PART + ks * 256), 128,
-                                                          (KW / 8) * 128);
-                            tc::mma_bf16(tmem + (uint32_t)(c * kTcN), ad, bd, IDESC, (gq | ks | k) ? 1u : 0u);
-                        }
-                    }
-                }
-                tc::commit(&bars[buf]);
-            }
-        }
-        if (!ok) break;
-        // the chunk's last MMAs (tile use - 1) done: read the rows out of tensor memory
-        const int last = use - 1;
-        ok = __syncthreads_and(tc::bar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), kTcWaitIter)) != 0;
-        if (!ok) break;
+    // rows of chunk k out of tensor-memory block k & 1, once its last job's MMAs are done
+    auto epilogue = [&](int k) -> bool {
+        const int last = 4 * k + 3;
+        const bool ok = __syncthreads_and(tc::bar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), kTcWaitIter)) != 0;
+        if (!ok) return false;
         tc::fence_after_sync();
+        const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
+        const uint32_t tb = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((k & 1) * Sh::TBLOCK);
         for (int c = half; c < nc; c += 2) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(c * kTcN), v);
+            tc::tmem_ld16(tb + (uint32_t)(c * kTcN), v);
             if (my_line < total) {
                 const int64_t row = c0 + c + rowbase;
 #pragma unroll
@@ -224,21 +192,94 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
             }
         }
         tc::fence_before_sync();
+        return true;
+    };
+
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(kTcLines, kTcN, 1, 0);
+    const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+    bool ok = true;
+    int done_chunks = 0;              // chunks whose rows are written
+    for (int j = 0; j < jobs; ++j) {
+        const int k = j >> 2, gq = j & 3, buf = j & 1;
+        const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
+        // raw tile (j + 1) & 1 was last read by job j - 1, whose split ended in a barrier
+        if (j + 1 < jobs) {
+            issue_copy(j + 1);
+            tc::cp_async_wait<1>();
+        } else {
+            tc::cp_async_wait<0>();
+        }
+        // BF16 tile buf was last read by the MMAs of job j - 2
+        const bool wok = (j >= 2) ? tc::bar_wait(&bars[buf], (uint32_t)(((j >> 1) - 1) & 1), kTcWaitIter) : true;
+        ok = __syncthreads_and(wok) != 0;            // also makes every thread's copies of job j visible
+        if (!ok) break;
+        const float* raw = sR + (size_t)buf * (kTcLines * ROWS);
+        unsigned char* tile = sA + (size_t)buf * Sh::A_BUF;
+        for (int item = tid; item < 16 * ROWS; item += kTcThreads) {
+            const int lg = item / ROWS, r = item - lg * ROWS;
+            const float* rp = raw + (size_t)lg * 8 * ROWS + r;
+            uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+            for (int l = 0; l < 8; l += 2) {
+                __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+                split3(rp[l * ROWS], a0, a1, a2);
+                split3(rp[(l + 1) * ROWS], b0, b1, b2);
+                w0[l / 2] = pack2(a0, b0);
+                w1[l / 2] = pack2(a1, b1);
+                w2[l / 2] = pack2(a2, b2);
+            }
+            const size_t off = ((size_t)lg * ROWS + r) * 16;
+            *reinterpret_cast<uint4*>(tile + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+            *reinterpret_cast<uint4*>(tile + Sh::A_SLICE + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+            *reinterpret_cast<uint4*>(tile + 2 * Sh::A_SLICE + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        }
+        tc::fence_async_smem();
         __syncthreads();
-        done_to = c0 + nc - 1;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a_base = sA_addr + (uint32_t)(buf * Sh::A_BUF);
+            const uint32_t b_base = sB_addr + (uint32_t)(gq * kTcSlices * Sh::B_PART);
+            const uint32_t d_base = tmem + (uint32_t)((k & 1) * Sh::TBLOCK);
+            for (int c = 0; c < nc; ++c) {
+#pragma unroll
+                for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
+                    const uint32_t arow = (uint32_t)(c * Q + ks * 16) * 16;
+                    // partial products a_i b_j of total order i + j <= 2
+#pragma unroll
+                    for (int pr = 0; pr < 6; ++pr) {
+                        const int pi = (pr == 2 || pr == 4) ? 1 : (pr == 5 ? 2 : 0);
+                        const int pj = (pr == 1 || pr == 4) ? 1 : (pr == 3 ? 2 : 0);
+                        const uint64_t ad = tc::sdesc(a_base + (uint32_t)(pi * Sh::A_SLICE) + arow, 128, ROWS * 16);
+                        const uint64_t bd = tc::sdesc(b_base + (uint32_t)(pj * Sh::B_PART + ks * 256), 128,
+                                                      (KW / 8) * 128);
+                        tc::mma_bf16(d_base + (uint32_t)(c * kTcN), ad, bd, IDESC, (gq | ks | pr) ? 1u : 0u);
+                    }
+                }
+            }
+            tc::commit(&bars[buf]);
+        }
+        if (gq == 0 && k >= 1) {
+            if (!epilogue(k - 1)) { ok = false; break; }
+            done_chunks = k;
+        }
+    }
+    if (ok) {
+        ok = epilogue(nchunks - 1);
+        if (ok) done_chunks = nchunks;
     }
     if (!ok) {
-        // give up: mark the status, NaN the rows not written, let every issued MMA drain before freeing
+        // give up: mark the status, let the copies and every issued MMA drain, NaN the rows not written
+        tc::cp_async_wait<0>();
         if (tid == 0) {
             atomicOr(&g_tc_status, 1);
             tc::commit(&bars[2]);
         }
         tc::bar_wait(&bars[2], 0u, kTcWaitIter);
         if (half == 0 && my_line < total)
-            for (int i0 = done_to + 1; i0 <= i0_hi; ++i0)
-                for (int dd = 0; dd < W; ++dd) ell[(int64_t)(slot0 + dd) * N + rowbase + i0] = __int_as_float(0x7fc00000);
+            for (int i0 = i0_lo + done_chunks * C; i0 <= i0_hi; ++i0)
+                for (int dd = 0; dd < W; ++dd)
+                    ell[(int64_t)(slot0 + dd) * N + rowbase + i0] = __int_as_float(0x7fc00000);
     }
-    tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, Sh::TMEM_COLS);
 }

@@ -447,14 +447,16 @@ __global__ void __launch_bounds__(kBlock) k_fill_common(Geo g, SplinePlan sp, Sp
 // block stages in shared memory the partially evaluated field of every
 // interpolated slot at its own line (upper entries, Phi~_delta at x~_i) and at
 // the neighbouring line of each lower slot (Phi~_{-delta} at x~_j), plus the
-// direction-0 evaluation table; thread (ty, x0) then writes slots
-// s = ty, ty + Y, ... of row x0 (consecutive rows of one slot are contiguous),
-// gathers the frame columns, and sums the row for the diagonal.  FP64 values:
-// the interpolant in double-float, converted by integer operations (df2d_exact),
+// direction-0 evaluation table.  Thread (ty, x0) then takes row x0 and the
+// offset pairs (delta_1, delta_2) number ty, ty + Y, ...: for each pair it
+// writes the 2p+1 slots delta_0 = -p..p (consecutive rows of one slot are
+// contiguous), gathering the frame columns, with the upper evaluation row held
+// in registers, and sums the row for the diagonal.  FP64 values: the
+// interpolant in double-float, converted by integer operations (df2d_exact),
 // the row sum in renormalised double-float (interpolated entries) and FP64
 // (frame entries, a minority), the Y partial sums of a row added in FP64.
 // FP32 values: FP32 evaluation and a compensated FP32 row sum.
-constexpr int kFillLineThreads = 256;
+constexpr int kFillLineThreads = 512;
 
 struct FillLineSmem {
     int U, nu0, R0, XR, Y;
@@ -538,47 +540,66 @@ __global__ void __launch_bounds__(kFillLineThreads) k_fill_line(Geo g, SplinePla
         double dframe = 0.0;                  // FP64 sum of gathered frame entries (FP64 values)
         if (active) {
             const int sp0 = sSp[x0];
-            for (int s = ty; s < S; s += Y) {
-                if (kp && s == C) continue;
-                const int d0 = s % W, d1 = (s / W) % W, d2 = (DIM == 3) ? s / (W * W) : P;
-                const int y0 = x0 + d0 - P, y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;
-                T out;
-                if (y0 >= 0 && y0 < R0 && y1 >= 0 && y1 < R1 && y2 >= 0 && y2 < R2) {
-                    const float2* row;
-                    int xe;
-                    if (s >= first) { row = sPu + (size_t)(s - first) * nu0 + sp0; xe = x0; }
-                    else { row = sPl + (size_t)(S - 1 - s - first) * nu0 + sSp[y0]; xe = y0; }
-                    if constexpr (sizeof(T) == 4) {
-                        float acc = 0.f;
+            float2 Eu[Q1];                    // direction-0 evaluation row of the upper entries (at x~_i)
 #pragma unroll
-                        for (int k = 0; k < Q1; ++k) acc = __fmaf_rn(sE[k * R0 + xe].x, row[k].x, acc);
-                        out = acc;
-                        // compensated row sum (two-sum, errors collected in dl)
-                        const float t = __fadd_rn(dh, acc);
-                        const float z = __fsub_rn(t, dh);
-                        dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(acc, z)));
-                        dh = t;
-                    } else {
-                        DFAcc acc = PolDF::zero();
+            for (int k = 0; k < Q1; ++k) Eu[k] = sE[k * R0 + x0];
+            constexpr int NPAIR = (DIM == 3) ? W * W : W;
+            for (int pr = ty; pr < NPAIR; pr += Y) {
+                const int d1 = pr % W, d2 = (DIM == 3) ? pr / W : P;
+                const int y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;
+                const bool in12 = y1 >= 0 && y1 < R1 && y2 >= 0 && y2 < R2;
+                const int sbase = W * (d1 + W * ((DIM == 3) ? d2 : 0));
+                // frame columns of the pair (the exact A_ji of frame row j), all loads issued before the
+                // pair's stores: they read frame rows, which this kernel never writes
+                const int64_t jb = i - P + (int64_t)m0 * ((d1 - P) + (int64_t)m1 * (d2 - P));
+                T gv[W];
 #pragma unroll
-                        for (int k = 0; k < Q1; ++k) PolDF::mac(acc, sE[k * R0 + xe], row[k]);
-                        out = df2d_exact(acc.h, acc.l);
-                        if (kp) df_add2(dh, dl, acc.h, acc.l);
-                    }
-                } else {
-                    const int64_t jrow = i + (d0 - P) + (int64_t)m0 * ((d1 - P) + (int64_t)m1 * (d2 - P));
-                    out = vals[(int64_t)(S - 1 - s) * N + jrow];
-                    if constexpr (sizeof(T) == 4) {
-                        const float v = (float)out;
-                        const float t = __fadd_rn(dh, v);
-                        const float z = __fsub_rn(t, dh);
-                        dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(v, z)));
-                        dh = t;
-                    } else {
-                        dframe += (double)out;
-                    }
+                for (int d0 = 0; d0 < W; ++d0) {
+                    const int y0 = x0 + d0 - P;
+                    const bool gat = !(in12 && y0 >= 0 && y0 < R0) && !(kp && sbase + d0 == C);
+                    gv[d0] = gat ? vals[(int64_t)(S - 1 - sbase - d0) * N + jb + d0] : (T)0;
                 }
-                vals[(int64_t)s * N + i] = out;
+#pragma unroll
+                for (int d0 = 0; d0 < W; ++d0) {
+                    const int s = sbase + d0;
+                    if (kp && s == C) continue;
+                    const int y0 = x0 + d0 - P;
+                    T out;
+                    if (in12 && y0 >= 0 && y0 < R0) {
+                        const bool upper = s >= first;
+                        const float2* row = upper ? sPu + (size_t)(s - first) * nu0 + sp0
+                                                  : sPl + (size_t)(S - 1 - s - first) * nu0 + sSp[y0];
+                        if constexpr (sizeof(T) == 4) {
+                            float acc = 0.f;
+#pragma unroll
+                            for (int k = 0; k < Q1; ++k)
+                                acc = __fmaf_rn(upper ? Eu[k].x : sE[k * R0 + y0].x, row[k].x, acc);
+                            out = acc;
+                            const float t = __fadd_rn(dh, acc);
+                            const float z = __fsub_rn(t, dh);
+                            dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(acc, z)));
+                            dh = t;
+                        } else {
+                            DFAcc acc = PolDF::zero();
+#pragma unroll
+                            for (int k = 0; k < Q1; ++k) PolDF::mac(acc, upper ? Eu[k] : sE[k * R0 + y0], row[k]);
+                            out = df2d_exact(acc.h, acc.l);
+                            if (kp) df_add2(dh, dl, acc.h, acc.l);
+                        }
+                    } else {
+                        out = gv[d0];
+                        if constexpr (sizeof(T) == 4) {
+                            const float v = (float)out;
+                            const float t = __fadd_rn(dh, v);
+                            const float z = __fsub_rn(t, dh);
+                            dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(v, z)));
+                            dh = t;
+                        } else {
+                            dframe += (double)out;
+                        }
+                    }
+                    vals[(int64_t)s * N + i] = out;
+                }
             }
         }
         if (kp) {

@@ -5,10 +5,12 @@
 // stencil stays inside the index range skip the bounds tests.
 //
 // FP64 values: GB300 runs FP64 FMAs at 1/64 of the FP32 rate, below what the
-// HBM stream of the values needs, so the products are formed in double-float
-// arithmetic on the FP32 pipe: x is split once into (hi, lo) float pairs, each
-// stored value is split by integer operations as it streams in, and the row
-// sum is a renormalised double-float accumulation, rounded once to double.
+// HBM stream of the values needs, so two thirds of the products (delta_0 >=
+// (2p+1)/3) are formed in double-float arithmetic on the FP32 pipe -- x split
+// once into (hi, lo) float pairs, each stored value split by integer operations
+// as it streams in, a renormalised double-float row sum -- and the other third
+// with FP64 FMAs, so that neither pipe limits the stream; the two partial sums
+// are added once per row.
 #include "arith.cuh"
 #include "iga_internal.cuh"
 
@@ -68,9 +70,11 @@ __device__ __forceinline__ void spmv_add2(float& ah, float& al, float bh, float 
 
 template <int P, int DIM>
 __global__ void __launch_bounds__(kBlock) k_spmv_df(int m0, int m1, int m2, const double* __restrict__ vals,
-                                                    const float2* __restrict__ xs, double* __restrict__ y)
+                                                    const double* __restrict__ x, const float2* __restrict__ xs,
+                                                    double* __restrict__ y)
 {
     constexpr int W = 2 * P + 1;
+    constexpr int F64 = W / 3;                  // slots delta_0 + p < F64 use FP64 FMAs
     const int64_t N = (int64_t)m0 * m1 * m2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -79,6 +83,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_df(int m0, int m1, int m2, cons
                        (DIM == 2 || (i2 >= P && i2 < m2 - P));
     const int64_t s1 = m0, s2 = (int64_t)m0 * m1;
     float ah = 0.f, al = 0.f;
+    double a64 = 0.0;
     const int n2 = (DIM == 3) ? W : 1;
     for (int d2 = 0; d2 < n2; ++d2) {
         const int o2 = (DIM == 3) ? d2 - P : 0;
@@ -93,7 +98,9 @@ __global__ void __launch_bounds__(kBlock) k_spmv_df(int m0, int m1, int m2, cons
 #pragma unroll
             for (int d0 = 0; d0 < W; ++d0) {
                 const int o0 = d0 - P;
-                if (inner || (i0 + o0 >= 0 && i0 + o0 < m0)) {
+                if (d0 < F64) {
+                    if (inner || (i0 + o0 >= 0 && i0 + o0 < m0)) a64 = fma(v[(int64_t)d0 * N], __ldg(x + jbase + o0), a64);
+                } else if (inner || (i0 + o0 >= 0 && i0 + o0 < m0)) {
                     const float2 a = d2df_split(v[(int64_t)d0 * N]);
                     const float2 b = xs[jbase + o0];
                     // a * b: exact product of the high parts, cross terms into the low part
@@ -106,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_df(int m0, int m1, int m2, cons
             }
         }
     }
-    y[i] = df2d_exact(ah, al);
+    y[i] = df2d_exact(ah, al) + a64;
 }
 
 template <int P>
@@ -134,8 +141,8 @@ static cudaError_t spmv_df_p(int dim, const int m[3], const double* vals, const 
     cudaError_t e = pool_alloc((size_t)N * sizeof(float2), s, (void**)&xs);
     if (e != cudaSuccess) return e;
     k_split_x<<<grid, kBlock, 0, s>>>(N, x, xs);
-    if (dim == 3) k_spmv_df<P, 3><<<grid, kBlock, 0, s>>>(m[0], m[1], m[2], vals, xs, y);
-    else k_spmv_df<P, 2><<<grid, kBlock, 0, s>>>(m[0], m[1], 1, vals, xs, y);
+    if (dim == 3) k_spmv_df<P, 3><<<grid, kBlock, 0, s>>>(m[0], m[1], m[2], vals, x, xs, y);
+    else k_spmv_df<P, 2><<<grid, kBlock, 0, s>>>(m[0], m[1], 1, vals, x, xs, y);
     e = cudaGetLastError();
     cudaError_t fe = cudaFreeAsync(xs, s);
     return e != cudaSuccess ? e : fe;

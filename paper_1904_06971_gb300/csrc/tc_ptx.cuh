@@ -115,5 +115,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float v[16])
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// Asynchronous 4-byte copy global -> shared (zero-filled when valid is false;
+// src must still be a mapped address), grouped by commit / wait.
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 :: "r"(smem_addr(dst_smem)), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
 }  // namespace tc
 }  // namespace iga
