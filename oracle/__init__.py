@@ -22,4 +22,4 @@ from .surrogate import (  # noqa: F401
     gauss_legendre, open_uniform_knots, bspline_all, coefficient, geometry_map,
 )
 from .linalg import apply, interior_dofs, cg, relative_entry_error  # noqa: F401
-from . import per_offset, adjoint, mass  # noqa: F401
+from . import per_offset, adjoint, mass, manufactured  # noqa: F401

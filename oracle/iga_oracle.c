@@ -619,3 +619,116 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Manufactured solution u(x) = prod_d sin(pi x_d) (the paper's        */
+/* "low-frequency" Poisson solution, Sec. 7.3): the load vector        */
+/*   F_i = a(u, B_i) = int_Omega kappa grad u . grad B_i dx            */
+/* and the energy a(u, u), pulled back to the parameter domain with    */
+/* the same (p+1)-point Gauss rule as the stiffness matrix:            */
+/*   grad B_i = J^{-T} grad_xi B_i,  dx = |det J| dxi  (eq. ChangeOfVars). */
+/* ------------------------------------------------------------------ */
+static void mms_point(const orc_problem* P, const double* xi, double* gradu_pull, double* dens)
+{
+    int n = P->dim;
+    double x[3] = {0, 0, 0}, J[9];
+    orc_map(P, xi, x, J);
+    double gu[3] = {0, 0, 0};
+    for (int a = 0; a < n; ++a) {
+        double v = ORC_PI * cos(ORC_PI * x[a]);
+        for (int b = 0; b < n; ++b) if (b != a) v *= sin(ORC_PI * x[b]);
+        gu[a] = v;
+    }
+    /* inverse of J by cofactors: Jinv[b][a] = cof[a][b] / det */
+    double det, Jinv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (n == 2) {
+        det = J[0] * J[4] - J[1] * J[3];
+        Jinv[0] = J[4] / det; Jinv[1] = -J[1] / det; Jinv[3] = -J[3] / det; Jinv[4] = J[0] / det;
+    } else {
+        det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+              J[2] * (J[3] * J[7] - J[4] * J[6]);
+        Jinv[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+        Jinv[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+        Jinv[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+        Jinv[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+        Jinv[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+        Jinv[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+        Jinv[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+        Jinv[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+        Jinv[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    }
+    double f = orc_kappa(P, x) * fabs(det);
+    /* grad u . (J^{-T} grad_xi B) = (J^{-1} grad u) . grad_xi B */
+    double g2 = 0.0;
+    for (int b = 0; b < n; ++b) {
+        double s = 0.0;
+        for (int a = 0; a < n; ++a) s += Jinv[b * 3 + a] * gu[a];
+        gradu_pull[b] = f * s;
+        g2 += gu[b] * gu[b];
+    }
+    *dens = f * g2;
+}
+
+int orc_manufactured_load(const orc_problem* P, double* F /* N */, double* energy)
+{
+    if (!problem_ok(P)) return -1;
+    tab1d T[3];
+    memset(T, 0, sizeof(T));
+    if (build_tables(P, T)) return -2;
+    int n = P->dim, p = P->p;
+    int64_t N = orc_num_dofs(P);
+    int m[3] = {1, 1, 1};
+    for (int d = 0; d < n; ++d) m[d] = P->n_el[d] + p;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t row = 0; row < N; ++row) {
+        int ii[3] = {0, 0, 0};
+        int64_t rem = row;
+        for (int d = 0; d < n; ++d) { ii[d] = (int)(rem % m[d]); rem /= m[d]; }
+        int elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+        for (int d = 0; d < n; ++d) {
+            elo[d] = ii[d] - p < 0 ? 0 : ii[d] - p;
+            ehi[d] = ii[d] > P->n_el[d] - 1 ? P->n_el[d] - 1 : ii[d];
+        }
+        double acc = 0.0;
+        int e[3] = {0, 0, 0}, r[3] = {0, 0, 0};
+        for (e[2] = (n == 3 ? elo[2] : 0); e[2] <= (n == 3 ? ehi[2] : 0); ++e[2])
+        for (e[1] = elo[1]; e[1] <= ehi[1]; ++e[1])
+        for (e[0] = elo[0]; e[0] <= ehi[0]; ++e[0])
+        for (r[2] = 0; r[2] <= (n == 3 ? p : 0); ++r[2])
+        for (r[1] = 0; r[1] <= p; ++r[1])
+        for (r[0] = 0; r[0] <= p; ++r[0]) {
+            int g[3] = {0, 0, 0};
+            double xi[3] = {0, 0, 0}, wgt = 1.0;
+            for (int d = 0; d < n; ++d) {
+                g[d] = e[d] * (p + 1) + r[d];
+                xi[d] = T[d].xi[g[d]];
+                wgt *= T[d].wq[g[d]];
+            }
+            double gp[3], dens;
+            mms_point(P, xi, gp, &dens);
+            for (int k = 0; k < n; ++k) {
+                double v = 1.0;
+                for (int d = 0; d < n; ++d) v *= tab_get(&T[d], g[d], ii[d], d == k);
+                acc += wgt * gp[k] * v;
+            }
+        }
+        F[row] = acc;
+    }
+    /* energy: every Gauss point of the patch once */
+    double en = 0.0;
+    int G[3] = {1, 1, 1};
+    for (int d = 0; d < n; ++d) G[d] = T[d].G;
+    for (int g2 = 0; g2 < G[2]; ++g2)
+    for (int g1 = 0; g1 < G[1]; ++g1)
+    for (int g0 = 0; g0 < G[0]; ++g0) {
+        int gg[3] = {g0, g1, g2};
+        double xi[3] = {0, 0, 0}, wgt = 1.0;
+        for (int d = 0; d < n; ++d) { xi[d] = T[d].xi[gg[d]]; wgt *= T[d].wq[gg[d]]; }
+        double gp[3], dens;
+        mms_point(P, xi, gp, &dens);
+        en += wgt * dens;
+    }
+    *energy = en;
+    for (int d = 0; d < P->dim; ++d) tab_free(&T[d]);
+    return 0;
+}
