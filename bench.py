@@ -629,6 +629,49 @@ def fp32_tier_report(iga, torch, wl, A64, E64, exact_solution, args, steps: int 
     return out
 
 
+def equal_accuracy_report(iga, torch, wl, E, ms_exact, args, Ms=(2, 4, 6, 8, 12, 16), steps: int = 5,
+                          warmup: int = 3):
+    """Surrogate vs exact at equal accuracy of the discrete solution (Sec. 7.3): for the manufactured
+    solution u = prod sin(pi x_d) (iga_manufactured_load) the discretisation error ||u - u_h||_a of the
+    exact matrix (Galerkin orthogonality: a(u,u) - F.u_h) and, per sampling length M, the consistency
+    error ||u_h - u~_h||_A of the surrogate, both relative to ||u||_a; the paper's rule of thumb keeps
+    the consistency error at or below 5 % of the discretisation error.  Reports the surrogate step time
+    per M and the speed-up over the exact step at the largest M that satisfies the rule."""
+    prob = wl.problem
+    stream = torch.cuda.current_stream()
+    F, en = iga.manufactured_load(prob)
+    energy = en.item()
+    u_h, it_h, res_h = E.cg(F, tol=args.cg_tol, maxit=args.cg_maxit)
+    disc = float(np.sqrt(max(energy - torch.dot(F, u_h).item(), 0.0) / energy))
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    tdt = torch.float64 if wl.dtype == "f64" else torch.float32
+    x = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dtype=tdt, device="cuda")
+    y = torch.empty_like(x)
+    rows = []
+    for M in Ms:
+        A = iga.assemble_surrogate(prob, M, wl.q, dtype=wl.dtype)
+
+        def step():
+            iga.assemble_surrogate(prob, M, wl.q, dtype=wl.dtype, out=A)
+            A.apply(x, y)
+
+        ms, _ = _time_steps(torch, step, steps, warmup, stream)
+        u_s, it_s, res_s = A.cg(F, tol=args.cg_tol, maxit=args.cg_maxit)
+        d = (u_s - u_h).to(tdt)
+        cons = float(np.sqrt(max(torch.dot(d.double(), E.apply(d).double()).item(), 0.0) / energy))
+        rows.append({"M": M, "q": wl.q, "ms_per_step": ms, "value": prob.nnz / (ms * 1e-3),
+                     "consistency_rel_energy": cons, "consistency_over_discretisation": cons / disc,
+                     "speedup_vs_exact": ms_exact / ms, "cg_iters": it_s})
+        A.destroy()
+    ok = [r for r in rows if r["consistency_over_discretisation"] <= 0.05]
+    best = max(ok, key=lambda r: r["M"]) if ok else None
+    return {"workload": wl.name, "solution": "u = prod_d sin(pi x_d) (Sec. 7.3), homogeneous Dirichlet",
+            "norm": "energy a(.,.), relative to ||u||_a", "discretisation_rel_energy": disc,
+            "exact_cg_iters": it_h, "exact_ms_per_step": ms_exact, "rule": "consistency <= 5% of discretisation",
+            "per_M": rows, "largest_M_within_rule": best["M"] if best else None,
+            "speedup_at_equal_accuracy": best["speedup_vs_exact"] if best else None}
+
+
 def side_report(iga, torch, wl, steps: int, warmup: int):
     """Surrogate (+ SpMV) and exact steps of another workload, with the surrogate's entry error."""
     prob = wl.problem
@@ -669,6 +712,8 @@ def run_gpu(args, wl):
     dist = init_dist(world, "nccl")
     import paper_1904_06971_gb300 as iga
     iga.load()
+    if args.arith:
+        iga.set_arithmetic("f64", args.arith)
     prob = wl.problem
     stream = torch.cuda.current_stream()
     primary = args.domains
@@ -805,6 +850,8 @@ def run_gpu(args, wl):
         extra["fp32_tier"] = fp32_tier_report(iga, torch, wl, A, E, exact_solution, args)
     if not args.no_extra:
         extra["p3_64cube"] = side_report(iga, torch, W.CFG_3D_P3, steps=8, warmup=3)
+    if not args.no_solve and not args.no_extra:
+        extra["equal_accuracy"] = equal_accuracy_report(iga, torch, wl, E, ms_e_max, args)
 
     if rank != 0:
         return 0
@@ -907,6 +954,8 @@ def main(argv=None):
                     help="skip the FP32-tier and 64^3 p = 3 reports beside the headline")
     ap.add_argument("--cg-tol", type=float, default=1e-10)
     ap.add_argument("--cg-maxit", type=int, default=20000)
+    ap.add_argument("--arith", default=None, choices=["df64", "df64_tc", "fp64"],
+                    help="contraction arithmetic of FP64 values (default: the library's)")
     ap.add_argument("--domains", choices=["common", "per_offset"], default="common",
                     help="interpolation domains of the headline surrogate (the other is reported beside it)")
     ap.add_argument("--mode", choices=["both", "surrogate", "exact"], default="both",

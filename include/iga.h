@@ -92,11 +92,19 @@ extern "C" {
  *     on the tensor cores: each FP32 operand split into three BF16 parts, the six
  *     partial products of order <= 2 accumulated in FP32 (FP32-level accuracy,
  *     Sec. 6 sum factorisation).  Only for IGA_F32 values, degrees 2..5.
+ *   IGA_ARITH_DF64_TC: IGA_ARITH_DF64, except that stage X of those rows runs
+ *     on the tensor cores with FP64 accuracy: every operand is scaled per T2
+ *     line and per offset column by a power of two and written as six signed
+ *     base-256 digits in BF16; the digit products of each level are summed
+ *     exactly in FP32 tensor memory (levels 0, 1, 2 apart, 3..5 together,
+ *     higher levels dropped, below 2^-48), then added in double-float and
+ *     rounded once.  Only for IGA_F64 values, degrees 2..5.
  */
 #define IGA_ARITH_FP64 0
 #define IGA_ARITH_DF64 1
 #define IGA_ARITH_FP32 2
 #define IGA_ARITH_BF16X3 3
+#define IGA_ARITH_DF64_TC 4
 
 typedef struct {
     int32_t dim;        /* n: 2 or 3 */
@@ -350,6 +358,25 @@ int iga_profile_enable(int on);
 int iga_profile_read(int n, int64_t* launches, double* ms);
 int iga_num_kernels(void);
 const char* iga_kernel_name(int k);
+
+/*
+ * Load vector and energy of the manufactured solution u(x) = prod_d sin(pi x_d)
+ * (the paper's low-frequency Poisson solution, Sec. 7.3), for the split of a
+ * surrogate solution's error into discretisation and consistency parts (the
+ * two terms of the a-priori bounds, eq. APrioriBoundH1; rule of thumb: keep the
+ * consistency error at or below 5 % of the discretisation error):
+ *   F[i]    = a(u, B_i) = int kappa grad u . grad B_i dx   (i = 0..N-1, colexicographic),
+ *   *energy = a(u, u)   = int kappa |grad u|^2 dx,
+ * both with the assembly's (p+1)-point Gauss rule, pulled back through the map
+ * (eq. ChangeOfVars), in FP64.  u vanishes on the boundary of the unit square /
+ * cube, so for maps of it onto itself (identity, sine-product) u solves the
+ * homogeneous Dirichlet problem whose Galerkin load is F, and for the solution
+ * u_h of A_II u_h = F_I: ||u - u_h||_a^2 = a(u, u) - F . u_h.
+ *   F, energy: caller-owned DEVICE buffers of N and 1 doubles; the call is
+ *   enqueued on the stream and allocates its scratch from the library's pool.
+ */
+int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+                          double* F, double* energy, void* stream);
 
 /*
  * Exact assembly that allocates no memory (the paper has no counterpart; this

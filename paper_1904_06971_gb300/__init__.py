@@ -23,13 +23,13 @@ import numpy as np
 from . import _build
 
 __all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "assemble_mass", "assemble_mass_surrogate",
-           "surrogate_plan",
+           "surrogate_plan", "manufactured_load",
            "kappa_gradient", "stiffness_apply", "assemble_batch", "batch_info", "load", "launch_count",
            "profile_enable", "profile_read", "kernel_names", "set_arithmetic", "get_arithmetic",
            "F64", "F32", "ARITH"]
 
 F64, F32 = 0, 1
-ARITH = {"fp64": 0, "df64": 1, "fp32": 2, "bf16x3": 3}
+ARITH = {"fp64": 0, "df64": 1, "fp32": 2, "bf16x3": 3, "df64_tc": 4}
 _MAP = {"identity": 0, "affine": 1, "sinprod": 2}
 _KAPPA = {"const": 0, "sin2d": 1, "expsin3d": 2, "poly": 3, "bspline3": 4}
 _lock = threading.Lock()
@@ -96,6 +96,8 @@ def load():
                                      ctypes.POINTER(ctypes.c_float)]
         L.iga_assemble_exact_noalloc.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                                  ctypes.POINTER(Kappa), ctypes.c_int, vp, vp]
+        L.iga_manufactured_load.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
+                                            ctypes.POINTER(Kappa), vp, vp, vp]
         L.iga_apply.argtypes = [H, vp, vp, vp]
         L.iga_cg.argtypes = [H, vp, vp, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_double)]
@@ -374,6 +376,20 @@ def profile_read():
     ms = (ctypes.c_double * n)()
     _check(L.iga_profile_read(n, la, ms))
     return {L.iga_kernel_name(k).decode(): (int(la[k]), float(ms[k])) for k in range(n)}
+
+
+def manufactured_load(prob, stream=None, kappa_ctrl=None):
+    """(F, energy) of the manufactured solution u = prod_d sin(pi x_d) (iga_manufactured_load):
+    F_i = a(u, B_i) as a float64 CUDA tensor of N entries and a(u, u) as a float64 CUDA scalar tensor."""
+    import torch
+    pt, mp, kp = _structs(prob, kappa_ctrl)
+    N = int(np.prod([int(prob.n_el[d]) + int(prob.p) for d in range(prob.dim)]))
+    F = torch.empty(N, dtype=torch.float64, device="cuda")
+    en = torch.empty((), dtype=torch.float64, device="cuda")
+    _check(load().iga_manufactured_load(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
+                                        ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(en.data_ptr()),
+                                        ctypes.c_void_p(_stream_ptr(stream))))
+    return F, en
 
 
 def kappa_gradient(prob, ybar, x, M: int = 0, q: int = 3, kappa_ctrl=None, stream=None):

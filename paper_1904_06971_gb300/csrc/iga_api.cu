@@ -47,6 +47,7 @@ int cuda_fail(cudaError_t e, const char* what)
 // ---- contraction arithmetic per value dtype (process-wide) ----
 std::atomic<int> g_arith[2] = {{kArithDF}, {kArithF32}};
 std::atomic<int> g_tc_f32{0};          // FP32 values: stage X of the cardinal rows on the tensor cores
+std::atomic<int> g_tc_f64{0};          // FP64 values: the same with exact BF16 digit products
 
 // ---- launch counting and optional per-kernel event timing ----
 std::atomic<int64_t> g_launches{0};
@@ -60,7 +61,8 @@ thread_local bool t_capture = false;        // inside a graph capture: no profil
 
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
                              "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg",
-                             "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter", "stage_x_tc"};
+                             "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter", "stage_x_tc",
+                             "manufactured"};
 
 cudaEvent_t take_event()
 {
@@ -414,9 +416,20 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     prepare_coef_df(g, arith);
     int64_t nblk[4] = {0, 0, 0, 0};
     bs.nb = (int)boxes.size();
+    // FP64 values with tensor-core stage X: per-line T2 exponents of every box and the group shifts
+    const int tc64 = (form == kFormStiffness && dtype == IGA_F64) ? current_tc(dtype) : 0;
+    int64_t o_gshift = -1, o_ex_lo = -1, o_ex_hi = -1;
+    if (tc64) o_gshift = lay.take(2);
     for (int k = 0; k < bs.nb; ++k) {
         Box& b = boxes[k];
         b.out_kind = 0;
+        b.ex_off = -1;
+        if (tc64) {
+            const int64_t lines = (dim == 3 ? (int64_t)b.R[2] * W : 1) * (int64_t)b.R[1] * W;
+            b.ex_off = lay.take((lines + 1) / 2);
+            if (o_ex_lo < 0) o_ex_lo = b.ex_off;
+            o_ex_hi = lay.total;
+        }
         b.c_off = lay.take(box_coef_len(dim, p, b));
         b.t1_off = lay.take(box_t1_len(dim, p, b));
         b.t2_off = lay.take(box_t2_len(dim, p, b));
@@ -495,10 +508,18 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
     }
     T.arith = arith;
-    T.tc = current_tc(dtype);
+    T.tc = (dtype == IGA_F32) ? current_tc(dtype) : 0;
+    T.tc64 = tc64;
+    T.gshift = tc64 ? reinterpret_cast<const int*>(P(o_gshift)) : nullptr;
     const char* stage = "basis tables";
     ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
     if (ce == cudaSuccess) { stage = "pair tables"; ce = launch_pairs(g, bv, bd, wq, X, Xs, arith, st); }
+    if (ce == cudaSuccess && tc64) {
+        stage = "tensor-core stage X set-up";
+        ce = launch_tc_group_shift(g, T, reinterpret_cast<int*>(P(o_gshift)), st);
+        if (ce == cudaSuccess && o_ex_lo >= 0)
+            ce = cudaMemsetAsync(P(o_ex_lo), 0, (size_t)(o_ex_hi - o_ex_lo) * sizeof(double), st);
+    }
     if (ce == cudaSuccess) { stage = "coefficient field"; ce = launch_coef(g, T, bs, nblk[0], scratch, st); }
     double* samples = do_spline ? P(o_samples) : nullptr;
     if (ce == cudaSuccess) {
@@ -573,7 +594,8 @@ int current_arith(int dtype)
 
 int current_tc(int dtype)
 {
-    return (dtype == IGA_F32 && g_arith[1].load() == kArithF32) ? g_tc_f32.load() : 0;
+    if (dtype == IGA_F32) return g_arith[1].load() == kArithF32 ? g_tc_f32.load() : 0;
+    return g_arith[0].load() == kArithDF ? g_tc_f64.load() : 0;
 }
 
 int report_error(int code, const char* msg)
@@ -815,6 +837,54 @@ int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, co
     return IGA_OK;
 }
 
+int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+                          double* F, double* energy, void* stream_v)
+{
+    t_err.clear();
+    Geo g;
+    int rc = check_geometry(patch, p, map, kappa, g);
+    if (rc) return rc;
+    if (!F || !energy) return fail(IGA_EINVAL, "F and energy must be non-null device pointers");
+    const int dim = g.dim, Q = p + 1;
+    int64_t npts = 1;
+    for (int d = 0; d < dim; ++d) npts *= (int64_t)g.n_el[d] * Q;
+    const int64_t npart = npts / (8 * kBlock) + 2;
+    cudaStream_t st = (cudaStream_t)stream_v;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    Layout lay;
+    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_tdf[3];
+    for (int d = 0; d < 3; ++d) {
+        const int64_t G = (d < dim) ? (int64_t)g.n_el[d] * Q : 1;
+        o_gx[d] = lay.take(G); o_sx[d] = lay.take(2 * G); o_cx[d] = lay.take(2 * G); o_wq[d] = lay.take(G);
+        o_bv[d] = lay.take(G * Q); o_bd[d] = lay.take(G * Q); o_tdf[d] = lay.take(4 * G);
+    }
+    const int64_t o_V = lay.take(dim * npts), o_E = lay.take(npts), o_part = lay.take(2 * npart);
+    cudaMemPool_t pool;
+    if ((ce = device_pool(dev, &pool)) != cudaSuccess) return cuda_fail(ce, "creating the memory pool");
+    double* scratch = nullptr;
+    ce = cudaMallocFromPoolAsync((void**)&scratch, (size_t)lay.total * sizeof(double), pool, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "allocating scratch");
+    double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3];
+    float2* tdf[3];
+    MmsArgs A;
+    for (int d = 0; d < 3; ++d) {
+        gx[d] = scratch + o_gx[d]; sx[d] = scratch + o_sx[d]; cx[d] = scratch + o_cx[d]; wq[d] = scratch + o_wq[d];
+        bv[d] = scratch + o_bv[d]; bd[d] = scratch + o_bd[d]; tdf[d] = reinterpret_cast<float2*>(scratch + o_tdf[d]);
+        A.gx[d] = gx[d]; A.wq[d] = wq[d]; A.bv[d] = bv[d]; A.bd[d] = bd[d];
+    }
+    A.V = scratch + o_V;
+    A.E = scratch + o_E;
+    const char* stage = "basis tables";
+    ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
+    if (ce == cudaSuccess) { stage = "manufactured load"; ce = launch_manufactured(g, A, F, energy, scratch + o_part, npart, st); }
+    cudaError_t fe = cudaFreeAsync(scratch, st);
+    if (ce == cudaSuccess) ce = fe;
+    if (ce != cudaSuccess) return cuda_fail(ce, stage);
+    return IGA_OK;
+}
+
 int iga_assemble_surrogate_domains(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
                                    int M, int q, int domains, int dtype, void* stream, iga_matrix_t* A)
 {
@@ -908,19 +978,25 @@ int iga_set_arithmetic(int dtype, int arith)
     case IGA_ARITH_DF64: a = kArithDF; break;
     case IGA_ARITH_FP32: a = kArithF32; break;
     case IGA_ARITH_BF16X3: a = kArithF32; tc = 1; break;
+    case IGA_ARITH_DF64_TC: a = kArithDF; tc = 1; break;
     default: return fail(IGA_EINVAL, "unknown arithmetic %d", arith);
     }
+    if (arith == IGA_ARITH_BF16X3 && dtype != IGA_F32)
+        return fail(IGA_EINVAL, "IGA_ARITH_BF16X3 is for IGA_F32 values (use IGA_ARITH_DF64_TC for IGA_F64)");
+    if (arith == IGA_ARITH_DF64_TC && dtype != IGA_F64)
+        return fail(IGA_EINVAL, "IGA_ARITH_DF64_TC is for IGA_F64 values (use IGA_ARITH_BF16X3 for IGA_F32)");
     if (dtype == IGA_F64 && a == kArithF32)
         return fail(IGA_EINVAL, "FP32 contractions cannot meet FP64 accuracy; use IGA_ARITH_FP64 or IGA_ARITH_DF64");
     g_arith[dtype == IGA_F32 ? 1 : 0].store(a);
     if (dtype == IGA_F32) g_tc_f32.store(tc);
+    else g_tc_f64.store(tc);
     return IGA_OK;
 }
 
 int iga_get_arithmetic(int dtype)
 {
     const int a = current_arith(dtype);
-    if (current_tc(dtype)) return IGA_ARITH_BF16X3;
+    if (current_tc(dtype)) return dtype == IGA_F32 ? IGA_ARITH_BF16X3 : IGA_ARITH_DF64_TC;
     return a == kArithF64 ? IGA_ARITH_FP64 : a == kArithDF ? IGA_ARITH_DF64 : IGA_ARITH_FP32;
 }
 

@@ -12,6 +12,7 @@ constexpr int kMaxP = 5;          // degrees 1..5 are instantiated
 constexpr int kMaxQ = 7;          // interpolation degree 0..7
 constexpr int kBlock = 256;       // threads per block of the item-parallel kernels
 constexpr int kLinesX = 2;        // output lines per thread in quadrature stage X
+constexpr int kTcExpOffset = 1000;    // per-line T2 exponents are stored as biased exponent + shift + this (0: all zero)
 
 // Geometry map + diffusion coefficient + mesh; passed by value to kernels.
 struct Geo {
@@ -44,6 +45,7 @@ struct Box {
     int64_t c_off;            // offset (doubles) of the box's coefficient fields in scratch
     int64_t t1_off, t2_off;   // offsets (doubles) of the stage intermediates
     int64_t blk[4];           // first block of this box in the K2 / Z / Y / X launches
+    int64_t ex_off;           // offset (doubles) of the per-line exponents of T2 (tensor-core FP64 stage X), or -1
 };
 
 constexpr int kMaxBoxes = 7;
@@ -100,6 +102,7 @@ __device__ __forceinline__ void get_box(const BoxSet& bs, int dim, int p, int st
             b.E[d] = (d < dim) ? p + 1 : 1;
         }
         b.out_kind = 1;
+        b.ex_off = -1;
         b.sample_id = sid;
         b.c_off = bs.s_c_off + sid * bs.s_c_len;
         b.t1_off = bs.s_t1_off + sid * bs.s_t1_len;
@@ -122,12 +125,14 @@ struct Tables {
     const float2* tdf[3];     // [G][4] double-float sin(pi xi), pi cos(pi xi), sin(2 pi xi), cos(2 pi xi)
     int arith;                // contraction arithmetic (arith.cuh: kArithF64 / kArithDF / kArithF32)
     int tc;                   // FP32 arithmetic: stage X of the cardinal rows on the tensor cores (k_quad_tc.cu)
+    int tc64;                 // double-float arithmetic: the same with exact BF16 digit products (k_quad_tc.cu)
+    const int* gshift;        // tc64: [4] exponent shifts sigma_g balancing the T2 groups (k_quad_tc.cu)
 };
 
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
     K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE,
-    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_NUM
+    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_MMS, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
@@ -173,10 +178,16 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
                         double* scratch, cudaStream_t s);
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
                           double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
-// Stage X of the cardinal rows of the explicit boxes on the tensor cores (BF16
-// parts, FP32 accumulation; FP32 values, p = 2..5); *used = false when it did not run.
-cudaError_t launch_stage_x_tc(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, float* ell,
-                              int64_t N, cudaStream_t s, bool* used);
+// Stage X of the cardinal rows of the explicit boxes on the tensor cores: FP32
+// values (BF16 parts, FP32 accumulation) or, with T.tc64, FP64 values (six
+// BF16 digits, products accumulated exactly per level); p = 2..5; *used =
+// false when it did not run.
+// The group shifts sigma_g of the FP64 variant (written to gshift, 4 ints) are
+// computed from the cardinal pair weights of direction 0 before stage Y, which
+// records each T2 line's largest exponent for it.
+cudaError_t launch_tc_group_shift(const Geo& g, const Tables& T, int* gshift, cudaStream_t s);
+cudaError_t launch_stage_x_tc(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, void* ell,
+                              int f64, int64_t N, cudaStream_t s, bool* used);
 // The same three stages for the mass form: one scalar field (|det Dphi| at the
 // Gauss points) and the value-value pair weights only (k_mass.cu).
 cudaError_t launch_mass_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
@@ -233,6 +244,19 @@ cudaError_t launch_spmv(int dim, int p, const int m[3], const void* values, int 
                         const void* x, void* y, cudaStream_t s);
 // K4 part 1 alone: knots, collocation LU and evaluation tables of every variant.
 cudaError_t launch_spline_setup(const SplinePlan& sp, const SplineBufs& sb, cudaStream_t s);
+
+// ---- manufactured solution u = prod sin(pi x_d): load a(u, B_i) and energy a(u, u) (k_tables.cu) ----
+struct MmsArgs {
+    const double* gx[3];      // [G] Gauss point coordinates
+    const double* wq[3];      // [G] weights (times h)
+    const double* bv[3];      // [G][p+1] values of the active basis functions
+    const double* bd[3];      // [G][p+1] their derivatives
+    double* V;                // [dim][points] w kappa |det J| J^{-1} grad u
+    double* E;                // [points] w kappa |det J| |grad u|^2
+};
+// partial: scratch of 2 * npart doubles, npart >= points / (8 * kBlock) + 1
+cudaError_t launch_manufactured(const Geo& g, const MmsArgs& A, double* F, double* energy, double* partial,
+                                int64_t npart, cudaStream_t s);
 
 // ---- adjoint with respect to B-spline control values of kappa (k_adjoint.cu) ----
 struct AdjTables {

@@ -111,6 +111,7 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
     }
     prepare_coef_df(g, arith);
     b.out_kind = 0;
+    b.ex_off = -1;
     b.c_off = off; off += up32(box_coef_len(g.dim, p, b));
     b.t1_off = off; off += up32(box_t1_len(g.dim, p, b));
     b.t2_off = off; off += up32(box_t2_len(g.dim, p, b));
@@ -149,7 +150,9 @@ extern "C" int iga_assemble_exact_noalloc(const iga_patch_t* patch, int p, const
         T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
     }
     T.arith = arith;
-    T.tc = current_tc(dtype);
+    T.tc = (dtype == IGA_F32) ? current_tc(dtype) : 0;
+    T.tc64 = 0;                       // the FP64 tensor-core stage needs per-line exponent scratch
+    T.gshift = nullptr;
     e = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
     if (e == cudaSuccess) e = launch_pairs(g, bv, bd, wq, X, Xs, arith, st);
     if (e == cudaSuccess) e = launch_coef(g, T, bs, nblk[0], scratch, st);

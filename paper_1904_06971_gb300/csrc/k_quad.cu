@@ -291,6 +291,30 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
             T2[(((int64_t)k * P3 + pair3) * P2 + (int64_t)i2l * W + dd) * G0 + g0] = Pol::to_store(acc[dd][k]);
+    if constexpr (Pol::kind == kArithDF) {
+        if (T.tc64 && b.out_kind == 0 && b.ex_off >= 0) {
+            // largest exponent of each T2 line (pair3, i2l W + dd), the groups shifted by sigma_g, for the
+            // exact-digit tensor-core stage X: max over this warp's lanes of the same line, one atomic each
+            int* ex = reinterpret_cast<int*>(scratch + b.ex_off);
+            const unsigned key = (unsigned)(item / G0);
+            const unsigned peers = __match_any_sync(__activemask(), key);
+            const bool leader = (__ffs(peers) - 1) == (int)(threadIdx.x & 31);
+            int sh[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sh[k] = T.gshift[k];
+#pragma unroll
+            for (int dd = 0; dd < W; ++dd) {
+                int m = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = (int)((__float_as_uint(Pol::to_store(acc[dd][k]).x) >> 23) & 0xffu);
+                    if (e > 0) m = max(m, e + sh[k] + kTcExpOffset);
+                }
+                m = (int)__reduce_max_sync(peers, (unsigned)m);
+                if (leader && m > 0) atomicMax(ex + pair3 * P2 + (int64_t)i2l * W + dd, m);
+            }
+        }
+    }
 }
 
 template <class Pol, int P, int DIM>
@@ -436,10 +460,11 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
         }
         if (nb[3] > 0) {
             int skip = 0;
-            if constexpr (Pol::kind == kArithF32) {
-                if (T.tc && ell_f32 && P >= 2) {
+            if constexpr (Pol::kind == kArithF32 || Pol::kind == kArithDF) {
+                const bool want = (Pol::kind == kArithF32) ? (T.tc && ell_f32) : (T.tc64 && !ell_f32);
+                if (want && P >= 2) {
                     bool used = false;
-                    cudaError_t e = launch_stage_x_tc(g, T, bs, scratch, (float*)ell, N, s, &used);
+                    cudaError_t e = launch_stage_x_tc(g, T, bs, scratch, ell, Pol::kind == kArithDF, N, s, &used);
                     if (e != cudaSuccess) return e;
                     skip = used ? 1 : 0;
                 }
@@ -457,10 +482,11 @@ static cudaError_t stages_p(const Geo& g, const Tables& T, const BoxSet& bs, con
         }
         if (nb[3] > 0) {
             int skip = 0;
-            if constexpr (Pol::kind == kArithF32) {
-                if (T.tc && ell_f32 && P >= 2) {
+            if constexpr (Pol::kind == kArithF32 || Pol::kind == kArithDF) {
+                const bool want = (Pol::kind == kArithF32) ? (T.tc && ell_f32) : (T.tc64 && !ell_f32);
+                if (want && P >= 2) {
                     bool used = false;
-                    cudaError_t e = launch_stage_x_tc(g, T, bs, scratch, (float*)ell, N, s, &used);
+                    cudaError_t e = launch_stage_x_tc(g, T, bs, scratch, ell, Pol::kind == kArithDF, N, s, &used);
                     if (e != cudaSuccess) return e;
                     skip = used ? 1 : 0;
                 }

@@ -31,7 +31,7 @@ namespace iga {
 
 namespace {
 
-constexpr int kTcThreads = 256;         // 8 warps: all copy and split, thread 0 issues the MMAs
+constexpr int kTcThreads = 256;         // 8 warps: all copy and split, every lane 0 issues MMAs
 constexpr int kTcLines = 128;           // MMA M: lines per block
 constexpr int kTcN = 16;                // MMA N: offsets delta0 (2p + 1 <= 11 used)
 constexpr int kTcSlices = 3;            // BF16 parts per FP32 value
@@ -87,8 +87,8 @@ __device__ int g_tc_status = 0;
 // job's Gauss points of their lines asynchronously into a raw FP32 tile (the
 // copy of the next job is in flight while this one is processed), split them
 // into three BF16 parts in an MN-major tile (16 groups of 8 lines, one 16-byte
-// row per Gauss point), and thread 0 issues, for every row of the chunk, the
-// MMAs of its window against the cardinal weights of that pattern (K-major,
+// row per Gauss point), and lane 0 of warp w issues, for the rows w, w + 8, ...
+// of the chunk, the MMAs of their windows against the cardinal weights of that pattern (K-major,
 // 16 offset columns) into the chunk's tensor-memory block.  mbarriers tell
 // when a BF16 tile's MMAs are done; after the first job of chunk k has been
 // issued, the rows of chunk k - 1 are read out of the other tensor-memory
@@ -149,9 +149,10 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
         base[Sh::B_PART + off] = x2;
     }
     if (tid == 0) {
-        tc::bar_init(&bars[0], 1);
-        tc::bar_init(&bars[1], 1);
-        tc::bar_init(&bars[2], 1);
+        // every warp's lane 0 issues MMAs and commits to these barriers
+        tc::bar_init(&bars[0], kTcThreads / 32);
+        tc::bar_init(&bars[1], kTcThreads / 32);
+        tc::bar_init(&bars[2], kTcThreads / 32);
         tc::fence_bar_init();
     }
     if (warp == 0) tc::tmem_alloc(tmem_slot, Sh::TMEM_COLS);
@@ -235,23 +236,24 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
         }
         tc::fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        // MMAs: warp w's lane 0 issues those of the chunk rows c = w, w + 8, ... (every row's chain stays
+        // in one thread, so its accumulation order is fixed); descriptors advance by whole 16-byte rows
+        if (lane == 0) {
             tc::fence_after_sync();
-            const uint32_t a_base = sA_addr + (uint32_t)(buf * Sh::A_BUF);
-            const uint32_t b_base = sB_addr + (uint32_t)(gq * kTcSlices * Sh::B_PART);
+            const uint64_t a0 = tc::sdesc(sA_addr + (uint32_t)(buf * Sh::A_BUF), 128, ROWS * 16);
+            const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * kTcSlices * Sh::B_PART), 128, (KW / 8) * 128);
             const uint32_t d_base = tmem + (uint32_t)((k & 1) * Sh::TBLOCK);
-            for (int c = 0; c < nc; ++c) {
+            for (int c = warp; c < nc; c += kTcThreads / 32) {
 #pragma unroll
                 for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
-                    const uint32_t arow = (uint32_t)(c * Q + ks * 16) * 16;
+                    const uint64_t arow = (uint64_t)(c * Q + ks * 16);
                     // partial products a_i b_j of total order i + j <= 2
 #pragma unroll
                     for (int pr = 0; pr < 6; ++pr) {
                         const int pi = (pr == 2 || pr == 4) ? 1 : (pr == 5 ? 2 : 0);
                         const int pj = (pr == 1 || pr == 4) ? 1 : (pr == 3 ? 2 : 0);
-                        const uint64_t ad = tc::sdesc(a_base + (uint32_t)(pi * Sh::A_SLICE) + arow, 128, ROWS * 16);
-                        const uint64_t bd = tc::sdesc(b_base + (uint32_t)(pj * Sh::B_PART + ks * 256), 128,
-                                                      (KW / 8) * 128);
+                        const uint64_t ad = a0 + (uint64_t)(pi * Sh::A_SLICE / 16) + arow;
+                        const uint64_t bd = b0 + (uint64_t)((pj * Sh::B_PART + ks * 256) / 16);
                         tc::mma_bf16(d_base + (uint32_t)(c * kTcN), ad, bd, IDESC, (gq | ks | pr) ? 1u : 0u);
                     }
                 }
@@ -270,10 +272,8 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     if (!ok) {
         // give up: mark the status, let the copies and every issued MMA drain, NaN the rows not written
         tc::cp_async_wait<0>();
-        if (tid == 0) {
-            atomicOr(&g_tc_status, 1);
-            tc::commit(&bars[2]);
-        }
+        if (tid == 0) atomicOr(&g_tc_status, 1);
+        if (lane == 0) tc::commit(&bars[2]);
         tc::bar_wait(&bars[2], 0u, kTcWaitIter);
         if (half == 0 && my_line < total)
             for (int i0 = i0_lo + done_chunks * C; i0 <= i0_hi; ++i0)
@@ -284,12 +284,321 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     if (warp == 0) tc::tmem_dealloc(tmem, Sh::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 values: exact BF16 digit products (the FP64 accuracy of double-float
+// stage X, on the tensor cores).
+//
+// Every T2 value of a line (double-float) is scaled by a power of two to
+// |alpha| < 1 -- per line, from the largest exponent stage Y recorded, with the
+// four T2 groups balanced by powers of two sigma_g against the pair weights
+// they meet -- and written as six signed base-256 digits alpha = sum_i a_i,
+// a_i = (integer of magnitude <= 129) 2^-(7+8i), each exact in BF16.  The pair
+// weights (FP64) get the same six digits per offset column.  A product a_i b_j
+// is an integer times 2^-(14+8(i+j)), so the products of one level L = i + j
+// summed over the K = 4 (p+1)^2 Gauss points of a row stay below 2^24 quanta:
+// the FP32 accumulation of levels 0, 1 and 2 is exact, each in its own block of
+// tensor memory; levels 3..5 share a fourth block (their FP32 rounding is
+// below 2^-48 of the row).  Levels >= 6 are dropped (below 2^-48).  The four
+// blocks are added in double-float, scaled back and rounded once to double.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kDigits = 6;              // BF16 digits per value
+constexpr int kAcc = 4;                 // tensor-memory accumulators per row: levels 0, 1, 2, 3..5
+
+template <int P>
+struct Tc64Shape {
+    static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
+    static constexpr int KW = (TT + 15) / 16 * 16;
+    static constexpr int KSTEPS = KW / 16;
+    static constexpr int C = (P >= 5) ? 4 : 8;               // rows i0 per chunk (kAcc * 16 columns each)
+    static constexpr int ROWS = (C - 1) * Q + KW;
+    static constexpr int A_SLICE = 16 * ROWS * 16;
+    static constexpr int A_BUF = kDigits * A_SLICE;          // one BF16 tile (single-buffered)
+    static constexpr int RAW = kTcLines * ROWS * 8;          // one raw double-float tile
+    static constexpr int B_PART = kTcN * KW * 2;
+    static constexpr int B_BYTES = 4 * kDigits * B_PART;
+    static constexpr int SMALL = kTcLines * 4 * 4 + kTcLines * 4 + kTcN * 4 + 64;   // scales, exponents, barriers
+    static constexpr int SMEM = A_BUF + RAW + B_BYTES + SMALL;
+    static constexpr int TMEM_COLS = 512;
+    static_assert(C * kAcc * kTcN <= TMEM_COLS, "chunk does not fit in tensor memory");
+    static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
+};
+
+__device__ __forceinline__ float pow2f(int k)
+{
+    k = max(-126, min(127, k));
+    return __int_as_float((127 + k) << 23);
+}
+
+}  // namespace
+
+// Group shifts sigma_g = E(max |X_g|) - E(max |X_0|) of the cardinal pair
+// weights of direction 0 (pattern of T2 group g: 11, 10, 01, 00), E = binary
+// exponent; one block.
+__global__ void k_tc_group_shift(const double* Xcard, int W, int TT, int* gshift)
+{
+    __shared__ int mx[4];
+    if (threadIdx.x < 4) mx[threadIdx.x] = -100000;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 4 * W * TT; idx += blockDim.x) {
+        const int gq = idx / (W * TT), r = idx % (W * TT);
+        const double x = Xcard[(int64_t)r * 4 + (3 - gq)];
+        if (x != 0.0) atomicMax(&mx[gq], ilogb(x));
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) gshift[threadIdx.x] = (mx[threadIdx.x] > -100000 && mx[0] > -100000) ? mx[threadIdx.x] - mx[0] : 0;
+}
+
+cudaError_t launch_tc_group_shift(const Geo& g, const Tables& T, int* gshift, cudaStream_t s)
+{
+    const int W = 2 * g.p + 1, TT = (g.p + 1) * (g.p + 1);
+    if (g.m[0] < 4 * g.p + 1) return cudaMemsetAsync(gshift, 0, 4 * sizeof(int), s);
+    launch_begin(K_STAGE_X_TC, s);
+    k_tc_group_shift<<<1, 256, 0, s>>>(T.X[0] + (int64_t)(2 * g.p) * W * TT * 4, W, TT, gshift);
+    launch_end(K_STAGE_X_TC, s);
+    return cudaGetLastError();
+}
+
+// One block per 128 lines of box b, rows i0 in [i0_lo, i0_hi] (cardinal) in
+// chunks of C rows, four jobs (T2 groups) per chunk as in k_stage_x_tc, with
+// one raw and one digit tile: the copy of job j + 1 runs during the MMAs of
+// job j, the digits of job j + 1 wait for those MMAs.  Lane 0 of warp w issues
+// the MMAs of the chunk rows w, w + 8, ...: for every row, K step and digit
+// pair (i, j) with i + j <= 5, one M = 128, N = 16, K = 16 MMA into the
+// accumulator block of level min(i + j, 3).
 template <int P, int DIM>
-static cudaError_t stage_x_tc_boxes(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, float* ell,
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch, double* ell, int64_t N)
+{
+    using Sh = Tc64Shape<P>;
+    constexpr int Q = Sh::Q, W = Sh::W, TT = Sh::TT, KW = Sh::KW, C = Sh::C, ROWS = Sh::ROWS;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;                                         // [digit 6][line group 16][ROWS][16 B]
+    float2* sR = reinterpret_cast<float2*>(tc_smem + Sh::A_BUF);         // [line 128][ROWS]
+    unsigned char* sB = tc_smem + Sh::A_BUF + Sh::RAW;                   // [group 4][digit 6][n group 2][K block][128 B]
+    float* sScale = reinterpret_cast<float*>(sB + Sh::B_BYTES);          // [group 4][line 128]
+    int* sEl = reinterpret_cast<int*>(sScale + 4 * kTcLines);            // [line 128] exponent of the line scale
+    int* sEb = sEl + kTcLines;                                           // [16] exponent of the column scale
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sEb + kTcN);            // [0] digit tile consumed, [1] drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int64_t G0 = (int64_t)b.E[0] * Q;
+    const int64_t P3 = (DIM == 3) ? (int64_t)b.R[2] * W : 1;
+    const int64_t P2 = (int64_t)b.R[1] * W;
+    const int64_t total = P3 * P2;
+    const int64_t line0 = (int64_t)blockIdx.x * kTcLines;
+    const float2* T2 = reinterpret_cast<const float2*>(scratch + b.t2_off);
+    const int64_t gs = total * G0;
+    const int* ex = reinterpret_cast<const int*>(scratch + b.ex_off);
+    const int nchunks = (i0_hi - i0_lo) / C + 1;
+    const int jobs = 4 * nchunks;
+
+    auto issue_copy = [&](int j) {
+        const int c0 = i0_lo + (j >> 2) * C, gq = j & 3;
+        const int64_t row0 = (int64_t)(c0 - P - b.elo[0]) * Q;
+        const float2* src = T2 + (int64_t)gq * gs;
+        for (int idx = tid; idx < kTcLines * ROWS; idx += kTcThreads) {
+            const int l = idx / ROWS, r = idx - l * ROWS;
+            const int64_t line = line0 + l, gp = row0 + r;
+            const bool valid = line < total && gp < G0;
+            tc::cp_async8(sR + idx, valid ? src + line * G0 + gp : T2, valid);
+        }
+        tc::cp_async_commit();
+    };
+    issue_copy(0);
+
+    // line scales: alpha = v 2^(sigma_g - e_line - 1), e_line the recorded largest shifted exponent
+    int sig[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sig[k] = T.gshift[k];
+    if (tid < kTcLines) {
+        const int64_t line = line0 + tid;
+        const int m = (line < total) ? ex[line] : 0;
+        const int el = m > 0 ? m - kTcExpOffset - 127 : 0;      // unbiased exponent of the shifted line maximum
+        sEl[tid] = el + 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sScale[k * kTcLines + tid] = m > 0 ? pow2f(sig[k] - el - 1) : 0.f;
+    }
+    // B: per offset column n the largest exponent of X_g 2^-sigma_g over groups and Gauss points, then
+    // six digits of X_g 2^-sigma_g 2^-(e_n + 1), K-major [16 offsets x KW points] per group and digit
+    const double* Xc = T.X[0] + (int64_t)(2 * P) * W * TT * 4;
+    if (tid < kTcN) sEb[tid] = -100000;
+    __syncthreads();
+    for (int idx = tid; idx < 4 * W * TT; idx += kTcThreads) {
+        const int gq = idx / (W * TT), n = (idx / TT) % W, k = idx % TT;
+        const double x = Xc[((int64_t)n * TT + k) * 4 + (3 - gq)];
+        if (x != 0.0) atomicMax(&sEb[n], ilogb(x) - sig[gq]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 4 * kTcN * KW; idx += kTcThreads) {
+        const int gq = idx / (kTcN * KW), n = (idx / KW) % kTcN, k = idx % KW;
+        double r = 0.0;
+        if (n < W && k < TT && sEb[n] > -100000)
+            r = ldexp(Xc[((int64_t)n * TT + k) * 4 + (3 - gq)], -sig[gq] - sEb[n] - 1);
+        const int off = ((n >> 3) * (KW / 8) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(sB + (size_t)gq * kDigits * Sh::B_PART);
+#pragma unroll
+        for (int i = 0; i < kDigits; ++i) {
+            const double q = rint(ldexp(r, 7 + 8 * i)) * ldexp(1.0, -7 - 8 * i);
+            r -= q;
+            base[i * (Sh::B_PART / 2) + off] = __double2bfloat16(q);
+        }
+    }
+    if (tid == 0) {
+        tc::bar_init(&bars[0], kTcThreads / 32);
+        tc::bar_init(&bars[1], kTcThreads / 32);
+        tc::fence_bar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, Sh::TMEM_COLS);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    // the epilogue's output line for this thread (warp w: tensor-memory lanes 32 (w % 4) ..)
+    const int q4 = warp & 3, half = warp >> 2;
+    const int64_t my_line = line0 + q4 * 32 + lane;
+    int64_t rowbase = 0;
+    int slot0 = 0;
+    if (my_line < total) {
+        const int64_t pair3 = my_line / P2, pair2 = my_line - pair3 * P2;
+        const int i1 = b.rlo[1] + (int)(pair2 / W), d1 = (int)(pair2 % W);
+        const int i2 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
+        const int d2 = (DIM == 3) ? (int)(pair3 % W) : 0;
+        rowbase = (int64_t)g.m[0] * (i1 + (int64_t)g.m[1] * i2);
+        slot0 = W * (d1 + W * d2);
+    }
+    const int my_el = sEl[q4 * 32 + lane];
+
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(kTcLines, kTcN, 1, 0);
+    const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+    bool ok = true;
+    int done_chunks = 0;
+    for (int j = 0; j < jobs; ++j) {
+        const int k = j >> 2, gq = j & 3;
+        const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
+        tc::cp_async_wait<0>();
+        // the digit tile was last read by the MMAs of job j - 1
+        const bool wok = (j >= 1) ? tc::bar_wait(&bars[0], (uint32_t)((j - 1) & 1), kTcWaitIter) : true;
+        ok = __syncthreads_and(wok) != 0;
+        if (!ok) break;
+        // digits of the raw tile, 8 lines x 1 Gauss point per item
+        for (int item = tid; item < 16 * ROWS; item += kTcThreads) {
+            const int lg = item / ROWS, r = item - lg * ROWS;
+            uint32_t w[kDigits][4];
+#pragma unroll
+            for (int l = 0; l < 8; l += 2) {
+                float qa[kDigits], qb[kDigits];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int line = lg * 8 + l + u;
+                    const float2 v = sR[(size_t)line * ROWS + r];
+                    const float sc = sScale[gq * kTcLines + line];
+                    float rh = __fmul_rn(v.x, sc), rl = __fmul_rn(v.y, sc);
+#pragma unroll
+                    for (int i = 0; i < kDigits; ++i) {
+                        const float up = __int_as_float((127 + 7 + 8 * i) << 23), dn = __int_as_float((127 - 7 - 8 * i) << 23);
+                        const float q = __fmul_rn(rintf(__fmul_rn(__fadd_rn(rh, rl), up)), dn);
+                        rh = __fsub_rn(rh, q);
+                        (u ? qb : qa)[i] = q;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kDigits; ++i) w[i][l / 2] = pack2(__float2bfloat16_rn(qa[i]), __float2bfloat16_rn(qb[i]));
+            }
+            const size_t off = ((size_t)lg * ROWS + r) * 16;
+#pragma unroll
+            for (int i = 0; i < kDigits; ++i)
+                *reinterpret_cast<uint4*>(sA + (size_t)i * Sh::A_SLICE + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        }
+        tc::fence_async_smem();
+        __syncthreads();                              // raw tile free, digit tile complete
+        if (j + 1 < jobs) issue_copy(j + 1);
+        if (lane == 0) {
+            tc::fence_after_sync();
+            const uint64_t a0 = tc::sdesc(sA_addr, 128, ROWS * 16);
+            const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * kDigits * Sh::B_PART), 128, (KW / 8) * 128);
+            for (int c = warp; c < nc; c += kTcThreads / 32) {
+#pragma unroll
+                for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
+                    const uint64_t arow = (uint64_t)(c * Q + ks * 16);
+#pragma unroll
+                    for (int i = 0; i < kDigits; ++i)
+#pragma unroll
+                        for (int jd = 0; jd < kDigits - i; ++jd) {
+                            const int lev = (i + jd < 3) ? i + jd : 3;
+                            const uint64_t ad = a0 + (uint64_t)(i * Sh::A_SLICE / 16) + arow;
+                            const uint64_t bd = b0 + (uint64_t)((jd * Sh::B_PART + ks * 256) / 16);
+                            // the first product into each accumulator block of the row starts it
+                            const bool first = gq == 0 && ks == 0 && (lev < 3 ? (i == 0) : (i == 0 && jd == 3));
+                            tc::mma_bf16(tmem + (uint32_t)((c * kAcc + lev) * kTcN), ad, bd, IDESC, first ? 0u : 1u);
+                        }
+                }
+            }
+            tc::commit(&bars[0]);
+        }
+        if (gq == 3) {
+            // rows of the chunk: the four level blocks added in double-float, scaled back, rounded to double
+            ok = __syncthreads_and(tc::bar_wait(&bars[0], (uint32_t)(j & 1), kTcWaitIter)) != 0;
+            if (!ok) break;
+            tc::fence_after_sync();
+            for (int c = half; c < nc; c += 2) {
+                float v[kAcc][16];
+#pragma unroll
+                for (int a = 0; a < kAcc; ++a)
+                    tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((c * kAcc + a) * kTcN), v[a]);
+                if (my_line < total) {
+                    const int64_t row = c0 + c + rowbase;
+#pragma unroll
+                    for (int dd = 0; dd < W; ++dd) {
+                        float sh = v[0][dd], sl = 0.f;
+#pragma unroll
+                        for (int a = 1; a < kAcc; ++a) {
+                            const float t = __fadd_rn(sh, v[a][dd]);
+                            const float z = __fsub_rn(t, sh);
+                            sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(v[a][dd], z)));
+                            sh = t;
+                        }
+                        const int e = my_el + sEb[dd] + 1;
+                        double out;
+                        if (e > -100 && e < 100) {
+                            const float f = pow2f(e);
+                            out = df2d_exact(__fmul_rn(sh, f), __fmul_rn(sl, f));
+                        } else {
+                            out = ldexp((double)sh + (double)sl, e);
+                        }
+                        ell[(int64_t)(slot0 + dd) * N + row] = (sEb[dd] > -100000) ? out : 0.0;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            done_chunks = k + 1;
+        }
+    }
+    if (!ok) {
+        tc::cp_async_wait<0>();
+        if (tid == 0) atomicOr(&g_tc_status, 1);
+        if (lane == 0) tc::commit(&bars[1]);
+        tc::bar_wait(&bars[1], 0u, kTcWaitIter);
+        if (half == 0 && my_line < total)
+            for (int i0 = i0_lo + done_chunks * C; i0 <= i0_hi; ++i0)
+                for (int dd = 0; dd < W; ++dd)
+                    ell[(int64_t)(slot0 + dd) * N + rowbase + i0] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, Sh::TMEM_COLS);
+}
+
+template <int P, int DIM, bool F64>
+static cudaError_t stage_x_tc_boxes(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, void* ell,
                                     int64_t N, cudaStream_t s, bool* used)
 {
-    using Sh = TcShape<P>;
     constexpr int W = 2 * P + 1;
+    constexpr int SMEM = F64 ? Tc64Shape<P>::SMEM : TcShape<P>::SMEM;
     *used = false;
     const int card_lo = 2 * P, card_hi = g.m[0] - 2 * P - 1;
     if (card_hi < card_lo) return cudaSuccess;
@@ -297,7 +606,8 @@ static cudaError_t stage_x_tc_boxes(const Geo& g, const Tables& T, const BoxSet&
     if (!attr_set) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return cudaSuccess;
-        cudaError_t e = cudaFuncSetAttribute(k_stage_x_tc<P, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+        cudaError_t e = F64 ? cudaFuncSetAttribute(k_stage_x_tc64<P, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM)
+                            : cudaFuncSetAttribute(k_stage_x_tc<P, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -305,11 +615,15 @@ static cudaError_t stage_x_tc_boxes(const Geo& g, const Tables& T, const BoxSet&
         const Box& b = bs.box[k];
         const int lo = max(card_lo, b.rlo[0]), hi = min(card_hi, b.rlo[0] + b.R[0] - 1);
         if (hi < lo) continue;
+        if (F64 && b.ex_off < 0) return cudaErrorInvalidValue;
         const int64_t lines = ((DIM == 3) ? (int64_t)b.R[2] * W : 1) * b.R[1] * W;
         const int64_t grid = (lines + kTcLines - 1) / kTcLines;
         if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
         launch_begin(K_STAGE_X_TC, s);
-        k_stage_x_tc<P, DIM><<<(unsigned)grid, kTcThreads, Sh::SMEM, s>>>(g, T, b, lo, hi, scratch, ell, N);
+        if constexpr (F64)
+            k_stage_x_tc64<P, DIM><<<(unsigned)grid, kTcThreads, SMEM, s>>>(g, T, b, lo, hi, scratch, (double*)ell, N);
+        else
+            k_stage_x_tc<P, DIM><<<(unsigned)grid, kTcThreads, SMEM, s>>>(g, T, b, lo, hi, scratch, (float*)ell, N);
         launch_end(K_STAGE_X_TC, s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -318,24 +632,32 @@ static cudaError_t stage_x_tc_boxes(const Geo& g, const Tables& T, const BoxSet&
     return cudaSuccess;
 }
 
-// Tensor-core stage X for the cardinal rows of every explicit box (FP32 values,
-// degrees 2..5); *used tells whether it ran (the CUDA-core stage X then skips
-// those rows).
-cudaError_t launch_stage_x_tc(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, float* ell,
-                              int64_t N, cudaStream_t s, bool* used)
+template <bool F64>
+static cudaError_t stage_x_tc_dispatch(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch,
+                                       void* ell, int64_t N, cudaStream_t s, bool* used)
 {
-    *used = false;
     switch (g.p * 4 + g.dim) {
-    case 2 * 4 + 2: return stage_x_tc_boxes<2, 2>(g, T, bs, scratch, ell, N, s, used);
-    case 2 * 4 + 3: return stage_x_tc_boxes<2, 3>(g, T, bs, scratch, ell, N, s, used);
-    case 3 * 4 + 2: return stage_x_tc_boxes<3, 2>(g, T, bs, scratch, ell, N, s, used);
-    case 3 * 4 + 3: return stage_x_tc_boxes<3, 3>(g, T, bs, scratch, ell, N, s, used);
-    case 4 * 4 + 2: return stage_x_tc_boxes<4, 2>(g, T, bs, scratch, ell, N, s, used);
-    case 4 * 4 + 3: return stage_x_tc_boxes<4, 3>(g, T, bs, scratch, ell, N, s, used);
-    case 5 * 4 + 2: return stage_x_tc_boxes<5, 2>(g, T, bs, scratch, ell, N, s, used);
-    case 5 * 4 + 3: return stage_x_tc_boxes<5, 3>(g, T, bs, scratch, ell, N, s, used);
+    case 2 * 4 + 2: return stage_x_tc_boxes<2, 2, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 2 * 4 + 3: return stage_x_tc_boxes<2, 3, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 3 * 4 + 2: return stage_x_tc_boxes<3, 2, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 3 * 4 + 3: return stage_x_tc_boxes<3, 3, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 4 * 4 + 2: return stage_x_tc_boxes<4, 2, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 4 * 4 + 3: return stage_x_tc_boxes<4, 3, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 5 * 4 + 2: return stage_x_tc_boxes<5, 2, F64>(g, T, bs, scratch, ell, N, s, used);
+    case 5 * 4 + 3: return stage_x_tc_boxes<5, 3, F64>(g, T, bs, scratch, ell, N, s, used);
     default: return cudaSuccess;
     }
+}
+
+// Tensor-core stage X for the cardinal rows of every explicit box (FP32 values
+// with T.tc, FP64 values with T.tc64; degrees 2..5); *used tells whether it ran
+// (the CUDA-core stage X then skips those rows).
+cudaError_t launch_stage_x_tc(const Geo& g, const Tables& T, const BoxSet& bs, const double* scratch, void* ell,
+                              int f64, int64_t N, cudaStream_t s, bool* used)
+{
+    *used = false;
+    return f64 ? stage_x_tc_dispatch<true>(g, T, bs, scratch, ell, N, s, used)
+               : stage_x_tc_dispatch<false>(g, T, bs, scratch, ell, N, s, used);
 }
 
 }  // namespace iga

@@ -575,4 +575,173 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Manufactured solution u(x) = prod_d sin(pi x_d) of the paper's Poisson
+// experiments (Sec. 7.3): load F_i = a(u, B_i) = int kappa grad u . grad B_i dx
+// and energy a(u, u), pulled back with the assembly's Gauss rule
+// (grad B_i = J^{-T} grad_xi B_i, dx = |det J| dxi, eq. ChangeOfVars), in FP64.
+// Pass 1 (every Gauss point of the patch): v = w kappa |det J| J^{-1} grad u
+// and e = w kappa |det J| |grad u|^2.  Pass 2 (one thread per basis function):
+// F_i = sum over the Gauss points of supp(B_i) of v . grad_xi B_i.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_mms_points(Geo g, MmsArgs A)
+{
+    const int Q = g.p + 1;
+    const int64_t G0 = (int64_t)g.n_el[0] * Q, G1 = (int64_t)g.n_el[1] * Q;
+    const int64_t G2 = (DIM == 3) ? (int64_t)g.n_el[2] * Q : 1;
+    const int64_t npts = G0 * G1 * G2;
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= npts) return;
+    const int gg[3] = {(int)(item % G0), (int)((item / G0) % G1), (int)(item / (G0 * G1))};
+    double xi[3] = {0, 0, 0}, x[3] = {0, 0, 0}, w = 1.0;
+    for (int d = 0; d < DIM; ++d) { xi[d] = A.gx[d][gg[d]]; w *= A.wq[d][gg[d]]; }
+    double Ji[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, det = 1.0;
+    if (g.map_kind == IGA_MAP_SINPROD) {
+        // J = I + amp 1 gr^T: det = 1 + amp sum gr, J^{-1} = I - c 1 gr^T, c = amp / det
+        double sv[3], cv[3], P = 1.0, gr[3] = {0, 0, 0}, gsum = 0.0;
+        for (int d = 0; d < DIM; ++d) { sincospi(xi[d], &sv[d], &cv[d]); P *= sv[d]; }
+        for (int b = 0; b < DIM; ++b) {
+            double v = CUDART_PI * cv[b];
+            for (int j = 0; j < DIM; ++j) if (j != b) v *= sv[j];
+            gr[b] = v;
+            gsum += v;
+        }
+        det = 1.0 + g.amp * gsum;
+        const double c = g.amp / det;
+        for (int a = 0; a < DIM; ++a) {
+            x[a] = xi[a] + g.amp * P;
+            for (int b = 0; b < DIM; ++b) Ji[a][b] = (a == b ? 1.0 : 0.0) - c * gr[b];
+        }
+    } else if (g.map_kind == IGA_MAP_AFFINE) {
+        double J[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int a = 0; a < DIM; ++a) {
+            x[a] = g.aff[9 + a];
+            for (int b = 0; b < DIM; ++b) { J[a][b] = g.aff[a * 3 + b]; x[a] += J[a][b] * xi[b]; }
+        }
+        if (DIM == 2) {
+            det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det; Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+        } else {
+            det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                  J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    // cofactor of J[b][a] over det
+                    const int r0 = (b + 1) % 3, r1 = (b + 2) % 3, c0 = (a + 1) % 3, c1 = (a + 2) % 3;
+                    Ji[a][b] = (J[r0][c0] * J[r1][c1] - J[r0][c1] * J[r1][c0]) / det;
+                }
+        }
+    } else {
+        for (int a = 0; a < DIM; ++a) x[a] = xi[a];
+    }
+    double su[3], cu[3];
+    for (int d = 0; d < DIM; ++d) sincospi(x[d], &su[d], &cu[d]);
+    double gu[3] = {0, 0, 0}, g2 = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        double v = CUDART_PI * cu[a];
+        for (int b = 0; b < DIM; ++b) if (b != a) v *= su[b];
+        gu[a] = v;
+        g2 += v * v;
+    }
+    const double f = w * kappa_at(g, x) * fabs(det);
+    for (int a = 0; a < DIM; ++a) {
+        double v = 0.0;
+        for (int b = 0; b < DIM; ++b) v += Ji[a][b] * gu[b];
+        A.V[a * npts + item] = f * v;
+    }
+    A.E[item] = f * g2;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_mms_rows(Geo g, MmsArgs A, double* F)
+{
+    const int p = g.p, Q = p + 1;
+    const int64_t N = (int64_t)g.m[0] * g.m[1] * (DIM == 3 ? g.m[2] : 1);
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    const int64_t G0 = (int64_t)g.n_el[0] * Q, G1 = (int64_t)g.n_el[1] * Q;
+    const int64_t G2 = (DIM == 3) ? (int64_t)g.n_el[2] * Q : 1;
+    const int64_t npts = G0 * G1 * G2;
+    const int ii[3] = {(int)(row % g.m[0]), (int)((row / g.m[0]) % g.m[1]), (int)(row / ((int64_t)g.m[0] * g.m[1]))};
+    int elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+    for (int d = 0; d < DIM; ++d) { elo[d] = max(0, ii[d] - p); ehi[d] = min(g.n_el[d] - 1, ii[d]); }
+    double acc = 0.0;
+    for (int e2 = elo[2]; e2 <= ehi[2]; ++e2)
+    for (int r2 = 0; r2 < (DIM == 3 ? Q : 1); ++r2) {
+        const int g2i = e2 * Q + r2;
+        const double v2 = (DIM == 3) ? A.bv[2][g2i * Q + (ii[2] - e2)] : 1.0;
+        const double d2 = (DIM == 3) ? A.bd[2][g2i * Q + (ii[2] - e2)] : 0.0;
+        for (int e1 = elo[1]; e1 <= ehi[1]; ++e1)
+        for (int r1 = 0; r1 < Q; ++r1) {
+            const int g1i = e1 * Q + r1;
+            const double v1 = A.bv[1][g1i * Q + (ii[1] - e1)], d1 = A.bd[1][g1i * Q + (ii[1] - e1)];
+            for (int e0 = elo[0]; e0 <= ehi[0]; ++e0)
+            for (int r0 = 0; r0 < Q; ++r0) {
+                const int g0i = e0 * Q + r0;
+                const double v0 = A.bv[0][g0i * Q + (ii[0] - e0)], d0 = A.bd[0][g0i * Q + (ii[0] - e0)];
+                const int64_t pt = g0i + G0 * (g1i + G1 * (int64_t)(DIM == 3 ? g2i : 0));
+                double t = A.V[pt] * d0 * v1 + A.V[npts + pt] * v0 * d1;
+                if (DIM == 3) t = t * v2 + A.V[2 * npts + pt] * v0 * v1 * d2;
+                acc += t;
+            }
+        }
+    }
+    F[row] = acc;
+}
+
+// deterministic sum: per-block tree sums in a fixed order, then one block over the partial sums
+__global__ void __launch_bounds__(kBlock) k_sum_partial(int64_t n, const double* a, double* partial)
+{
+    __shared__ double sh[kBlock];
+    double s = 0.0;
+    const int64_t per = (int64_t)kBlock * 8;
+    const int64_t base = (int64_t)blockIdx.x * per;
+    for (int k = 0; k < 8; ++k) {
+        const int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+        if (i < n) s += a[i];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_manufactured(const Geo& g, const MmsArgs& A, double* F, double* energy, double* partial,
+                                int64_t npart, cudaStream_t s)
+{
+    const int Q = g.p + 1;
+    int64_t npts = 1, N = 1;
+    for (int d = 0; d < g.dim; ++d) { npts *= (int64_t)g.n_el[d] * Q; N *= g.m[d]; }
+    const unsigned gp = (unsigned)((npts + kBlock - 1) / kBlock), gr = (unsigned)((N + kBlock - 1) / kBlock);
+    launch_begin(K_MMS, s);
+    if (g.dim == 3) k_mms_points<3><<<gp, kBlock, 0, s>>>(g, A);
+    else k_mms_points<2><<<gp, kBlock, 0, s>>>(g, A);
+    launch_end(K_MMS, s);
+    launch_begin(K_MMS, s);
+    if (g.dim == 3) k_mms_rows<3><<<gr, kBlock, 0, s>>>(g, A, F);
+    else k_mms_rows<2><<<gr, kBlock, 0, s>>>(g, A, F);
+    launch_end(K_MMS, s);
+    // energy: sum of E over the points, then of the partial sums (both deterministic)
+    int64_t n = npts;
+    const double* src = A.E;
+    double* bufs[2] = {partial, partial + npart};
+    int k = 0;
+    while (true) {
+        const int64_t nb = (n + (int64_t)kBlock * 8 - 1) / ((int64_t)kBlock * 8);
+        double* dst = (nb == 1) ? energy : bufs[k];
+        launch_begin(K_MMS, s);
+        k_sum_partial<<<(unsigned)nb, kBlock, 0, s>>>(n, src, dst);
+        launch_end(K_MMS, s);
+        if (nb == 1) break;
+        src = dst;
+        n = nb;
+        k ^= 1;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace iga

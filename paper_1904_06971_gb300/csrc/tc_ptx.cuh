@@ -122,6 +122,11 @@ __device__ __forceinline__ void cp_async4(void* dst_smem, const void* src, bool 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
                  :: "r"(smem_addr(dst_smem)), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                 :: "r"(smem_addr(dst_smem)), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }

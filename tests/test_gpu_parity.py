@@ -126,6 +126,24 @@ def test_exact_f32_tensor_core_stage(iga, prob, arith):
     assert rel(v, ref32.astype(np.float64)) <= 2e-6
 
 
+@pytest.mark.parametrize("arith", ["df64_tc"], indirect=True)
+@pytest.mark.parametrize("prob", TC_EXACT, ids=lambda q: f"{q.dim}d_p{q.p}_{'x'.join(map(str, q.n_el))}")
+def test_exact_f64_tensor_core_stage(iga, prob, arith):
+    """FP64 values with stage X of the cardinal rows as exact BF16 digit products on the tensor cores:
+    the FP64 tolerance against the oracle, and agreement with the double-float CUDA-core contraction."""
+    iga.set_arithmetic("f64", "df64")
+    ref_df = gpu_exact(iga, prob)
+    use(iga, "f64", arith)
+    assert iga.get_arithmetic("f64") == "df64_tc"
+    iga.profile_read()
+    iga.profile_enable(True)
+    v = gpu_exact(iga, prob)
+    iga.profile_enable(False)
+    assert iga.profile_read()["stage_x_tc"][0] >= 2      # group shifts + at least one stage launch
+    assert rel(v, oracle.exact_matrix(prob)) <= TOL64
+    assert rel(v, ref_df) <= TOL64
+
+
 SMALL_SURR = [
     (W.CFG_2D_P2.problem, 4, 3),
     (W.CFG_2D_P2.problem, 3, 2),
@@ -151,7 +169,7 @@ SMALL_SURR = [
 ]
 
 
-@pytest.mark.parametrize("arith", ["df64", "fp64"], indirect=True)
+@pytest.mark.parametrize("arith", ["df64", "fp64", "df64_tc"], indirect=True)
 @pytest.mark.parametrize("prob,M,q", SMALL_SURR,
                          ids=lambda x: f"{x.dim}d_p{x.p}_{'x'.join(map(str, x.n_el))}" if hasattr(x, "dim") else str(x))
 def test_surrogate_full_matrix(iga, prob, M, q, arith):
@@ -229,7 +247,8 @@ def _sampled_rows(prob, k, seed):
 
 
 @pytest.mark.parametrize("wl,arith", [(W.CFG_3D_P3, "df64"), (W.CFG_3D_P4_F64, "df64"), (W.CFG_3D_P4, "fp32"),
-                                     (W.CFG_3D_P4, "bf16x3")], ids=["p3_64", "p4_96_f64", "p4_96_f32", "p4_96_f32_tc"],
+                                     (W.CFG_3D_P4, "bf16x3"), (W.CFG_3D_P4_F64, "df64_tc"), (W.CFG_3D_P3, "df64_tc")],
+                         ids=["p3_64", "p4_96_f64", "p4_96_f32", "p4_96_f32_tc", "p4_96_f64_tc", "p3_64_tc"],
                          indirect=["arith"])
 def test_full_size_surrogate_sampled_rows(iga, wl, arith):
     use(iga, wl.dtype, arith)
@@ -264,8 +283,10 @@ def test_full_size_surrogate_sampled_rows(iga, wl, arith):
     A.destroy()
 
 
-@pytest.mark.parametrize("wl", [W.CFG_3D_P3, W.CFG_3D_P4_F64], ids=lambda w: w.name)
-def test_full_size_exact_sampled_rows(iga, wl):
+@pytest.mark.parametrize("wl,arith", [(W.CFG_3D_P3, "df64"), (W.CFG_3D_P4_F64, "df64"), (W.CFG_3D_P4_F64, "df64_tc")],
+                         ids=["p3_64", "p4_96", "p4_96_tc"], indirect=["arith"])
+def test_full_size_exact_sampled_rows(iga, wl, arith):
+    use(iga, "f64", arith)
     prob = wl.problem
     A = iga.assemble_exact(prob, dtype="f64")
     vals = A.values()
