@@ -291,27 +291,28 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
 // Every T2 value of a line (double-float) is scaled by a power of two to
 // |alpha| < 1 -- per line, from the largest exponent stage Y recorded, with the
 // four T2 groups balanced by powers of two sigma_g against the pair weights
-// they meet -- and written as six signed base-256 digits alpha = sum_i a_i,
+// they meet -- and written as seven signed base-256 digits alpha = sum_i a_i,
 // a_i = (integer of magnitude <= 129) 2^-(7+8i), each exact in BF16.  The pair
-// weights (FP64) get the same six digits per offset column.  A product a_i b_j
-// is an integer times 2^-(14+8(i+j)), so the products of one level L = i + j
-// summed over the K = 4 (p+1)^2 Gauss points of a row stay below 2^24 quanta:
-// the FP32 accumulation of levels 0, 1 and 2 is exact, each in its own block of
-// tensor memory; levels 3..5 share a fourth block (their FP32 rounding is
-// below 2^-48 of the row).  Levels >= 6 are dropped (below 2^-48).  The four
-// blocks are added in double-float, scaled back and rounded once to double.
+// weights (FP64) get the same seven digits per offset column.  A product
+// a_i b_j is an integer times 2^-(14+8(i+j)), so the products of one level
+// L = i + j <= 3 summed over the K = 4 (p+1)^2 Gauss points of a row stay below
+// 2^24 quanta: their FP32 accumulation is exact, each level in its own block of
+// tensor memory; levels 4..6 share a fifth block (its FP32 rounding is below
+// 2^-50 of the row's terms).  Levels >= 7 and the digits beyond the seventh
+// are dropped (below 2^-55).  The five blocks are added in double-float, scaled
+// back and rounded once to double.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kDigits = 6;              // BF16 digits per value
-constexpr int kAcc = 4;                 // tensor-memory accumulators per row: levels 0, 1, 2, 3..5
+constexpr int kDigits = 7;              // BF16 digits per value
+constexpr int kAcc = 5;                 // tensor-memory accumulators per row: levels 0, 1, 2, 3, 4..6
 
 template <int P>
 struct Tc64Shape {
     static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     static constexpr int KW = (TT + 15) / 16 * 16;
     static constexpr int KSTEPS = KW / 16;
-    static constexpr int C = (P >= 5) ? 4 : 8;               // rows i0 per chunk (kAcc * 16 columns each)
+    static constexpr int C = (P >= 5) ? 3 : 6;               // rows i0 per chunk (kAcc * 16 columns each)
     static constexpr int ROWS = (C - 1) * Q + KW;
     static constexpr int A_SLICE = 16 * ROWS * 16;
     static constexpr int A_BUF = kDigits * A_SLICE;          // one BF16 tile (single-buffered)
@@ -365,8 +366,8 @@ cudaError_t launch_tc_group_shift(const Geo& g, const Tables& T, int* gshift, cu
 // one raw and one digit tile: the copy of job j + 1 runs during the MMAs of
 // job j, the digits of job j + 1 wait for those MMAs.  Lane 0 of warp w issues
 // the MMAs of the chunk rows w, w + 8, ...: for every row, K step and digit
-// pair (i, j) with i + j <= 5, one M = 128, N = 16, K = 16 MMA into the
-// accumulator block of level min(i + j, 3).
+// pair (i, j) with i + j <= 6, one M = 128, N = 16, K = 16 MMA into the
+// accumulator block of level min(i + j, 4).
 template <int P, int DIM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch, double* ell, int64_t N)
@@ -529,11 +530,11 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
                     for (int i = 0; i < kDigits; ++i)
 #pragma unroll
                         for (int jd = 0; jd < kDigits - i; ++jd) {
-                            const int lev = (i + jd < 3) ? i + jd : 3;
+                            const int lev = (i + jd < kAcc - 1) ? i + jd : kAcc - 1;
                             const uint64_t ad = a0 + (uint64_t)(i * Sh::A_SLICE / 16) + arow;
                             const uint64_t bd = b0 + (uint64_t)((jd * Sh::B_PART + ks * 256) / 16);
                             // the first product into each accumulator block of the row starts it
-                            const bool first = gq == 0 && ks == 0 && (lev < 3 ? (i == 0) : (i == 0 && jd == 3));
+                            const bool first = gq == 0 && ks == 0 && i == 0 && (lev < kAcc - 1 || jd == kAcc - 1);
                             tc::mma_bf16(tmem + (uint32_t)((c * kAcc + lev) * kTcN), ad, bd, IDESC, first ? 0u : 1u);
                         }
                 }
@@ -541,7 +542,7 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
             tc::commit(&bars[0]);
         }
         if (gq == 3) {
-            // rows of the chunk: the four level blocks added in double-float, scaled back, rounded to double
+            // rows of the chunk: the level blocks added in double-float, scaled back, rounded to double
             ok = __syncthreads_and(tc::bar_wait(&bars[0], (uint32_t)(j & 1), kTcWaitIter)) != 0;
             if (!ok) break;
             tc::fence_after_sync();

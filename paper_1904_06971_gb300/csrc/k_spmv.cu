@@ -4,13 +4,14 @@
 // column is i + delta_0 + m_0 (delta_1 + m_1 delta_2).  Rows whose whole
 // stencil stays inside the index range skip the bounds tests.
 //
-// FP64 values: GB300 runs FP64 FMAs at 1/64 of the FP32 rate, below what the
-// HBM stream of the values needs, so two thirds of the products (delta_0 >=
-// (2p+1)/3) are formed in double-float arithmetic on the FP32 pipe -- x split
-// once into (hi, lo) float pairs, each stored value split by integer operations
-// as it streams in, a renormalised double-float row sum -- and the other third
-// with FP64 FMAs, so that neither pipe limits the stream; the two partial sums
-// are added once per row.
+// FP64 values: GB300 runs FP64 FMAs at 1/64 of the FP32 rate, just below what
+// the HBM stream of the values needs, so a quarter of the products (the last
+// (2p+1)/4 offsets delta_0 of every run) are formed in double-float arithmetic
+// on the FP32 pipe -- x split once into (hi, lo) float pairs, each stored value
+// split by integer operations as it streams in, a renormalised double-float
+// row sum -- and the rest with FP64 FMAs, so that neither pipe limits the
+// stream (more double-float work delays the loads behind it); the two partial
+// sums are added once per row.
 #include "arith.cuh"
 #include "iga_internal.cuh"
 
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_df(int m0, int m1, int m2, cons
                                                     double* __restrict__ y)
 {
     constexpr int W = 2 * P + 1;
-    constexpr int F64 = W / 3;                  // slots delta_0 + p < F64 use FP64 FMAs
+    constexpr int F64 = W - W / 4;              // slots delta_0 + p < F64 use FP64 FMAs, the rest double-float
     const int64_t N = (int64_t)m0 * m1 * m2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
