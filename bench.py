@@ -629,25 +629,23 @@ def fp32_tier_report(iga, torch, wl, A64, E64, exact_solution, args, steps: int 
     return out
 
 
-def equal_accuracy_report(iga, torch, wl, E, ms_exact, args, Ms=(2, 4, 6, 8, 12, 16), steps: int = 5,
+def equal_accuracy_report(iga, torch, wl, E, ms_exact, args, Ms=(2, 4, 6, 8, 12, 16), freqs=(20, 1), steps: int = 5,
                           warmup: int = 3):
     """Surrogate vs exact at equal accuracy of the discrete solution (Sec. 7.3): for the manufactured
-    solution u = prod sin(pi x_d) (iga_manufactured_load) the discretisation error ||u - u_h||_a of the
-    exact matrix (Galerkin orthogonality: a(u,u) - F.u_h) and, per sampling length M, the consistency
-    error ||u_h - u~_h||_A of the surrogate, both relative to ||u||_a; the paper's rule of thumb keeps
-    the consistency error at or below 5 % of the discretisation error.  Reports the surrogate step time
-    per M and the speed-up over the exact step at the largest M that satisfies the rule."""
+    solutions u = prod sin(k pi x_d) (k = 20 and k = 1, the paper's high- and low-frequency loads;
+    iga_manufactured_load) the discretisation error ||u - u_h||_a of the exact matrix (Galerkin
+    orthogonality: a(u,u) - F.u_h) and, per sampling length M, the consistency error ||u_h - u~_h||_A of
+    the surrogate, both relative to ||u||_a; the paper's rule of thumb keeps the consistency error at or
+    below 5 % of the discretisation error.  Reports the surrogate step time per M and the speed-up over
+    the exact step at the largest M that satisfies the rule.  When the discretisation error is below what
+    FP64 resolves in a(u,u) - F.u_h (relative square under 1e-12), it is reported as unresolved."""
     prob = wl.problem
     stream = torch.cuda.current_stream()
-    F, en = iga.manufactured_load(prob)
-    energy = en.item()
-    u_h, it_h, res_h = E.cg(F, tol=args.cg_tol, maxit=args.cg_maxit)
-    disc = float(np.sqrt(max(energy - torch.dot(F, u_h).item(), 0.0) / energy))
     gen = torch.Generator(device="cpu").manual_seed(0)
     tdt = torch.float64 if wl.dtype == "f64" else torch.float32
     x = torch.randn(prob.N, generator=gen, dtype=torch.float64).to(dtype=tdt, device="cuda")
     y = torch.empty_like(x)
-    rows = []
+    times = {}
     for M in Ms:
         A = iga.assemble_surrogate(prob, M, wl.q, dtype=wl.dtype)
 
@@ -655,21 +653,36 @@ def equal_accuracy_report(iga, torch, wl, E, ms_exact, args, Ms=(2, 4, 6, 8, 12,
             iga.assemble_surrogate(prob, M, wl.q, dtype=wl.dtype, out=A)
             A.apply(x, y)
 
-        ms, _ = _time_steps(torch, step, steps, warmup, stream)
-        u_s, it_s, res_s = A.cg(F, tol=args.cg_tol, maxit=args.cg_maxit)
-        d = (u_s - u_h).to(tdt)
-        cons = float(np.sqrt(max(torch.dot(d.double(), E.apply(d).double()).item(), 0.0) / energy))
-        rows.append({"M": M, "q": wl.q, "ms_per_step": ms, "value": prob.nnz / (ms * 1e-3),
-                     "consistency_rel_energy": cons, "consistency_over_discretisation": cons / disc,
-                     "speedup_vs_exact": ms_exact / ms, "cg_iters": it_s})
+        times[M], _ = _time_steps(torch, step, steps, warmup, stream)
         A.destroy()
-    ok = [r for r in rows if r["consistency_over_discretisation"] <= 0.05]
-    best = max(ok, key=lambda r: r["M"]) if ok else None
-    return {"workload": wl.name, "solution": "u = prod_d sin(pi x_d) (Sec. 7.3), homogeneous Dirichlet",
-            "norm": "energy a(.,.), relative to ||u||_a", "discretisation_rel_energy": disc,
-            "exact_cg_iters": it_h, "exact_ms_per_step": ms_exact, "rule": "consistency <= 5% of discretisation",
-            "per_M": rows, "largest_M_within_rule": best["M"] if best else None,
-            "speedup_at_equal_accuracy": best["speedup_vs_exact"] if best else None}
+    out = {"workload": wl.name, "norm": "energy a(.,.), relative to ||u||_a", "exact_ms_per_step": ms_exact,
+           "rule": "consistency <= 5% of discretisation",
+           "surrogate_ms_per_step": {str(M): times[M] for M in Ms}, "solutions": []}
+    for k in freqs:
+        F, en = iga.manufactured_load(prob, freq=k)
+        energy = en.item()
+        u_h, it_h, _ = E.cg(F, tol=args.cg_tol, maxit=args.cg_maxit)
+        d2 = (energy - torch.dot(F, u_h).item()) / energy
+        disc = float(np.sqrt(d2)) if d2 > 1e-12 else None
+        rows = []
+        for M in Ms:
+            A = iga.assemble_surrogate(prob, M, wl.q, dtype=wl.dtype)
+            u_s, it_s, _ = A.cg(F, tol=args.cg_tol, maxit=args.cg_maxit)
+            d = (u_s - u_h).to(tdt)
+            cons = float(np.sqrt(max(torch.dot(d.double(), E.apply(d).double()).item(), 0.0) / energy))
+            rows.append({"M": M, "q": wl.q, "consistency_rel_energy": cons,
+                         "consistency_over_discretisation": (cons / disc) if disc else None,
+                         "speedup_vs_exact": ms_exact / times[M], "cg_iters": it_s})
+            A.destroy()
+        ok = [r for r in rows if r["consistency_over_discretisation"] is not None
+              and r["consistency_over_discretisation"] <= 0.05]
+        best = max(ok, key=lambda r: r["M"]) if ok else None
+        out["solutions"].append({
+            "u": f"prod_d sin({k} pi x_d)", "discretisation_rel_energy": disc,
+            "discretisation_note": None if disc else "below FP64 resolution of a(u,u) - F.u_h",
+            "exact_cg_iters": it_h, "per_M": rows, "largest_M_within_rule": best["M"] if best else None,
+            "speedup_at_equal_accuracy": best["speedup_vs_exact"] if best else None})
+    return out
 
 
 def side_report(iga, torch, wl, steps: int, warmup: int):

@@ -360,8 +360,9 @@ int iga_num_kernels(void);
 const char* iga_kernel_name(int k);
 
 /*
- * Load vector and energy of the manufactured solution u(x) = prod_d sin(pi x_d)
- * (the paper's low-frequency Poisson solution, Sec. 7.3), for the split of a
+ * Load vector and energy of the manufactured solution u(x) = prod_d sin(k pi x_d)
+ * (k = freq in 1..1000; the paper's Poisson experiments use k = 1 and k = 20,
+ * Sec. 7.3), for the split of a
  * surrogate solution's error into discretisation and consistency parts (the
  * two terms of the a-priori bounds, eq. APrioriBoundH1; rule of thumb: keep the
  * consistency error at or below 5 % of the discretisation error):
@@ -376,7 +377,7 @@ const char* iga_kernel_name(int k);
  *   enqueued on the stream and allocates its scratch from the library's pool.
  */
 int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
-                          double* F, double* energy, void* stream);
+                          int freq, double* F, double* energy, void* stream);
 
 /*
  * Exact assembly that allocates no memory (the paper has no counterpart; this

@@ -79,7 +79,7 @@ def lib():
         L.orc_exact_rows.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp]
         L.orc_mass_rows.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp]
         L.orc_elementwise_dense.argtypes = [P, dp]
-        L.orc_manufactured_load.argtypes = [P, dp, dp]
+        L.orc_manufactured_load.argtypes = [P, ctypes.c_int, dp, dp]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -621,22 +621,23 @@ int orc_num_threads(void)
 }
 
 /* ------------------------------------------------------------------ */
-/* Manufactured solution u(x) = prod_d sin(pi x_d) (the paper's        */
-/* "low-frequency" Poisson solution, Sec. 7.3): the load vector        */
+/* Manufactured solution u(x) = prod_d sin(k pi x_d), k = 1 and k = 20  */
+/* being the paper's "low-" and "high-frequency" Poisson solutions     */
+/* (Sec. 7.3): the load vector                                          */
 /*   F_i = a(u, B_i) = int_Omega kappa grad u . grad B_i dx            */
 /* and the energy a(u, u), pulled back to the parameter domain with    */
 /* the same (p+1)-point Gauss rule as the stiffness matrix:            */
 /*   grad B_i = J^{-T} grad_xi B_i,  dx = |det J| dxi  (eq. ChangeOfVars). */
 /* ------------------------------------------------------------------ */
-static void mms_point(const orc_problem* P, const double* xi, double* gradu_pull, double* dens)
+static void mms_point(const orc_problem* P, int freq, const double* xi, double* gradu_pull, double* dens)
 {
     int n = P->dim;
     double x[3] = {0, 0, 0}, J[9];
     orc_map(P, xi, x, J);
     double gu[3] = {0, 0, 0};
     for (int a = 0; a < n; ++a) {
-        double v = ORC_PI * cos(ORC_PI * x[a]);
-        for (int b = 0; b < n; ++b) if (b != a) v *= sin(ORC_PI * x[b]);
+        double v = freq * ORC_PI * cos(freq * ORC_PI * x[a]);
+        for (int b = 0; b < n; ++b) if (b != a) v *= sin(freq * ORC_PI * x[b]);
         gu[a] = v;
     }
     /* inverse of J by cofactors: Jinv[b][a] = cof[a][b] / det */
@@ -669,9 +670,9 @@ static void mms_point(const orc_problem* P, const double* xi, double* gradu_pull
     *dens = f * g2;
 }
 
-int orc_manufactured_load(const orc_problem* P, double* F /* N */, double* energy)
+int orc_manufactured_load(const orc_problem* P, int freq, double* F /* N */, double* energy)
 {
-    if (!problem_ok(P)) return -1;
+    if (!problem_ok(P) || freq < 1) return -1;
     tab1d T[3];
     memset(T, 0, sizeof(T));
     if (build_tables(P, T)) return -2;
@@ -705,7 +706,7 @@ int orc_manufactured_load(const orc_problem* P, double* F /* N */, double* energ
                 wgt *= T[d].wq[g[d]];
             }
             double gp[3], dens;
-            mms_point(P, xi, gp, &dens);
+            mms_point(P, freq, xi, gp, &dens);
             for (int k = 0; k < n; ++k) {
                 double v = 1.0;
                 for (int d = 0; d < n; ++d) v *= tab_get(&T[d], g[d], ii[d], d == k);
@@ -725,7 +726,7 @@ int orc_manufactured_load(const orc_problem* P, double* F /* N */, double* energ
         double xi[3] = {0, 0, 0}, wgt = 1.0;
         for (int d = 0; d < n; ++d) { xi[d] = T[d].xi[gg[d]]; wgt *= T[d].wq[gg[d]]; }
         double gp[3], dens;
-        mms_point(P, xi, gp, &dens);
+        mms_point(P, freq, xi, gp, &dens);
         en += wgt * dens;
     }
     *energy = en;

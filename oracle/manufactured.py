@@ -2,8 +2,9 @@
 Poisson experiments and the split of the surrogate solution's error into a
 discretisation and a consistency part (Sec. 7.3).
 
-u(x) = prod_d sin(pi x_d) (the "low-frequency" solution of Sec. 7.3) vanishes
-on the boundary of the unit square / cube, so for maps of the unit cube onto
+u(x) = prod_d sin(k pi x_d) (k = 1: the "low-frequency", k = 20: the
+"high-frequency" solution of Sec. 7.3; k a positive integer) vanishes on the
+boundary of the unit square / cube, so for maps of the unit cube onto
 itself it solves the homogeneous Dirichlet problem -div(kappa grad u) = f.
 With the load F_i = a(u, B_i) (the Galerkin load of that f, no f needed) and
 the same Gauss rule a_h as the stiffness matrix, Galerkin orthogonality gives
@@ -23,13 +24,13 @@ from ._lib import _dptr, lib, make_problem
 from .linalg import apply, cg
 
 
-def manufactured_load(prob):
+def manufactured_load(prob, freq: int = 1):
     """(F, energy): F_i = a(u, B_i) for every basis function i (colexicographic), and a(u, u)."""
     P = make_problem(prob)
     N = int(np.prod([e + prob.p for e in prob.n_el]))
     F = np.zeros(N)
     en = np.zeros(1)
-    rc = lib().orc_manufactured_load(P, _dptr(F), _dptr(en))
+    rc = lib().orc_manufactured_load(P, int(freq), _dptr(F), _dptr(en))
     if rc != 0:
         raise ValueError(f"orc_manufactured_load failed ({rc})")
     return F, float(en[0])

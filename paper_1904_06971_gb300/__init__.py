@@ -97,7 +97,7 @@ def load():
         L.iga_assemble_exact_noalloc.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                                  ctypes.POINTER(Kappa), ctypes.c_int, vp, vp]
         L.iga_manufactured_load.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
-                                            ctypes.POINTER(Kappa), vp, vp, vp]
+                                            ctypes.POINTER(Kappa), ctypes.c_int, vp, vp, vp]
         L.iga_apply.argtypes = [H, vp, vp, vp]
         L.iga_cg.argtypes = [H, vp, vp, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_double)]
@@ -378,8 +378,8 @@ def profile_read():
     return {L.iga_kernel_name(k).decode(): (int(la[k]), float(ms[k])) for k in range(n)}
 
 
-def manufactured_load(prob, stream=None, kappa_ctrl=None):
-    """(F, energy) of the manufactured solution u = prod_d sin(pi x_d) (iga_manufactured_load):
+def manufactured_load(prob, freq: int = 1, stream=None, kappa_ctrl=None):
+    """(F, energy) of the manufactured solution u = prod_d sin(freq pi x_d) (iga_manufactured_load):
     F_i = a(u, B_i) as a float64 CUDA tensor of N entries and a(u, u) as a float64 CUDA scalar tensor."""
     import torch
     pt, mp, kp = _structs(prob, kappa_ctrl)
@@ -387,7 +387,7 @@ def manufactured_load(prob, stream=None, kappa_ctrl=None):
     F = torch.empty(N, dtype=torch.float64, device="cuda")
     en = torch.empty((), dtype=torch.float64, device="cuda")
     _check(load().iga_manufactured_load(ctypes.byref(pt), int(prob.p), ctypes.byref(mp), ctypes.byref(kp),
-                                        ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(en.data_ptr()),
+                                        int(freq), ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(en.data_ptr()),
                                         ctypes.c_void_p(_stream_ptr(stream))))
     return F, en
 

@@ -837,7 +837,7 @@ int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, co
     return IGA_OK;
 }
 
-int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa,
+int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, int freq,
                           double* F, double* energy, void* stream_v)
 {
     t_err.clear();
@@ -845,6 +845,7 @@ int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map,
     int rc = check_geometry(patch, p, map, kappa, g);
     if (rc) return rc;
     if (!F || !energy) return fail(IGA_EINVAL, "F and energy must be non-null device pointers");
+    if (freq < 1 || freq > 1000) return fail(IGA_EINVAL, "frequency k must be in 1..1000 (got %d)", freq);
     const int dim = g.dim, Q = p + 1;
     int64_t npts = 1;
     for (int d = 0; d < dim; ++d) npts *= (int64_t)g.n_el[d] * Q;
@@ -876,6 +877,7 @@ int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map,
     }
     A.V = scratch + o_V;
     A.E = scratch + o_E;
+    A.freq = freq;
     const char* stage = "basis tables";
     ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
     if (ce == cudaSuccess) { stage = "manufactured load"; ce = launch_manufactured(g, A, F, energy, scratch + o_part, npart, st); }

@@ -245,8 +245,9 @@ cudaError_t launch_spmv(int dim, int p, const int m[3], const void* values, int 
 // K4 part 1 alone: knots, collocation LU and evaluation tables of every variant.
 cudaError_t launch_spline_setup(const SplinePlan& sp, const SplineBufs& sb, cudaStream_t s);
 
-// ---- manufactured solution u = prod sin(pi x_d): load a(u, B_i) and energy a(u, u) (k_tables.cu) ----
+// ---- manufactured solution u = prod sin(k pi x_d): load a(u, B_i) and energy a(u, u) (k_tables.cu) ----
 struct MmsArgs {
+    int freq;                 // k
     const double* gx[3];      // [G] Gauss point coordinates
     const double* wq[3];      // [G] weights (times h)
     const double* bv[3];      // [G][p+1] values of the active basis functions

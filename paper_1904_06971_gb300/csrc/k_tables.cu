@@ -576,8 +576,8 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Manufactured solution u(x) = prod_d sin(pi x_d) of the paper's Poisson
-// experiments (Sec. 7.3): load F_i = a(u, B_i) = int kappa grad u . grad B_i dx
+// Manufactured solution u(x) = prod_d sin(k pi x_d) of the paper's Poisson
+// experiments (Sec. 7.3; k = 1 and k = 20 there): load F_i = a(u, B_i) = int kappa grad u . grad B_i dx
 // and energy a(u, u), pulled back with the assembly's Gauss rule
 // (grad B_i = J^{-T} grad_xi B_i, dx = |det J| dxi, eq. ChangeOfVars), in FP64.
 // Pass 1 (every Gauss point of the patch): v = w kappa |det J| J^{-1} grad u
@@ -636,10 +636,10 @@ __global__ void __launch_bounds__(kBlock) k_mms_points(Geo g, MmsArgs A)
         for (int a = 0; a < DIM; ++a) x[a] = xi[a];
     }
     double su[3], cu[3];
-    for (int d = 0; d < DIM; ++d) sincospi(x[d], &su[d], &cu[d]);
+    for (int d = 0; d < DIM; ++d) sincospi((double)A.freq * x[d], &su[d], &cu[d]);
     double gu[3] = {0, 0, 0}, g2 = 0.0;
     for (int a = 0; a < DIM; ++a) {
-        double v = CUDART_PI * cu[a];
+        double v = A.freq * CUDART_PI * cu[a];
         for (int b = 0; b < DIM; ++b) if (b != a) v *= su[b];
         gu[a] = v;
         g2 += v * v;

@@ -31,10 +31,11 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("freq", [1, 20])
 @pytest.mark.parametrize("prob", CASES, ids=lambda q: f"{q.dim}d_p{q.p}_{q.map_kind}")
-def test_manufactured_load_matches_oracle(iga, prob):
-    F, en = iga.manufactured_load(prob)
-    Fr, enr = manufactured.manufactured_load(prob)
+def test_manufactured_load_matches_oracle(iga, prob, freq):
+    F, en = iga.manufactured_load(prob, freq=freq)
+    Fr, enr = manufactured.manufactured_load(prob, freq=freq)
     assert np.abs(F.cpu().numpy() - Fr).max() <= 1e-12 * np.abs(Fr).max()
     assert abs(en.item() - enr) <= 1e-12 * enr
 

@@ -1,12 +1,12 @@
 """Pins of the oracle's manufactured-solution load and error split (no GPU).
 
-u(x) = prod_d sin(pi x_d), the low-frequency solution of the paper's Poisson
-experiments (Sec. 7.3).  F_i = a(u, B_i) and a(u, u) by the assembly's Gauss
+u(x) = prod_d sin(k pi x_d), the low- (k = 1) and high-frequency (k = 20)
+solutions of the paper's Poisson experiments (Sec. 7.3) for general k.  F_i = a(u, B_i) and a(u, u) by the assembly's Gauss
 rule are pinned against quantities fixed independently of the oracle:
-  * identity map, kappa = 1: -Laplace u = n pi^2 u, so for basis functions that
-    vanish on the boundary F_i = n pi^2 int u B_i, a tensor product of 1-D
+  * identity map, kappa = 1: -Laplace u = n (k pi)^2 u, so for basis functions that
+    vanish on the boundary F_i = n (k pi)^2 int u B_i, a tensor product of 1-D
     integrals computed here with scipy's adaptive quadrature and scipy's B-splines;
-  * a(u, u) = n pi^2 / 2^n for the identity map and kappa = 1;
+  * a(u, u) = n (k pi)^2 / 2^n for the identity map and kappa = 1;
   * sum_i F_i = a(u, 1) = 0 for any map and coefficient (partition of unity);
   * the discretisation error ||u - u_h||_a, from Galerkin orthogonality, falls
     like h^p under refinement (the H^1 rate of degree-p splines) and equals
@@ -28,8 +28,8 @@ def _knots(p, n_el):
     return np.concatenate([np.zeros(p), np.linspace(0.0, 1.0, n_el + 1), np.ones(p)])
 
 
-def _sin_moments(p, n_el):
-    """int_0^1 sin(pi x) B_i(x) dx for every B-spline of the open uniform knot vector (element by element)."""
+def _sin_moments(p, n_el, k=1):
+    """int_0^1 sin(k pi x) B_i(x) dx for every B-spline of the open uniform knot vector (element by element)."""
     t = _knots(p, n_el)
     m = n_el + p
     out = np.zeros(m)
@@ -40,22 +40,23 @@ def _sin_moments(p, n_el):
         tot = 0.0
         for a, c in zip(brk[:-1], brk[1:]):
             if c > a:
-                tot += quad(lambda x: np.sin(np.pi * x) * np.nan_to_num(b(x)), a, c, epsabs=1e-15, epsrel=1e-13)[0]
+                tot += quad(lambda x: np.sin(k * np.pi * x) * np.nan_to_num(b(x)), a, c, epsabs=1e-15, epsrel=1e-13)[0]
         out[i] = tot
         assert lo <= hi
     return out
 
 
-@pytest.mark.parametrize("dim,p,n_el", [(2, 2, (12, 10)), (3, 3, (7, 6, 8)), (2, 4, (9, 11))])
-def test_load_identity_map_equals_laplacian_moments(dim, p, n_el):
+@pytest.mark.parametrize("dim,p,n_el,k", [(2, 2, (12, 10), 1), (3, 3, (7, 6, 8), 1), (2, 4, (9, 11), 1),
+                                          (2, 3, (24, 22), 3)])
+def test_load_identity_map_equals_laplacian_moments(dim, p, n_el, k):
     prob = W.Problem(dim=dim, p=p, n_el=n_el, map_kind="identity", kappa_kind="const", kappa_a=1.0)
-    F, en = manufactured.manufactured_load(prob)
-    mom = [_sin_moments(p, ne) for ne in n_el]
+    F, en = manufactured.manufactured_load(prob, freq=k)
+    mom = [_sin_moments(p, ne, k) for ne in n_el]
     mi = multi_index(np.arange(prob.N), np.array(prob.m))
-    ref = dim * np.pi ** 2 * np.prod([mom[d][mi[:, d]] for d in range(dim)], axis=0)
+    ref = dim * (k * np.pi) ** 2 * np.prod([mom[d][mi[:, d]] for d in range(dim)], axis=0)
     I = interior_dofs(prob)
     assert np.abs(F[I] - ref[I]).max() <= 2e-6 * np.abs(ref).max()
-    assert abs(en - dim * np.pi ** 2 / 2 ** dim) <= 1e-6 * en
+    assert abs(en - dim * (k * np.pi) ** 2 / 2 ** dim) <= 1e-6 * en
 
 
 @pytest.mark.parametrize("prob", [
