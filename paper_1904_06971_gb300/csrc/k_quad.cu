@@ -356,18 +356,27 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
     const int64_t P3 = (DIM == 3) ? (int64_t)b.R[2] * W : 1;
     const int64_t P2 = (int64_t)b.R[1] * W;
     const int64_t NL = (P2 + LINES - 1) / LINES;       // line groups
-    const int R1 = b.R[0];
+    const int m0 = g.m[0];
+    // With the tensor-core stage X the cardinal rows of the explicit boxes are written there: the
+    // threads then run over the box's other rows only, nlo below the cardinal range and the rest
+    // above it, so that whole warps carry work (the grid keeps its size; the tail exits).
+    int R1 = b.R[0], nlo = R1, hi0 = 0;
+    if (skip_card && has_card && b.out_kind == 0) {
+        const int lo = b.rlo[0], end = b.rlo[0] + b.R[0];
+        nlo = max(0, min(end, 2 * P) - lo);
+        hi0 = max(lo, m0 - 2 * P);
+        R1 = nlo + max(0, end - hi0);
+        if (R1 == 0) return;
+    }
     const int64_t item = (int64_t)(blockIdx.x - b.blk[3]) * kBlock + threadIdx.x;
     if (item >= P3 * NL * R1) return;
     const int i1l = (int)(item % R1);
     const int64_t lg = (item / R1) % NL;
     const int64_t pair3 = item / (R1 * NL);
-    const int i1 = b.rlo[0] + i1l;
+    const int i1 = (i1l < nlo) ? b.rlo[0] + i1l : hi0 + (i1l - nlo);
     const int i3 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
     const int d3 = (DIM == 3) ? (int)(pair3 % W) : 0;
-    const int m0 = g.m[0];
     const bool card = has_card && i1 >= 2 * P && i1 <= m0 - 2 * P - 1;
-    if (skip_card && card && b.out_kind == 0) return;      // written by the tensor-core stage X
     const S* Xi = card ? sX : X0 + (int64_t)i1 * W * TT * 4;
     const int64_t gs = P3 * P2 * G0;        // group stride
     int nl = (int)(P2 - lg * LINES);

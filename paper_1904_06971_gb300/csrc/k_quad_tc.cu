@@ -31,7 +31,7 @@ namespace iga {
 
 namespace {
 
-constexpr int kTcThreads = 256;         // 8 warps: all copy and split, every lane 0 issues MMAs
+constexpr int kTcThreads = 512;         // 16 warps: all copy and split, the lanes 0 of the first ones issue MMAs
 constexpr int kTcLines = 128;           // MMA M: lines per block
 constexpr int kTcN = 16;                // MMA N: offsets delta0 (2p + 1 <= 11 used)
 constexpr int kTcSlices = 3;            // BF16 parts per FP32 value
@@ -46,15 +46,16 @@ struct TcShape {
     static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     static constexpr int KW = (TT + 15) / 16 * 16;           // K rows of one window (zero weights beyond TT)
     static constexpr int KSTEPS = KW / 16;
-    static constexpr int C = (P >= 5) ? 4 : (P == 4 ? 8 : 16);   // rows i0 per chunk
+    static constexpr int C = (P >= 5) ? 4 : 5;               // rows i0 per chunk
     static constexpr int ROWS = (C - 1) * Q + KW;            // Gauss points of a chunk's tile
     static constexpr int A_SLICE = 16 * ROWS * 16;           // bytes of one BF16 part of the A tile (16 line groups)
     static constexpr int A_BUF = kTcSlices * A_SLICE;        // bytes of one BF16 tile
     static constexpr int RAW = kTcLines * ROWS * 4;          // bytes of one raw FP32 tile
-    static constexpr int B_PART = kTcN * KW * 2;             // bytes of one BF16 part of one pattern's B
-    static constexpr int B_BYTES = 4 * kTcSlices * B_PART;
-    static constexpr int SMEM = 2 * A_BUF + 2 * RAW + B_BYTES + 64;
-    static constexpr int TBLOCK = C * kTcN;                  // tensor-memory columns of one chunk
+    static constexpr int NB = kTcSlices * kTcN;              // B rows of one pattern: its three parts side by side
+    static constexpr int B_GROUP = NB * KW * 2;              // bytes of one pattern's B
+    static constexpr int B_BYTES = 4 * B_GROUP;
+    static constexpr int SMEM = 2 * A_BUF + 2 * RAW + B_BYTES + 128;
+    static constexpr int TBLOCK = C * NB;                    // tensor-memory columns of one chunk (three level blocks a row)
     static constexpr int TMEM_COLS = (2 * TBLOCK <= 128) ? 128 : (2 * TBLOCK <= 256 ? 256 : 512);
     static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
     static_assert(2 * TBLOCK <= 512, "chunk does not fit in tensor memory");
@@ -87,9 +88,12 @@ __device__ int g_tc_status = 0;
 // job's Gauss points of their lines asynchronously into a raw FP32 tile (the
 // copy of the next job is in flight while this one is processed), split them
 // into three BF16 parts in an MN-major tile (16 groups of 8 lines, one 16-byte
-// row per Gauss point), and lane 0 of warp w issues, for the rows w, w + 8, ...
-// of the chunk, the MMAs of their windows against the cardinal weights of that pattern (K-major,
-// 16 offset columns) into the chunk's tensor-memory block.  mbarriers tell
+// row per Gauss point), and lane 0 of warp w issues the MMAs of chunk row w:
+// per K step and A part i one MMA against the B parts 0 .. 2 - i of the
+// pattern side by side (K-major, 16 offset columns each, N = 16 (3 - i)), its
+// D starting at the row's level block i, so part j lands in block i + j (the
+// three blocks of a row are added in the epilogue).  One MMA thus reads its A
+// part from shared memory once for all its B parts.  mbarriers tell
 // when a BF16 tile's MMAs are done; after the first job of chunk k has been
 // issued, the rows of chunk k - 1 are read out of the other tensor-memory
 // block and written to the stencil-ELL values.
@@ -102,7 +106,7 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;                                         // [2][part 3][line group 16][ROWS][16 B]
     float* sR = reinterpret_cast<float*>(tc_smem + 2 * Sh::A_BUF);       // [2][line 128][ROWS]
-    unsigned char* sB = tc_smem + 2 * Sh::A_BUF + 2 * Sh::RAW;           // [group 4][part 3][n group 2][K block][128 B]
+    unsigned char* sB = tc_smem + 2 * Sh::A_BUF + 2 * Sh::RAW;           // [group 4][part x 16 + n: 6 groups of 8][K block][128 B]
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + Sh::B_BYTES);      // [0..1] BF16 tile consumed, [2] drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -134,19 +138,21 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     issue_copy(0);
 
     // B: cardinal pair weights of direction 0 in three BF16 parts, one K-major
-    // [16 offsets x KW Gauss points] matrix per pattern (zero beyond 2p+1 and TT)
+    // [3 x 16 offsets x KW Gauss points] matrix per pattern, part j in rows 16 j .. 16 j + 15
+    // (zero beyond 2p+1 and TT)
     const float* Xc = reinterpret_cast<const float*>(T.Xs[0]) + (int64_t)(2 * P) * W * TT * 4;
     for (int idx = tid; idx < 4 * kTcN * KW; idx += kTcThreads) {
         const int gq = idx / (kTcN * KW), n = (idx / KW) % kTcN, k = idx % KW;
         const int pat = 3 - gq;                       // T2 group 0: pattern 11, 1: 10, 2: 01, 3: 00
         const float x = (n < W && k < TT) ? Xc[((int64_t)n * TT + k) * 4 + pat] : 0.f;
-        __nv_bfloat16 x0, x1, x2;
-        split3(x, x0, x1, x2);
-        const int off = ((n >> 3) * (KW / 8) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
-        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(sB + (size_t)gq * kTcSlices * Sh::B_PART);
-        base[off] = x0;
-        base[Sh::B_PART / 2 + off] = x1;
-        base[Sh::B_PART + off] = x2;
+        __nv_bfloat16 xp[3];
+        split3(x, xp[0], xp[1], xp[2]);
+        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(sB + (size_t)gq * Sh::B_GROUP);
+#pragma unroll
+        for (int jd = 0; jd < 3; ++jd) {
+            const int r = jd * kTcN + n;
+            base[((r >> 3) * (KW / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)] = xp[jd];
+        }
     }
     if (tid == 0) {
         // every warp's lane 0 issues MMAs and commits to these barriers
@@ -163,7 +169,7 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     const uint32_t tmem = *tmem_slot;
 
     // this thread's output line (epilogue): warp w reads tensor-memory lanes 32 (w % 4) ..
-    const int q4 = warp & 3, half = warp >> 2;
+    const int q4 = warp & 3, quarter = warp >> 2;
     const int64_t my_line = line0 + q4 * 32 + lane;
     int64_t rowbase = 0;
     int slot0 = 0;
@@ -183,20 +189,21 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
         tc::fence_after_sync();
         const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
         const uint32_t tb = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((k & 1) * Sh::TBLOCK);
-        for (int c = half; c < nc; c += 2) {
-            float v[16];
-            tc::tmem_ld16(tb + (uint32_t)(c * kTcN), v);
+        for (int c = quarter; c < nc; c += kTcThreads / 128) {
+            float v0[16], v1[16], v2[16];
+            tc::tmem_ld16(tb + (uint32_t)(c * Sh::NB), v0);
+            tc::tmem_ld16(tb + (uint32_t)(c * Sh::NB + kTcN), v1);
+            tc::tmem_ld16(tb + (uint32_t)(c * Sh::NB + 2 * kTcN), v2);
             if (my_line < total) {
                 const int64_t row = c0 + c + rowbase;
 #pragma unroll
-                for (int dd = 0; dd < W; ++dd) ell[(int64_t)(slot0 + dd) * N + row] = v[dd];
+                for (int dd = 0; dd < W; ++dd) ell[(int64_t)(slot0 + dd) * N + row] = v0[dd] + (v1[dd] + v2[dd]);
             }
         }
         tc::fence_before_sync();
         return true;
     };
 
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(kTcLines, kTcN, 1, 0);
     const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
     bool ok = true;
     int done_chunks = 0;              // chunks whose rows are written
@@ -236,25 +243,24 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
         }
         tc::fence_async_smem();
         __syncthreads();
-        // MMAs: warp w's lane 0 issues those of the chunk rows c = w, w + 8, ... (every row's chain stays
-        // in one thread, so its accumulation order is fixed); descriptors advance by whole 16-byte rows
+        // MMAs: lane 0 of warp c issues those of chunk row c (a row's chain stays in one thread, so its
+        // accumulation order is fixed); descriptors advance by whole 16-byte rows
         if (lane == 0) {
             tc::fence_after_sync();
             const uint64_t a0 = tc::sdesc(sA_addr + (uint32_t)(buf * Sh::A_BUF), 128, ROWS * 16);
-            const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * kTcSlices * Sh::B_PART), 128, (KW / 8) * 128);
+            const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * Sh::B_GROUP), 128, (KW / 8) * 128);
             const uint32_t d_base = tmem + (uint32_t)((k & 1) * Sh::TBLOCK);
             for (int c = warp; c < nc; c += kTcThreads / 32) {
 #pragma unroll
                 for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
                     const uint64_t arow = (uint64_t)(c * Q + ks * 16);
-                    // partial products a_i b_j of total order i + j <= 2
 #pragma unroll
-                    for (int pr = 0; pr < 6; ++pr) {
-                        const int pi = (pr == 2 || pr == 4) ? 1 : (pr == 5 ? 2 : 0);
-                        const int pj = (pr == 1 || pr == 4) ? 1 : (pr == 3 ? 2 : 0);
-                        const uint64_t ad = a0 + (uint64_t)(pi * Sh::A_SLICE / 16) + arow;
-                        const uint64_t bd = b0 + (uint64_t)((pj * Sh::B_PART + ks * 256) / 16);
-                        tc::mma_bf16(d_base + (uint32_t)(c * kTcN), ad, bd, IDESC, (gq | ks | pr) ? 1u : 0u);
+                    for (int i = 0; i < kTcSlices; ++i) {
+                        // A part i times B parts 0 .. 2 - i: products of order i + j <= 2, part j into level block i + j
+                        const uint32_t idesc = tc::idesc_bf16_f32(kTcLines, kTcN * (kTcSlices - i), 1, 0);
+                        const uint64_t ad = a0 + (uint64_t)(i * Sh::A_SLICE / 16) + arow;
+                        const uint64_t bd = b0 + (uint64_t)(ks * 256 / 16);
+                        tc::mma_bf16(d_base + (uint32_t)(c * Sh::NB + i * kTcN), ad, bd, idesc, (gq | ks | i) ? 1u : 0u);
                     }
                 }
             }
@@ -275,7 +281,7 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
         if (tid == 0) atomicOr(&g_tc_status, 1);
         if (lane == 0) tc::commit(&bars[2]);
         tc::bar_wait(&bars[2], 0u, kTcWaitIter);
-        if (half == 0 && my_line < total)
+        if (quarter == 0 && my_line < total)
             for (int i0 = i0_lo + done_chunks * C; i0 <= i0_hi; ++i0)
                 for (int dd = 0; dd < W; ++dd)
                     ell[(int64_t)(slot0 + dd) * N + rowbase + i0] = __int_as_float(0x7fc00000);
@@ -296,33 +302,36 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
 // weights (FP64) get the same seven digits per offset column.  A product
 // a_i b_j is an integer times 2^-(14+8(i+j)), so the products of one level
 // L = i + j <= 3 summed over the K = 4 (p+1)^2 Gauss points of a row stay below
-// 2^24 quanta: their FP32 accumulation is exact, each level in its own block of
-// tensor memory; levels 4..6 share a fifth block (its FP32 rounding is below
-// 2^-50 of the row's terms).  Levels >= 7 and the digits beyond the seventh
-// are dropped (below 2^-55).  The five blocks are added in double-float, scaled
-// back and rounded once to double.
+// 2^24 quanta: their FP32 accumulation is exact; every level has its own block
+// of tensor memory (the FP32 rounding of levels 4..6 is below 2^-50 of the
+// row's terms).  Levels >= 7 and the digits beyond the seventh are dropped
+// (below 2^-55).  One MMA takes A digit i against B digits 0 .. 6 - i side by
+// side (N = 16 (7 - i)), its D starting at the row's level block i, so digit j
+// lands in block i + j: the A digit is read from shared memory once for all of
+// them.  The seven blocks are added in double-float, scaled back and rounded
+// once to double.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kDigits = 7;              // BF16 digits per value
-constexpr int kAcc = 5;                 // tensor-memory accumulators per row: levels 0, 1, 2, 3, 4..6
+constexpr int kDigits = 7;              // BF16 digits per value (and level blocks of tensor memory per row)
 
 template <int P>
 struct Tc64Shape {
     static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     static constexpr int KW = (TT + 15) / 16 * 16;
     static constexpr int KSTEPS = KW / 16;
-    static constexpr int C = (P >= 5) ? 3 : 6;               // rows i0 per chunk (kAcc * 16 columns each)
+    static constexpr int C = (P >= 5) ? 3 : 4;               // rows i0 per chunk (NB columns of tensor memory each)
     static constexpr int ROWS = (C - 1) * Q + KW;
     static constexpr int A_SLICE = 16 * ROWS * 16;
     static constexpr int A_BUF = kDigits * A_SLICE;          // one BF16 tile (single-buffered)
     static constexpr int RAW = kTcLines * ROWS * 8;          // one raw double-float tile
-    static constexpr int B_PART = kTcN * KW * 2;
-    static constexpr int B_BYTES = 4 * kDigits * B_PART;
+    static constexpr int NB = kDigits * kTcN;                // B rows of one pattern: its seven digits side by side
+    static constexpr int B_GROUP = NB * KW * 2;
+    static constexpr int B_BYTES = 4 * B_GROUP;
     static constexpr int SMALL = kTcLines * 4 * 4 + kTcLines * 4 + kTcN * 4 + 64;   // scales, exponents, barriers
     static constexpr int SMEM = A_BUF + RAW + B_BYTES + SMALL;
     static constexpr int TMEM_COLS = 512;
-    static_assert(C * kAcc * kTcN <= TMEM_COLS, "chunk does not fit in tensor memory");
+    static_assert(C * NB <= TMEM_COLS, "chunk does not fit in tensor memory");
     static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
 };
 
@@ -364,10 +373,9 @@ cudaError_t launch_tc_group_shift(const Geo& g, const Tables& T, int* gshift, cu
 // One block per 128 lines of box b, rows i0 in [i0_lo, i0_hi] (cardinal) in
 // chunks of C rows, four jobs (T2 groups) per chunk as in k_stage_x_tc, with
 // one raw and one digit tile: the copy of job j + 1 runs during the MMAs of
-// job j, the digits of job j + 1 wait for those MMAs.  Lane 0 of warp w issues
-// the MMAs of the chunk rows w, w + 8, ...: for every row, K step and digit
-// pair (i, j) with i + j <= 6, one M = 128, N = 16, K = 16 MMA into the
-// accumulator block of level min(i + j, 4).
+// job j, the digits of job j + 1 wait for those MMAs.  Lane 0 of warp c issues
+// the MMAs of chunk row c: for every K step and A digit i, one M = 128,
+// N = 16 (7 - i), K = 16 MMA (see above).
 template <int P, int DIM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch, double* ell, int64_t N)
@@ -438,13 +446,13 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
         double r = 0.0;
         if (n < W && k < TT && sEb[n] > -100000)
             r = ldexp(Xc[((int64_t)n * TT + k) * 4 + (3 - gq)], -sig[gq] - sEb[n] - 1);
-        const int off = ((n >> 3) * (KW / 8) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
-        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(sB + (size_t)gq * kDigits * Sh::B_PART);
+        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(sB + (size_t)gq * Sh::B_GROUP);
 #pragma unroll
         for (int i = 0; i < kDigits; ++i) {
             const double q = rint(ldexp(r, 7 + 8 * i)) * ldexp(1.0, -7 - 8 * i);
             r -= q;
-            base[i * (Sh::B_PART / 2) + off] = __double2bfloat16(q);
+            const int row = i * kTcN + n;             // digit i of offset n: B row 16 i + n
+            base[((row >> 3) * (KW / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7)] = __double2bfloat16(q);
         }
     }
     if (tid == 0) {
@@ -460,7 +468,7 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     const uint32_t tmem = *tmem_slot;
 
     // the epilogue's output line for this thread (warp w: tensor-memory lanes 32 (w % 4) ..)
-    const int q4 = warp & 3, half = warp >> 2;
+    const int q4 = warp & 3, quarter = warp >> 2;
     const int64_t my_line = line0 + q4 * 32 + lane;
     int64_t rowbase = 0;
     int slot0 = 0;
@@ -474,7 +482,6 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     }
     const int my_el = sEl[q4 * 32 + lane];
 
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(kTcLines, kTcN, 1, 0);
     const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
     bool ok = true;
     int done_chunks = 0;
@@ -521,22 +528,19 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
         if (lane == 0) {
             tc::fence_after_sync();
             const uint64_t a0 = tc::sdesc(sA_addr, 128, ROWS * 16);
-            const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * kDigits * Sh::B_PART), 128, (KW / 8) * 128);
+            const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * Sh::B_GROUP), 128, (KW / 8) * 128);
             for (int c = warp; c < nc; c += kTcThreads / 32) {
 #pragma unroll
                 for (int ks = 0; ks < Sh::KSTEPS; ++ks) {
                     const uint64_t arow = (uint64_t)(c * Q + ks * 16);
 #pragma unroll
-                    for (int i = 0; i < kDigits; ++i)
-#pragma unroll
-                        for (int jd = 0; jd < kDigits - i; ++jd) {
-                            const int lev = (i + jd < kAcc - 1) ? i + jd : kAcc - 1;
-                            const uint64_t ad = a0 + (uint64_t)(i * Sh::A_SLICE / 16) + arow;
-                            const uint64_t bd = b0 + (uint64_t)((jd * Sh::B_PART + ks * 256) / 16);
-                            // the first product into each accumulator block of the row starts it
-                            const bool first = gq == 0 && ks == 0 && i == 0 && (lev < kAcc - 1 || jd == kAcc - 1);
-                            tc::mma_bf16(tmem + (uint32_t)((c * kAcc + lev) * kTcN), ad, bd, IDESC, first ? 0u : 1u);
-                        }
+                    for (int i = 0; i < kDigits; ++i) {
+                        const uint32_t idesc = tc::idesc_bf16_f32(kTcLines, kTcN * (kDigits - i), 1, 0);
+                        const uint64_t ad = a0 + (uint64_t)(i * Sh::A_SLICE / 16) + arow;
+                        const uint64_t bd = b0 + (uint64_t)(ks * 256 / 16);
+                        // the first MMA of the row in the chunk (digit 0, all seven blocks) starts them
+                        tc::mma_bf16(tmem + (uint32_t)(c * Sh::NB + i * kTcN), ad, bd, idesc, (gq | ks | i) ? 1u : 0u);
+                    }
                 }
             }
             tc::commit(&bars[0]);
@@ -546,30 +550,34 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
             ok = __syncthreads_and(tc::bar_wait(&bars[0], (uint32_t)(j & 1), kTcWaitIter)) != 0;
             if (!ok) break;
             tc::fence_after_sync();
-            for (int c = half; c < nc; c += 2) {
-                float v[kAcc][16];
+            for (int c = quarter; c < nc; c += kTcThreads / 128) {
+                // level blocks from the smallest up, each added to the row's double-float sums
+                float sh[W], sl[W];
 #pragma unroll
-                for (int a = 0; a < kAcc; ++a)
-                    tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((c * kAcc + a) * kTcN), v[a]);
+                for (int dd = 0; dd < W; ++dd) { sh[dd] = 0.f; sl[dd] = 0.f; }
+#pragma unroll 1
+                for (int a = kDigits - 1; a >= 0; --a) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(c * Sh::NB + a * kTcN), v);
+#pragma unroll
+                    for (int dd = 0; dd < W; ++dd) {
+                        const float t = __fadd_rn(sh[dd], v[dd]);
+                        const float z = __fsub_rn(t, sh[dd]);
+                        sl[dd] = __fadd_rn(sl[dd], __fadd_rn(__fsub_rn(sh[dd], __fsub_rn(t, z)), __fsub_rn(v[dd], z)));
+                        sh[dd] = t;
+                    }
+                }
                 if (my_line < total) {
                     const int64_t row = c0 + c + rowbase;
 #pragma unroll
                     for (int dd = 0; dd < W; ++dd) {
-                        float sh = v[0][dd], sl = 0.f;
-#pragma unroll
-                        for (int a = 1; a < kAcc; ++a) {
-                            const float t = __fadd_rn(sh, v[a][dd]);
-                            const float z = __fsub_rn(t, sh);
-                            sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(v[a][dd], z)));
-                            sh = t;
-                        }
                         const int e = my_el + sEb[dd] + 1;
                         double out;
                         if (e > -100 && e < 100) {
                             const float f = pow2f(e);
-                            out = df2d_exact(__fmul_rn(sh, f), __fmul_rn(sl, f));
+                            out = df2d_exact(__fmul_rn(sh[dd], f), __fmul_rn(sl[dd], f));
                         } else {
-                            out = ldexp((double)sh + (double)sl, e);
+                            out = ldexp((double)sh[dd] + (double)sl[dd], e);
                         }
                         ell[(int64_t)(slot0 + dd) * N + row] = (sEb[dd] > -100000) ? out : 0.0;
                     }
@@ -585,7 +593,7 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
         if (tid == 0) atomicOr(&g_tc_status, 1);
         if (lane == 0) tc::commit(&bars[1]);
         tc::bar_wait(&bars[1], 0u, kTcWaitIter);
-        if (half == 0 && my_line < total)
+        if (quarter == 0 && my_line < total)
             for (int i0 = i0_lo + done_chunks * C; i0 <= i0_hi; ++i0)
                 for (int dd = 0; dd < W; ++dd)
                     ell[(int64_t)(slot0 + dd) * N + rowbase + i0] = __longlong_as_double(0x7ff8000000000000LL);
