@@ -320,16 +320,15 @@ struct Tc64Shape {
     static constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     static constexpr int KW = (TT + 15) / 16 * 16;
     static constexpr int KSTEPS = KW / 16;
-    static constexpr int C = (P >= 5) ? 3 : 4;               // rows i0 per chunk (NB columns of tensor memory each)
+    static constexpr int C = (P >= 5) ? 1 : 4;               // rows i0 per chunk (NB columns of tensor memory each)
     static constexpr int ROWS = (C - 1) * Q + KW;
     static constexpr int A_SLICE = 16 * ROWS * 16;
-    static constexpr int A_BUF = kDigits * A_SLICE;          // one BF16 tile (single-buffered)
-    static constexpr int RAW = kTcLines * ROWS * 8;          // one raw double-float tile
+    static constexpr int A_BUF = kDigits * A_SLICE;          // one digit tile (two alternate)
     static constexpr int NB = kDigits * kTcN;                // B rows of one pattern: its seven digits side by side
     static constexpr int B_GROUP = NB * KW * 2;
     static constexpr int B_BYTES = 4 * B_GROUP;
     static constexpr int SMALL = kTcLines * 4 * 4 + kTcLines * 4 + kTcN * 4 + 64;   // scales, exponents, barriers
-    static constexpr int SMEM = A_BUF + RAW + B_BYTES + SMALL;
+    static constexpr int SMEM = 2 * A_BUF + B_BYTES + SMALL;
     static constexpr int TMEM_COLS = 512;
     static_assert(C * NB <= TMEM_COLS, "chunk does not fit in tensor memory");
     static_assert(SMEM <= 227 * 1024, "tile does not fit in shared memory");
@@ -371,9 +370,10 @@ cudaError_t launch_tc_group_shift(const Geo& g, const Tables& T, int* gshift, cu
 }
 
 // One block per 128 lines of box b, rows i0 in [i0_lo, i0_hi] (cardinal) in
-// chunks of C rows, four jobs (T2 groups) per chunk as in k_stage_x_tc, with
-// one raw and one digit tile: the copy of job j + 1 runs during the MMAs of
-// job j, the digits of job j + 1 wait for those MMAs.  Lane 0 of warp c issues
+// chunks of C rows, four jobs (T2 groups) per chunk as in k_stage_x_tc.  The
+// digits of a job are computed straight from the T2 values in global memory
+// into one of two digit tiles, so those of job j + 1 are built while the MMAs
+// of job j run (the tile waits only for the MMAs of job j - 1).  Lane 0 of warp c issues
 // the MMAs of chunk row c: for every K step and A digit i, one M = 128,
 // N = 16 (7 - i), K = 16 MMA (see above).
 template <int P, int DIM>
@@ -383,14 +383,13 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     using Sh = Tc64Shape<P>;
     constexpr int Q = Sh::Q, W = Sh::W, TT = Sh::TT, KW = Sh::KW, C = Sh::C, ROWS = Sh::ROWS;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char* sA = tc_smem;                                         // [digit 6][line group 16][ROWS][16 B]
-    float2* sR = reinterpret_cast<float2*>(tc_smem + Sh::A_BUF);         // [line 128][ROWS]
-    unsigned char* sB = tc_smem + Sh::A_BUF + Sh::RAW;                   // [group 4][digit 6][n group 2][K block][128 B]
+    unsigned char* sA = tc_smem;                                         // [tile 2][digit 7][line group 16][ROWS][16 B]
+    unsigned char* sB = tc_smem + 2 * Sh::A_BUF;                         // [group 4][digit x 16 + n: 14 groups of 8][K block][128 B]
     float* sScale = reinterpret_cast<float*>(sB + Sh::B_BYTES);          // [group 4][line 128]
     int* sEl = reinterpret_cast<int*>(sScale + 4 * kTcLines);            // [line 128] exponent of the line scale
     int* sEb = sEl + kTcLines;                                           // [16] exponent of the column scale
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sEb + kTcN);            // [0] digit tile consumed, [1] drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sEb + kTcN);            // [0..1] digit tile consumed, [2] drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int64_t G0 = (int64_t)b.E[0] * Q;
@@ -403,20 +402,6 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     const int* ex = reinterpret_cast<const int*>(scratch + b.ex_off);
     const int nchunks = (i0_hi - i0_lo) / C + 1;
     const int jobs = 4 * nchunks;
-
-    auto issue_copy = [&](int j) {
-        const int c0 = i0_lo + (j >> 2) * C, gq = j & 3;
-        const int64_t row0 = (int64_t)(c0 - P - b.elo[0]) * Q;
-        const float2* src = T2 + (int64_t)gq * gs;
-        for (int idx = tid; idx < kTcLines * ROWS; idx += kTcThreads) {
-            const int l = idx / ROWS, r = idx - l * ROWS;
-            const int64_t line = line0 + l, gp = row0 + r;
-            const bool valid = line < total && gp < G0;
-            tc::cp_async8(sR + idx, valid ? src + line * G0 + gp : T2, valid);
-        }
-        tc::cp_async_commit();
-    };
-    issue_copy(0);
 
     // line scales: alpha = v 2^(sigma_g - e_line - 1), e_line the recorded largest shifted exponent
     int sig[4];
@@ -458,6 +443,7 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     if (tid == 0) {
         tc::bar_init(&bars[0], kTcThreads / 32);
         tc::bar_init(&bars[1], kTcThreads / 32);
+        tc::bar_init(&bars[2], kTcThreads / 32);
         tc::fence_bar_init();
     }
     if (warp == 0) tc::tmem_alloc(tmem_slot, Sh::TMEM_COLS);
@@ -486,16 +472,25 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     bool ok = true;
     int done_chunks = 0;
     for (int j = 0; j < jobs; ++j) {
-        const int k = j >> 2, gq = j & 3;
+        const int k = j >> 2, gq = j & 3, buf = j & 1;
         const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
-        tc::cp_async_wait<0>();
-        // the digit tile was last read by the MMAs of job j - 1
-        const bool wok = (j >= 1) ? tc::bar_wait(&bars[0], (uint32_t)((j - 1) & 1), kTcWaitIter) : true;
+        // digit tile buf was last read by the MMAs of job j - 2
+        const bool wok = (j >= 2) ? tc::bar_wait(&bars[buf], (uint32_t)(((j >> 1) - 1) & 1), kTcWaitIter) : true;
         ok = __syncthreads_and(wok) != 0;
         if (!ok) break;
-        // digits of the raw tile, 8 lines x 1 Gauss point per item
+        // digits of the job's T2 values (zero beyond the box), 8 lines x 1 Gauss point per item
+        const int64_t row0 = (int64_t)(c0 - P - b.elo[0]) * Q;
+        const float2* src = T2 + (int64_t)gq * gs;
+        unsigned char* tile = sA + (size_t)buf * Sh::A_BUF;
         for (int item = tid; item < 16 * ROWS; item += kTcThreads) {
             const int lg = item / ROWS, r = item - lg * ROWS;
+            const int64_t gp = row0 + r;
+            float2 vv[8];
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const int64_t line = line0 + lg * 8 + l;
+                vv[l] = (line < total && gp < G0) ? src[line * G0 + gp] : make_float2(0.f, 0.f);
+            }
             uint32_t w[kDigits][4];
 #pragma unroll
             for (int l = 0; l < 8; l += 2) {
@@ -503,7 +498,7 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int line = lg * 8 + l + u;
-                    const float2 v = sR[(size_t)line * ROWS + r];
+                    const float2 v = vv[l + u];
                     const float sc = sScale[gq * kTcLines + line];
                     float rh = __fmul_rn(v.x, sc), rl = __fmul_rn(v.y, sc);
 #pragma unroll
@@ -520,14 +515,13 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
             const size_t off = ((size_t)lg * ROWS + r) * 16;
 #pragma unroll
             for (int i = 0; i < kDigits; ++i)
-                *reinterpret_cast<uint4*>(sA + (size_t)i * Sh::A_SLICE + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+                *reinterpret_cast<uint4*>(tile + (size_t)i * Sh::A_SLICE + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
         }
         tc::fence_async_smem();
-        __syncthreads();                              // raw tile free, digit tile complete
-        if (j + 1 < jobs) issue_copy(j + 1);
+        __syncthreads();                              // digit tile complete
         if (lane == 0) {
             tc::fence_after_sync();
-            const uint64_t a0 = tc::sdesc(sA_addr, 128, ROWS * 16);
+            const uint64_t a0 = tc::sdesc(sA_addr + (uint32_t)(buf * Sh::A_BUF), 128, ROWS * 16);
             const uint64_t b0 = tc::sdesc(sB_addr + (uint32_t)(gq * Sh::B_GROUP), 128, (KW / 8) * 128);
             for (int c = warp; c < nc; c += kTcThreads / 32) {
 #pragma unroll
@@ -543,11 +537,12 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
                     }
                 }
             }
-            tc::commit(&bars[0]);
+            tc::commit(&bars[buf]);
         }
         if (gq == 3) {
-            // rows of the chunk: the level blocks added in double-float, scaled back, rounded to double
-            ok = __syncthreads_and(tc::bar_wait(&bars[0], (uint32_t)(j & 1), kTcWaitIter)) != 0;
+            // rows of the chunk (once the MMAs of this job, and so of all the chunk's jobs, are done): the
+            // level blocks added in double-float, scaled back, rounded to double
+            ok = __syncthreads_and(tc::bar_wait(&bars[buf], (uint32_t)((j >> 1) & 1), kTcWaitIter)) != 0;
             if (!ok) break;
             tc::fence_after_sync();
             for (int c = quarter; c < nc; c += kTcThreads / 128) {
@@ -591,8 +586,8 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
     if (!ok) {
         tc::cp_async_wait<0>();
         if (tid == 0) atomicOr(&g_tc_status, 1);
-        if (lane == 0) tc::commit(&bars[1]);
-        tc::bar_wait(&bars[1], 0u, kTcWaitIter);
+        if (lane == 0) tc::commit(&bars[2]);
+        tc::bar_wait(&bars[2], 0u, kTcWaitIter);
         if (quarter == 0 && my_line < total)
             for (int i0 = i0_lo + done_chunks * C; i0 <= i0_hi; ++i0)
                 for (int dd = 0; dd < W; ++dd)
