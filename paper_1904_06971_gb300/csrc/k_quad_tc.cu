@@ -184,7 +184,8 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
     // rows of chunk k out of tensor-memory block k & 1, once its last job's MMAs are done
     auto epilogue = [&](int k) -> bool {
         const int last = 4 * k + 3;
-        const bool ok = __syncthreads_and(tc::bar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), kTcWaitIter)) != 0;
+        const bool ok = __syncthreads_and(warp == 0 ? tc::bar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1), kTcWaitIter)
+                                                    : true) != 0;
         if (!ok) return false;
         tc::fence_after_sync();
         const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
@@ -218,7 +219,8 @@ k_stage_x_tc(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scratch
             tc::cp_async_wait<0>();
         }
         // BF16 tile buf was last read by the MMAs of job j - 2
-        const bool wok = (j >= 2) ? tc::bar_wait(&bars[buf], (uint32_t)(((j >> 1) - 1) & 1), kTcWaitIter) : true;
+        // (one warp polls the mbarrier; the others wait at the block barrier without taking issue slots)
+        const bool wok = (j >= 2 && warp == 0) ? tc::bar_wait(&bars[buf], (uint32_t)(((j >> 1) - 1) & 1), kTcWaitIter) : true;
         ok = __syncthreads_and(wok) != 0;            // also makes every thread's copies of job j visible
         if (!ok) break;
         const float* raw = sR + (size_t)buf * (kTcLines * ROWS);
@@ -475,7 +477,8 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
         const int k = j >> 2, gq = j & 3, buf = j & 1;
         const int c0 = i0_lo + k * C, nc = min(C, i0_hi - c0 + 1);
         // digit tile buf was last read by the MMAs of job j - 2
-        const bool wok = (j >= 2) ? tc::bar_wait(&bars[buf], (uint32_t)(((j >> 1) - 1) & 1), kTcWaitIter) : true;
+        // (one warp polls the mbarrier; the others wait at the block barrier without taking issue slots)
+        const bool wok = (j >= 2 && warp == 0) ? tc::bar_wait(&bars[buf], (uint32_t)(((j >> 1) - 1) & 1), kTcWaitIter) : true;
         ok = __syncthreads_and(wok) != 0;
         if (!ok) break;
         // digits of the job's T2 values (zero beyond the box), 8 lines x 1 Gauss point per item
@@ -542,7 +545,7 @@ k_stage_x_tc64(Geo g, Tables T, Box b, int i0_lo, int i0_hi, const double* scrat
         if (gq == 3) {
             // rows of the chunk (once the MMAs of this job, and so of all the chunk's jobs, are done): the
             // level blocks added in double-float, scaled back, rounded to double
-            ok = __syncthreads_and(tc::bar_wait(&bars[buf], (uint32_t)((j >> 1) & 1), kTcWaitIter)) != 0;
+            ok = __syncthreads_and(warp == 0 ? tc::bar_wait(&bars[buf], (uint32_t)((j >> 1) & 1), kTcWaitIter) : true) != 0;
             if (!ok) break;
             tc::fence_after_sync();
             for (int c = quarter; c < nc; c += kTcThreads / 128) {
