@@ -209,7 +209,10 @@ struct PolDF {
         a.h = s;
         a.l = __fadd_rn(a.l, __fadd_rn(t, pe));
     }
-    __device__ __forceinline__ static double to_double(const acc& a) { return df2d_exact(a.h, a.l); }
+    // the double nearest to hi + lo (bit for bit df2d_exact): two exact conversions and one FP64 add;
+    // the quadrature stages convert one value per ~10^2 multiply-adds, where the add is free and the
+    // integer-only df2d_exact costs more issue slots (kernels bound by the FP64 pipe call df2d_exact)
+    __device__ __forceinline__ static double to_double(const acc& a) { return f2d_exact(a.h) + f2d_exact(a.l); }
     // the float nearest to hi + lo: one rounding of the exact sum
     __device__ __forceinline__ static float to_float(const acc& a) { return __fadd_rn(a.h, a.l); }
     __device__ __forceinline__ static store to_store(const acc& a)

@@ -292,7 +292,7 @@ cudaError_t launch_spline(const Geo& g, const SplinePlan& sp, double* samples,
 // (about 48 significand bits); the diagonal sums are FP64.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T from_df(const DFAcc& a) { return PolDF::to_double(a); }
+__device__ __forceinline__ T from_df(const DFAcc& a) { return df2d_exact(a.h, a.l); }
 template <>
 __device__ __forceinline__ float from_df<float>(const DFAcc& a) { return __fadd_rn(a.h, a.l); }
 

@@ -80,6 +80,33 @@ def test_exact_full_matrix(iga, prob, arith):
     assert rel(gpu_exact(iga, prob), ref) <= TOL64
 
 
+# Entry error of the FP64-value contractions by degree.  Besides the global
+# measure (relative to the largest entry), every stencil slot s is held to its
+# own scale, max_i |X_si - ref_si| / max_i |ref_si|: the far-corner slots are
+# ~1e-3 of the diagonal, so a global 1e-12 alone would let them carry ~1e-9
+# relative errors.  Bounds: native FP64 reaches ~1e-14 (1e-3-term diagonal sums),
+# double-float products carry ~2^-48 ~ 3.6e-15 per operation and reach a few 1e-13.
+ENTRY_BOUND = {"fp64": 5e-14, "df64": 5e-13}
+SLOT_BOUND = {"fp64": 1e-11, "df64": 1e-10}
+
+
+@pytest.mark.parametrize("arith", ["df64", "fp64"], indirect=True)
+@pytest.mark.parametrize("prob", [SMALL_EXACT[i] for i in (1, 2, 3, 4, 5, 6, 7)],
+                         ids=lambda q: f"{q.dim}d_p{q.p}_{'x'.join(map(str, q.n_el))}")
+def test_entry_error_by_degree(iga, prob, arith):
+    use(iga, "f64", arith)
+    ref = oracle.exact_matrix(prob)
+    got = gpu_exact(iga, prob)
+    glob = rel(got, ref)
+    scale = np.max(np.abs(ref), axis=1)
+    err = np.max(np.abs(got - ref), axis=1)
+    live = scale > 0
+    per_slot = float(np.max(err[live] / scale[live]))
+    print(f"p={prob.p} dim={prob.dim} {arith}: global {glob:.2e}, worst slot {per_slot:.2e}")
+    assert glob <= ENTRY_BOUND[arith]
+    assert per_slot <= SLOT_BOUND[arith]
+
+
 @pytest.mark.parametrize("arith", ["fp32", "df64", "fp64"], indirect=True)
 @pytest.mark.parametrize("idx", [3, 6, 7])
 def test_exact_f32(iga, idx, arith):
