@@ -495,22 +495,42 @@ def batch_report(iga, torch, steps: int, warmup: int):
         return a.elapsed_time(b) / steps, (iga.launch_count() - l0) // steps
 
     ms_eager, k_eager = timed(eager)
-    t0 = time.perf_counter()
-    iga.assemble_batch(items, dtype="f32", out=mats)          # capture + autotune
-    torch.cuda.synchronize()
-    t_tune = time.perf_counter() - t0
-    branches, kernels, _, tuned_ms = iga.batch_info()
-    ms_graph, k_graph = timed(lambda: iga.assemble_batch(items, dtype="f32", out=mats))
+
+    def tuned(branches_ok, persistent_ok):
+        # a fresh autotune restricted to the given candidate kinds, then timed cached replays
+        iga.batch_release()
+        iga.batch_set_modes(branches_ok, persistent_ok)
+        t0 = time.perf_counter()
+        iga.assemble_batch(items, dtype="f32", out=mats)      # capture + autotune
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t0
+        branches, kernels, _, tuned_ms = iga.batch_info()
+        persistent, bps, chunk = iga.batch_mode()
+        ms, _ = timed(lambda: iga.assemble_batch(items, dtype="f32", out=mats))
+        iga.batch_status()
+        out = {"value": nnz / (ms * 1e-3), "ms_per_batch": ms, "kind": "persistent" if persistent else "branches",
+               "branches": branches, "kernels_per_launch": kernels, "graph_launches_per_batch": 1,
+               "capture_and_tune_s": t_tune, "tuned_replay_ms": tuned_ms}
+        if persistent:
+            out.update({"blocks_per_sm": bps, "items_per_claim": chunk})
+        return out
+
+    try:
+        best = tuned(True, True)
+        only_persistent = tuned(False, True)
+        only_branches = tuned(True, False)
+    finally:
+        iga.batch_set_modes(True, True)
+        iga.batch_release()
     for A in mats:
         A.destroy()
     return {"workload": "256 patches: 192 2-D (p 2..5, 16..256 el/dir) + 64 3-D (p 2..4, 8..48 el/dir), M in {4,8}, "
                         "q 3, FP32 values, seed 0",
             "patches": len(items), "nnz": nnz, "unit": "nnz/s",
-            "graph": {"value": nnz / (ms_graph * 1e-3), "ms_per_batch": ms_graph, "branches": branches,
-                      "kernels_per_launch": kernels, "graph_launches_per_batch": 1},
+            "graph": best, "persistent_only": only_persistent, "branches_only": only_branches,
             "eager_one_stream": {"value": nnz / (ms_eager * 1e-3), "ms_per_batch": ms_eager,
                                  "kernel_launches_per_batch": k_eager},
-            "create_s": t_create, "capture_and_tune_s": t_tune, "tuned_replay_ms": tuned_ms}
+            "create_s": t_create}
 
 
 def _time_steps(torch, step, steps: int, warmup: int, stream, profile_iga=None):

@@ -52,7 +52,7 @@ extern "C" {
 #define IGA_ENOMEM       (-2)   /* device allocation failed */
 #define IGA_ECUDA        (-3)   /* a CUDA runtime call or launch failed */
 #define IGA_EUNSUPPORTED (-4)   /* valid request outside what is built (p, n, q range) */
-#define IGA_ETIMEOUT     (-5)   /* reserved for a bounded device wait that gave up; no call waits on the device today */
+#define IGA_ETIMEOUT     (-5)   /* a bounded device wait gave up (persistent batch kernel); the context stays usable */
 
 /* storage type of matrix values and of the SpMV vectors */
 #define IGA_F64 0
@@ -262,20 +262,34 @@ int iga_kappa_gradient(const iga_patch_t* patch, int p, const iga_map_t* map, co
                        int M, int q, const double* ybar, const double* x, double* grad, void* stream);
 
 /*
- * Batched assembly (no counterpart in the paper, which assembles one patch):
- * many patches of uneven size, degree, map and coefficient as one CUDA graph.
- * Item k is assembled like iga_assemble_surrogate_domains (M >= 1) or
- * iga_assemble_exact (M = 0) into A[k].
+ * Batched assembly (no counterpart in the paper, which assembles one patch;
+ * per patch it is the method of Sec. 6 -- quadrature of the exact rows and
+ * sample rows, interpolation, fill): many patches of uneven size, degree, map
+ * and coefficient as one CUDA graph.  Item k is assembled like
+ * iga_assemble_surrogate_domains (M >= 1) or iga_assemble_exact (M = 0) into A[k].
  *   First call with any A[k] == NULL: every matrix is created by an eager
  *   assembly on `stream` (handles returned in A).  Calls with all handles set:
  *   the batch (descriptions, handles, dtype and contraction arithmetic) is
- *   looked up in a graph cache; on a miss the kernel chains of all patches are
- *   captured on B concurrent branches (B = 1, 2, 4, ..., 32 tried, the fastest of
- *   two timed replays kept -- this first graph call synchronises), on a hit the
- *   cached graph is launched on `stream` as one graph launch.  Device pointers in
- *   the descriptions (IGA_KAPPA_BSPLINE3 control values) are captured by address.
+ *   looked up in a graph cache; on a miss an autotuner captures candidate graphs
+ *   and keeps the fastest of two timed replays (this first graph call
+ *   synchronises); on a hit the cached graph is launched on `stream` as one
+ *   graph launch.  Candidates (iga_batch_set_modes restricts them):
+ *     branches: every patch's kernel chain on B concurrent branches, B = 1, 2,
+ *       4, ..., 32;
+ *     persistent: the quadrature stages of all patches of one (dimension,
+ *       degree, arithmetic) as ONE persistent kernel over device-side patch
+ *       descriptors -- work items are the stage blocks, claimed from a device
+ *       counter; an item waits for the previous stage of its patch on a
+ *       completion counter, each wait bounded (2 s of the GPU's global timer);
+ *       tuned over resident blocks per SM and items per claim.  Not used with
+ *       the tensor-core stage X modes.  Its scratch is one device allocation
+ *       owned by the cached graph (freed by iga_batch_release or when a matrix
+ *       of the batch is destroyed).
+ *   Device pointers in the descriptions (IGA_KAPPA_BSPLINE3 control values) are
+ *   captured by address.
  *   Errors: IGA_EINVAL for n < 1, null arrays or a bad dtype; item errors as for
- *   the single-patch calls.
+ *   the single-patch calls; IGA_ETIMEOUT when a persistent wait gave up during
+ *   tuning (replays report it through iga_batch_status).
  */
 typedef struct {
     iga_patch_t patch;
@@ -297,6 +311,24 @@ int iga_batch_info(int* branches, int64_t* kernels, int* cached, float* tuned_ms
 /* Destroys every cached batch graph (iga_matrix_destroy already drops the graphs
  * that write into the destroyed matrix). */
 int iga_batch_release(void);
+
+/* Restricts the batch autotuner's candidates (process-wide; both allowed by
+ * default; at least one must be).  Affects graphs tuned after the call. */
+int iga_batch_set_modes(int allow_branches, int allow_persistent);
+
+/* The calling thread's last iga_assemble_batch: 1 if its graph is the
+ * persistent kind, with the tuned resident blocks per SM and items per claim. */
+int iga_batch_mode(int* persistent, int* blocks_per_sm, int* chunk);
+
+/* Synchronises `stream` and returns IGA_ETIMEOUT if a wait of the calling
+ * thread's last persistent batch replay gave up, else IGA_OK. */
+int iga_batch_status(void* stream);
+
+/* Self-test of the bounded wait: launches the persistent kernel on one work
+ * item whose dependency nothing ever completes; the wait must give up after
+ * limit_us microseconds (1..1e7) and the call returns IGA_ETIMEOUT with the
+ * device still usable (IGA_OK would mean the wait did not run out). */
+int iga_batch_selftest_timeout(long long limit_us, void* stream);
 
 /*
  * y = A x (eq. DiscreteVariationalProblems), stencil SpMV.  x and y are

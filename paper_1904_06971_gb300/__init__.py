@@ -24,7 +24,8 @@ from . import _build
 
 __all__ = ["IgaError", "Matrix", "assemble_exact", "assemble_surrogate", "assemble_mass", "assemble_mass_surrogate",
            "surrogate_plan", "manufactured_load",
-           "kappa_gradient", "stiffness_apply", "assemble_batch", "batch_info", "load", "launch_count",
+           "kappa_gradient", "stiffness_apply", "assemble_batch", "batch_info", "batch_set_modes", "batch_mode", "batch_release",
+           "batch_status", "batch_selftest_timeout", "load", "launch_count",
            "profile_enable", "profile_read", "kernel_names", "set_arithmetic", "get_arithmetic",
            "F64", "F32", "ARITH"]
 
@@ -94,6 +95,11 @@ def load():
                                          ctypes.POINTER(H)]
         L.iga_batch_info.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_float)]
+        L.iga_batch_release.argtypes = []
+        L.iga_batch_set_modes.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.iga_batch_mode.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3
+        L.iga_batch_status.argtypes = [vp]
+        L.iga_batch_selftest_timeout.argtypes = [ctypes.c_longlong, vp]
         L.iga_assemble_exact_noalloc.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
                                                  ctypes.POINTER(Kappa), ctypes.c_int, vp, vp]
         L.iga_manufactured_load.argtypes = [ctypes.POINTER(Patch), ctypes.c_int, ctypes.POINTER(Map),
@@ -479,6 +485,34 @@ def assemble_batch(items, dtype="f32", stream=None, out=None):
     for m, kp in zip(mats, keep):
         _keep(m, kp)
     return mats
+
+
+def batch_release():
+    """Destroy every cached batch graph (the next batch call re-tunes)."""
+    _check(load().iga_batch_release())
+
+
+def batch_set_modes(branches=True, persistent=True):
+    """Restrict the batch autotuner to branch graphs and/or persistent-kernel graphs."""
+    _check(load().iga_batch_set_modes(int(bool(branches)), int(bool(persistent))))
+
+
+def batch_mode():
+    """(persistent, resident blocks per SM, items per claim) of this thread's last batch call."""
+    p, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().iga_batch_mode(ctypes.byref(p), ctypes.byref(b), ctypes.byref(c)))
+    return bool(p.value), b.value, c.value
+
+
+def batch_status(stream=None):
+    """Synchronise the stream; raise IgaError(IGA_ETIMEOUT) if the last persistent replay's wait gave up."""
+    _check(load().iga_batch_status(ctypes.c_void_p(_stream_ptr(stream))))
+
+
+def batch_selftest_timeout(limit_us=20000, stream=None) -> int:
+    """Run the persistent kernel on a work item whose dependency never completes; returns the status code
+    (IGA_ETIMEOUT = -5 when the bounded wait gave up as it should)."""
+    return int(load().iga_batch_selftest_timeout(int(limit_us), ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def batch_info():

@@ -62,7 +62,7 @@ thread_local bool t_capture = false;        // inside a graph capture: no profil
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
                              "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg",
                              "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter", "stage_x_tc",
-                             "manufactured"};
+                             "manufactured", "persist"};
 
 cudaEvent_t take_event()
 {
@@ -312,18 +312,49 @@ void spline_bufs(double* scratch, const SplinePlan& sp, const SplineLayout& o, S
         }
 }
 
-int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
-             int M, int q, int domains, int dtype, void* stream_v, iga_matrix_t* out, int form = kFormStiffness)
-{
-    t_err.clear();
+}  // namespace
+
+// One assembly split into its phases, so that a batch can run the quadrature
+// stages of many patches as one persistent launch: plan (argument checks,
+// boxes, sampling lattice, scratch layout, matrix storage), bind (scratch
+// pointers), pre (tables, coefficient field), quad (sum-factorised stages),
+// post (interpolation and fill).
+struct iga::Job {
     Geo g;
+    BoxSet bs;
+    SplinePlan sp;
+    SplineLayout slo;
+    Layout lay;
+    int empty = 0, dtype = 0, form = 0, arith = 0, tc64 = 0;
+    bool do_spline = false, surrogate = false, created = false;
+    int64_t nblk[4] = {0, 0, 0, 0};
+    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3], o_Xs[3], o_tdf[3];
+    int64_t o_gshift = -1, o_ex_lo = -1, o_ex_hi = -1, o_samples = 0, o_partial = 0, o_mid = 0;
+    iga_matrix* A = nullptr;
+    double* scratch = nullptr;
+    double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
+    void* Xs[3];
+    float2* tdf[3];
+    Tables T;
+    SplineBufs sb;
+    double* samples = nullptr;
+};
+
+namespace {
+
+int job_plan(Job& J, const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
+             int M, int q, int domains, int dtype, int form, iga_matrix* existing)
+{
+    Geo& g = J.g;
     int rc = check_geometry(patch, p, map, kappa, g);
     if (rc) return rc;
     g.form = form;
+    J.form = form;
+    J.dtype = dtype;
+    J.surrogate = surrogate;
     if (form == kFormMass && domains != IGA_DOMAINS_COMMON)
         return fail(IGA_EUNSUPPORTED, "the mass surrogate uses the common domain Omega~");
     if (dtype != IGA_F64 && dtype != IGA_F32) return fail(IGA_EINVAL, "dtype must be IGA_F64 or IGA_F32");
-    if (!out) return fail(IGA_EINVAL, "output handle pointer is null");
     if (surrogate) {
         if (M < 1) return fail(IGA_EINVAL, "sampling parameter M must be >= 1 (got %d)", M);
         if (q < 0 || q > kMaxQ) return fail(IGA_EUNSUPPORTED, "interpolation degree q must be in 0..%d (got %d)", kMaxQ, q);
@@ -338,12 +369,11 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         nnz *= (int64_t)g.m[d] * W - (int64_t)p * (p + 1);
     }
     const size_t esz = (dtype == IGA_F32) ? 4 : 8;
-    cudaStream_t st = (cudaStream_t)stream_v;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
 
-    iga_matrix* A = *out;
+    iga_matrix* A = existing;
     if (A) {
         bool same = A->dim == dim && A->p == p && A->dtype == dtype && A->device == dev;
         for (int d = 0; d < dim; ++d) same = same && A->n_el[d] == g.n_el[d];
@@ -351,22 +381,20 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     }
 
     // ---------------- plan: boxes and sampling lattice ----------------
-    BoxSet bs;
+    BoxSet& bs = J.bs;
     memset(&bs, 0, sizeof(bs));
-    SplinePlan sp;
+    SplinePlan& sp = J.sp;
     memset(&sp, 0, sizeof(sp));
-    int empty = 0;
-    bool do_spline = false;
     std::vector<Box> boxes;
     if (surrogate) {
         const int k0 = (domains == IGA_DOMAINS_PER_OFFSET) ? p : 2 * p;
         int k1[3] = {0, 0, 0};
-        rc = plan_spline(g, p, M, q, domains, sp, empty, k1);
+        rc = plan_spline(g, p, M, q, domains, sp, J.empty, k1);
         if (rc) return rc;
-        if (!empty) {
+        if (!J.empty) {
             for (int d = 0; d < 3; ++d) bs.ax[d] = sp.ax[d];
             bs.n_samples = sp.n_samples;
-            do_spline = true;
+            J.do_spline = true;
             // frame = rows with an index outside [k0, k1], as disjoint slabs
             Box b;
             if (dim == 3) {
@@ -393,7 +421,7 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
             }
         }
     }
-    if (!surrogate || empty) {
+    if (!surrogate || J.empty) {
         Box b;
         int lo[3] = {0, 0, 0}, R[3] = {g.m[0], g.m[1], g.m[2]};
         make_box(g, b, lo, R);
@@ -402,24 +430,24 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
     if ((int)boxes.size() > kMaxBoxes) return fail(IGA_EINVAL, "internal: too many boxes");
 
     // ---------------- scratch layout ----------------
-    Layout lay;
+    Layout& lay = J.lay;
     const int arith = current_arith(dtype);
-    int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3], o_Xs[3], o_tdf[3];
+    J.arith = arith;
     for (int d = 0; d < 3; ++d) {
         const int64_t G = (d < dim) ? (int64_t)g.n_el[d] * Q : 1;
         const int64_t nX = (d < dim) ? (int64_t)4 * g.m[d] * W * TT : 1;
-        o_gx[d] = lay.take(G); o_sx[d] = lay.take(2 * G); o_cx[d] = lay.take(2 * G); o_wq[d] = lay.take(G);
-        o_bv[d] = lay.take(G * Q); o_bd[d] = lay.take(G * Q); o_X[d] = lay.take(nX);
-        o_Xs[d] = (arith == kArithF64) ? o_X[d] : lay.take(nX);
-        o_tdf[d] = lay.take(4 * G);
+        J.o_gx[d] = lay.take(G); J.o_sx[d] = lay.take(2 * G); J.o_cx[d] = lay.take(2 * G); J.o_wq[d] = lay.take(G);
+        J.o_bv[d] = lay.take(G * Q); J.o_bd[d] = lay.take(G * Q); J.o_X[d] = lay.take(nX);
+        J.o_Xs[d] = (arith == kArithF64) ? J.o_X[d] : lay.take(nX);
+        J.o_tdf[d] = lay.take(4 * G);
     }
     prepare_coef_df(g, arith);
-    int64_t nblk[4] = {0, 0, 0, 0};
+    int64_t* nblk = J.nblk;
     bs.nb = (int)boxes.size();
     // FP64 values with tensor-core stage X: per-line T2 exponents of every box and the group shifts
     const int tc64 = (form == kFormStiffness && dtype == IGA_F64) ? current_tc(dtype) : 0;
-    int64_t o_gshift = -1, o_ex_lo = -1, o_ex_hi = -1;
-    if (tc64) o_gshift = lay.take(2);
+    J.tc64 = tc64;
+    if (tc64) J.o_gshift = lay.take(2);
     for (int k = 0; k < bs.nb; ++k) {
         Box& b = boxes[k];
         b.out_kind = 0;
@@ -427,21 +455,19 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         if (tc64) {
             const int64_t lines = (dim == 3 ? (int64_t)b.R[2] * W : 1) * (int64_t)b.R[1] * W;
             b.ex_off = lay.take((lines + 1) / 2);
-            if (o_ex_lo < 0) o_ex_lo = b.ex_off;
-            o_ex_hi = lay.total;
+            if (J.o_ex_lo < 0) J.o_ex_lo = b.ex_off;
+            J.o_ex_hi = lay.total;
         }
         b.c_off = lay.take(box_coef_len(dim, p, b));
         b.t1_off = lay.take(box_t1_len(dim, p, b));
         b.t2_off = lay.take(box_t2_len(dim, p, b));
-        for (int s = 0; s < 4; ++s) {
-            b.blk[s] = nblk[s];
-            nblk[s] += div_up(box_items(dim, p, b, s), kBlock);
+        for (int st = 0; st < 4; ++st) {
+            b.blk[st] = nblk[st];
+            nblk[st] += div_up(box_items(dim, p, b, st), kBlock);
         }
         bs.box[k] = b;
     }
-    int64_t o_samples = 0, o_partial = 0, o_mid = 0;
-    SplineLayout slo;
-    if (do_spline) {
+    if (J.do_spline) {
         Box sbx;                         // shape of every sample box: one row, p + 1 elements per direction
         memset(&sbx, 0, sizeof(sbx));
         for (int d = 0; d < 3; ++d) { sbx.R[d] = 1; sbx.E[d] = (d < dim) ? p + 1 : 1; }
@@ -451,22 +477,21 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         bs.s_c_off = lay.take(bs.s_c_len * sp.n_samples);
         bs.s_t1_off = lay.take(bs.s_t1_len * sp.n_samples);
         bs.s_t2_off = lay.take(bs.s_t2_len * sp.n_samples);
-        for (int s = 0; s < 4; ++s) {
-            bs.blk_s[s] = nblk[s];
-            bs.bper_s[s] = div_up(box_items(dim, p, sbx, s), kBlock);
-            nblk[s] += bs.bper_s[s] * sp.n_samples;
+        for (int st = 0; st < 4; ++st) {
+            bs.blk_s[st] = nblk[st];
+            bs.bper_s[st] = div_up(box_items(dim, p, sbx, st), kBlock);
+            nblk[st] += bs.bper_s[st] * sp.n_samples;
         }
-        o_samples = lay.take((int64_t)S * sp.n_samples);
-        spline_layout(lay, sp, slo);
+        J.o_samples = lay.take((int64_t)S * sp.n_samples);
+        spline_layout(lay, sp, J.slo);
         const int64_t S_up = S - sp.first;
-        o_mid = lay.take(dim == 3 ? S_up * sp.Lmax[2] * (int64_t)sp.nu[1] * sp.nu[0] : 1);
-        o_partial = lay.take(S_up * (dim == 3 ? sp.Lmax[2] : 1) * (int64_t)sp.Lmax[1] * sp.nu[0]);
+        J.o_mid = lay.take(dim == 3 ? S_up * sp.Lmax[2] * (int64_t)sp.nu[1] * sp.nu[0] : 1);
+        J.o_partial = lay.take(S_up * (dim == 3 ? sp.Lmax[2] : 1) * (int64_t)sp.Lmax[1] * sp.nu[0]);
     }
-    for (int s = 0; s < 4; ++s)
-        if (nblk[s] > 0x7fffffffLL) return fail(IGA_EUNSUPPORTED, "problem too large for one launch");
+    for (int st = 0; st < 4; ++st)
+        if (nblk[st] > 0x7fffffffLL) return fail(IGA_EUNSUPPORTED, "problem too large for one launch");
 
     // ---------------- storage ----------------
-    bool created = false;
     if (!A) {
         A = new (std::nothrow) iga_matrix;
         if (!A) return fail(IGA_ENOMEM, "host allocation failed");
@@ -477,75 +502,119 @@ int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_ka
         A->bytes = (size_t)S * (size_t)N * esz;
         ce = cudaMalloc(&A->values, A->bytes);
         if (ce != cudaSuccess) { delete A; return cuda_fail(ce, "allocating matrix values"); }
-        created = true;
+        J.created = true;
     }
+    J.A = A;
+    return IGA_OK;
+}
+
+// Scratch pointers, tables and spline buffers of a planned job.
+void job_bind(Job& J, double* scratch)
+{
+    J.scratch = scratch;
+    auto P = [&](int64_t off) { return scratch + off; };
+    for (int d = 0; d < 3; ++d) {
+        J.gx[d] = P(J.o_gx[d]); J.sx[d] = P(J.o_sx[d]); J.cx[d] = P(J.o_cx[d]); J.wq[d] = P(J.o_wq[d]);
+        J.bv[d] = P(J.o_bv[d]); J.bd[d] = P(J.o_bd[d]); J.X[d] = P(J.o_X[d]); J.Xs[d] = P(J.o_Xs[d]);
+        J.tdf[d] = reinterpret_cast<float2*>(P(J.o_tdf[d]));
+    }
+    Tables& T = J.T;
+    for (int d = 0; d < 3; ++d) {
+        T.gx[d] = J.gx[d]; T.sx[d] = J.sx[d]; T.cx[d] = J.cx[d]; T.X[d] = J.X[d]; T.Xs[d] = J.Xs[d];
+        T.tdf[d] = J.tdf[d];
+    }
+    T.arith = J.arith;
+    T.tc = (J.dtype == IGA_F32) ? current_tc(J.dtype) : 0;
+    T.tc64 = J.tc64;
+    T.gshift = J.tc64 ? reinterpret_cast<const int*>(P(J.o_gshift)) : nullptr;
+    J.samples = J.do_spline ? P(J.o_samples) : nullptr;
+    memset(&J.sb, 0, sizeof(J.sb));
+    if (J.do_spline) {
+        spline_bufs(scratch, J.sp, J.slo, J.sb);
+        J.sb.partial = reinterpret_cast<float2*>(P(J.o_partial));
+        J.sb.mid = P(J.o_mid);
+    }
+}
+
+cudaError_t job_pre_impl(Job& J, cudaStream_t st, const char** stage)
+{
+    *stage = "basis tables";
+    cudaError_t ce = launch_basis(J.g, J.gx, J.sx, J.cx, J.bv, J.bd, J.wq, J.tdf, st);
+    if (ce == cudaSuccess) { *stage = "pair tables"; ce = launch_pairs(J.g, J.bv, J.bd, J.wq, J.X, J.Xs, J.arith, st); }
+    if (ce == cudaSuccess && J.tc64) {
+        *stage = "tensor-core stage X set-up";
+        ce = launch_tc_group_shift(J.g, J.T, reinterpret_cast<int*>(J.scratch + J.o_gshift), st);
+        if (ce == cudaSuccess && J.o_ex_lo >= 0)
+            ce = cudaMemsetAsync(J.scratch + J.o_ex_lo, 0, (size_t)(J.o_ex_hi - J.o_ex_lo) * sizeof(double), st);
+    }
+    if (ce == cudaSuccess) { *stage = "coefficient field"; ce = launch_coef(J.g, J.T, J.bs, J.nblk[0], J.scratch, st); }
+    return ce;
+}
+
+cudaError_t job_quad_impl(Job& J, cudaStream_t st, const char** stage)
+{
+    *stage = "quadrature stages";
+    return (J.form == kFormMass)
+               ? launch_mass_stages(J.g, J.T, J.bs, J.nblk, J.scratch, J.A->values, J.dtype == IGA_F32, J.samples, st)
+               : launch_stages(J.g, J.T, J.bs, J.nblk, J.scratch, J.A->values, J.dtype == IGA_F32, J.samples, st);
+}
+
+cudaError_t job_post_impl(Job& J, cudaStream_t st, const char** stage)
+{
+    cudaError_t ce = cudaSuccess;
+    if (J.do_spline) { *stage = "spline interpolation"; ce = launch_spline(J.g, J.sp, J.samples, J.sb, st); }
+    if (J.surrogate && ce == cudaSuccess) {
+        *stage = "surrogate fill";
+        ce = launch_fill(J.g, J.sp, J.empty, J.sb, J.A->values, J.dtype == IGA_F32, st);
+    }
+    return ce;
+}
+
+void job_discard_matrix(Job& J)
+{
+    if (J.created && J.A) {
+        cudaFree(J.A->values);
+        delete J.A;
+        J.A = nullptr;
+        J.created = false;
+    }
+}
+
+int assemble(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
+             int M, int q, int domains, int dtype, void* stream_v, iga_matrix_t* out, int form = kFormStiffness)
+{
+    t_err.clear();
+    if (!out) return fail(IGA_EINVAL, "output handle pointer is null");
+    Job J;
+    int rc = job_plan(J, patch, p, map, kappa, surrogate, M, q, domains, dtype, form, *out);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream_v;
     cudaMemPool_t pool;
-    if ((ce = device_pool(dev, &pool)) != cudaSuccess) {
-        if (created) { cudaFree(A->values); delete A; }
+    cudaError_t ce = device_pool(J.A->device, &pool);
+    if (ce != cudaSuccess) {
+        job_discard_matrix(J);
         return cuda_fail(ce, "creating the memory pool");
     }
     double* scratch = nullptr;
     // inside a graph capture the allocation becomes a graph memory node (default pool)
-    ce = t_capture ? cudaMallocAsync((void**)&scratch, (size_t)lay.total * sizeof(double), st)
-                   : cudaMallocFromPoolAsync((void**)&scratch, (size_t)lay.total * sizeof(double), pool, st);
+    ce = t_capture ? cudaMallocAsync((void**)&scratch, (size_t)J.lay.total * sizeof(double), st)
+                   : cudaMallocFromPoolAsync((void**)&scratch, (size_t)J.lay.total * sizeof(double), pool, st);
     if (ce != cudaSuccess) {
-        if (created) { cudaFree(A->values); delete A; }
+        job_discard_matrix(J);
         return cuda_fail(ce, "allocating scratch");
     }
-
-    // ---------------- launches ----------------
-    auto P = [&](int64_t off) { return scratch + off; };
-    double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
-    void* Xs[3];
-    float2* tdf[3];
-    for (int d = 0; d < 3; ++d) {
-        gx[d] = P(o_gx[d]); sx[d] = P(o_sx[d]); cx[d] = P(o_cx[d]); wq[d] = P(o_wq[d]);
-        bv[d] = P(o_bv[d]); bd[d] = P(o_bd[d]); X[d] = P(o_X[d]); Xs[d] = P(o_Xs[d]);
-        tdf[d] = reinterpret_cast<float2*>(P(o_tdf[d]));
-    }
-    Tables T;
-    for (int d = 0; d < 3; ++d) {
-        T.gx[d] = gx[d]; T.sx[d] = sx[d]; T.cx[d] = cx[d]; T.X[d] = X[d]; T.Xs[d] = Xs[d]; T.tdf[d] = tdf[d];
-    }
-    T.arith = arith;
-    T.tc = (dtype == IGA_F32) ? current_tc(dtype) : 0;
-    T.tc64 = tc64;
-    T.gshift = tc64 ? reinterpret_cast<const int*>(P(o_gshift)) : nullptr;
-    const char* stage = "basis tables";
-    ce = launch_basis(g, gx, sx, cx, bv, bd, wq, tdf, st);
-    if (ce == cudaSuccess) { stage = "pair tables"; ce = launch_pairs(g, bv, bd, wq, X, Xs, arith, st); }
-    if (ce == cudaSuccess && tc64) {
-        stage = "tensor-core stage X set-up";
-        ce = launch_tc_group_shift(g, T, reinterpret_cast<int*>(P(o_gshift)), st);
-        if (ce == cudaSuccess && o_ex_lo >= 0)
-            ce = cudaMemsetAsync(P(o_ex_lo), 0, (size_t)(o_ex_hi - o_ex_lo) * sizeof(double), st);
-    }
-    if (ce == cudaSuccess) { stage = "coefficient field"; ce = launch_coef(g, T, bs, nblk[0], scratch, st); }
-    double* samples = do_spline ? P(o_samples) : nullptr;
-    if (ce == cudaSuccess) {
-        stage = "quadrature stages";
-        ce = (form == kFormMass) ? launch_mass_stages(g, T, bs, nblk, scratch, A->values, dtype == IGA_F32, samples, st)
-                                 : launch_stages(g, T, bs, nblk, scratch, A->values, dtype == IGA_F32, samples, st);
-    }
-    SplineBufs sb;
-    memset(&sb, 0, sizeof(sb));
-    if (do_spline) {
-        spline_bufs(scratch, sp, slo, sb);
-        sb.partial = reinterpret_cast<float2*>(P(o_partial));
-        sb.mid = P(o_mid);
-        if (ce == cudaSuccess) { stage = "spline interpolation"; ce = launch_spline(g, sp, samples, sb, st); }
-    }
-    if (surrogate && ce == cudaSuccess) {
-        stage = "surrogate fill";
-        ce = launch_fill(g, sp, empty, sb, A->values, dtype == IGA_F32, st);
-    }
+    job_bind(J, scratch);
+    const char* stage = "";
+    ce = job_pre_impl(J, st, &stage);
+    if (ce == cudaSuccess) ce = job_quad_impl(J, st, &stage);
+    if (ce == cudaSuccess) ce = job_post_impl(J, st, &stage);
     cudaError_t fe = cudaFreeAsync(scratch, st);
     if (ce == cudaSuccess) ce = fe;
     if (ce != cudaSuccess) {
-        if (created) { cudaFree(A->values); delete A; }
+        job_discard_matrix(J);
         return cuda_fail(ce, stage);
     }
-    *out = A;
+    *out = J.A;
     return IGA_OK;
 }
 
@@ -619,6 +688,68 @@ int assemble_patch(const iga_patch_t* patch, int p, const iga_map_t* map, const 
                    int M, int q, int domains, int dtype, void* stream, iga_matrix_t* out)
 {
     return assemble(patch, p, map, kappa, surrogate, M, q, domains, dtype, stream, out);
+}
+
+int job_create(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate, int M,
+               int q, int domains, int dtype, iga_matrix_t existing, Job** out)
+{
+    t_err.clear();
+    Job* J = new (std::nothrow) Job;
+    if (!J) return fail(IGA_ENOMEM, "host allocation failed");
+    const int rc = job_plan(*J, patch, p, map, kappa, surrogate, M, q, domains, dtype, kFormStiffness, existing);
+    if (rc) {
+        delete J;
+        return rc;
+    }
+    *out = J;
+    return IGA_OK;
+}
+
+int64_t job_scratch_doubles(const Job* J) { return J->lay.total; }
+void job_set_scratch(Job* J, double* scratch) { job_bind(*J, scratch); }
+iga_matrix_t job_matrix(const Job* J) { return J->A; }
+
+cudaError_t job_pre(Job* J, cudaStream_t s)
+{
+    const char* stage = "";
+    return job_pre_impl(*J, s, &stage);
+}
+cudaError_t job_quad(Job* J, cudaStream_t s)
+{
+    const char* stage = "";
+    return job_quad_impl(*J, s, &stage);
+}
+cudaError_t job_post(Job* J, cudaStream_t s)
+{
+    const char* stage = "";
+    return job_post_impl(*J, s, &stage);
+}
+
+bool job_persist_work(const Job* J, PersistWork* w)
+{
+    if (J->form != kFormStiffness || J->T.tc || J->T.tc64) return false;
+    memset(w, 0, sizeof(*w));
+    w->g = J->g;
+    w->T = J->T;
+    w->bs = J->bs;
+    w->scratch = J->scratch;
+    w->ell = J->A->values;
+    w->ell_f32 = J->dtype == IGA_F32;
+    w->N = J->A->N;
+    w->samples = J->samples;
+    for (int k = 0; k < 4; ++k) w->nb[k] = J->nblk[k];
+    return true;
+}
+
+int job_dim(const Job* J) { return J->g.dim; }
+int job_degree(const Job* J) { return J->g.p; }
+int job_arith(const Job* J) { return J->arith; }
+
+void job_destroy(Job* J, bool discard_new_matrix)
+{
+    if (!J) return;
+    if (discard_new_matrix) job_discard_matrix(*J);
+    delete J;
 }
 
 void launch_end(int kid, cudaStream_t s)

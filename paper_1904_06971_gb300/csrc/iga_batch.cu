@@ -3,16 +3,27 @@
 //
 // The first call with a given batch creates the matrices eagerly.  Later calls
 // with the same batch (same descriptions, the same matrix handles, dtype and
-// contraction arithmetic) replay a cached graph: every patch's kernel chain
-// (tables, coefficient field, quadrature stages, interpolation, fill; with their
-// stream-ordered scratch allocations) captured on B concurrent branches, patches
-// assigned to branches longest-first by their stencil slot count.  B is picked
-// by an autotuner on the first graph call: it captures B = 1, 2, 4, ..., 32
-// (up to the batch size), times two replays of each and keeps the fastest.
+// contraction arithmetic) replay a cached graph.  On a cache miss an autotuner
+// captures candidate graphs of two kinds, times two replays of each and keeps
+// the fastest:
+//   - branches: every patch's kernel chain (tables, coefficient field,
+//     quadrature stages, interpolation, fill; with their stream-ordered scratch
+//     allocations) on B concurrent branches, B = 1, 2, 4, ..., 32, patches
+//     assigned longest-first to the least loaded branch;
+//   - persistent: the tables and coefficient fields of all patches on B
+//     branches, then the quadrature stages Z, Y, X of all patches of one
+//     (dimension, degree, arithmetic) as ONE persistent launch over device-side
+//     patch descriptors (k_quad.cu: work items = stage blocks, a device claim
+//     counter, per-patch completion counters, bounded waits), then the
+//     interpolation and fill on B branches; tuned over the persistent grid
+//     (resident blocks per SM) and the items claimed at a time.  Its scratch
+//     is one allocation owned by the cached graph.
 // Replays add the graph's kernel count to iga_launch_count.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <atomic>
 #include <unordered_map>
 #include <vector>
 
@@ -21,11 +32,42 @@
 namespace iga {
 namespace {
 
+// Device resources of the persistent mode: the jobs (planned assemblies bound to
+// one scratch allocation) and, per (dimension, degree, arithmetic), the patch
+// descriptors, work segments, claim counter / status and completion counters.
+struct PersistGroup {
+    int dim = 0, p = 0, arith = 0, nwork = 0, nseg = 0;
+    int64_t total = 0;
+    PersistWork* works = nullptr;
+    PersistSeg* segs = nullptr;
+    PersistCtl* ctl = nullptr;
+    unsigned* done = nullptr;
+};
+struct PersistState {
+    double* scratch = nullptr;
+    std::vector<Job*> jobs;
+    std::vector<PersistGroup> groups;
+    ~PersistState()
+    {
+        // the owner synchronised the device before dropping the last reference
+        for (auto& G : groups) {
+            cudaFree(G.works);
+            cudaFree(G.segs);
+            cudaFree(G.ctl);
+            cudaFree(G.done);
+        }
+        for (Job* J : jobs) job_destroy(J, false);
+        if (scratch) cudaFree(scratch);
+    }
+};
+
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
     int branches = 0;
     float ms = 0.f;
+    int persistent = 0, bps = 0, chunk = 0;   // persistent mode: resident blocks per SM, items per claim
+    std::shared_ptr<PersistState> ps;
     std::vector<iga_matrix_t> mats;      // the matrices the graph writes into
 };
 
@@ -44,6 +86,10 @@ thread_local int t_branches = 0;
 thread_local int64_t t_kernels = 0;
 thread_local int t_cached = 0;
 thread_local float t_ms = 0.f;
+thread_local int t_persistent = 0, t_bps = 0, t_chunk = 0;
+thread_local std::shared_ptr<PersistState> t_last_ps;     // persistent state of this thread's last replay
+std::atomic<int> g_allow_graph{1}, g_allow_persistent{1};
+constexpr long long kPersistLimitNs = 2000000000LL;      // 2 s per wait for another block's item
 
 uint64_t fnv(uint64_t h, const void* data, size_t n)
 {
@@ -127,6 +173,165 @@ int capture(Streams& S, int n, const iga_batch_item_t* items, int dtype, iga_mat
     return IGA_OK;
 }
 
+// Plan every patch as a job bound to one scratch allocation and build the
+// persistent work of each (dimension, degree, arithmetic) group.  Returns
+// IGA_EUNSUPPORTED (nothing kept) when a patch's stages cannot run in the
+// persistent kernel (tensor-core stage X).
+int persist_setup(int n, const iga_batch_item_t* items, int dtype, iga_matrix_t* A, const std::vector<int>& order,
+                  std::shared_ptr<PersistState>& out)
+{
+    auto ps = std::make_shared<PersistState>();
+    std::vector<int64_t> off(n, 0);
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const iga_batch_item_t& it = items[i];
+        Job* J = nullptr;
+        const int rc = job_create(&it.patch, it.p, &it.map, &it.kappa, it.M >= 1, it.M >= 1 ? it.M : 1, it.q,
+                                  it.domains, dtype, A[i], &J);
+        if (rc != IGA_OK) return rc;
+        ps->jobs.push_back(J);
+        off[i] = total;
+        total += (job_scratch_doubles(J) + 31) / 32 * 32;
+    }
+    cudaError_t e = cudaMalloc((void**)&ps->scratch, (size_t)std::max<int64_t>(total, 1) * sizeof(double));
+    if (e != cudaSuccess) return report_error(IGA_ENOMEM, "persistent batch: scratch allocation failed");
+    std::vector<std::vector<PersistWork>> works;
+    for (int i = 0; i < n; ++i) job_set_scratch(ps->jobs[i], ps->scratch + off[i]);
+    // groups in the order of their first (longest) patch
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        Job* J = ps->jobs[i];
+        PersistWork w;
+        if (!job_persist_work(J, &w)) return report_error(IGA_EUNSUPPORTED, "persistent batch: tensor-core stage X");
+        int gi = -1;
+        for (size_t g = 0; g < ps->groups.size(); ++g)
+            if (ps->groups[g].dim == job_dim(J) && ps->groups[g].p == job_degree(J) && ps->groups[g].arith == job_arith(J))
+                gi = (int)g;
+        if (gi < 0) {
+            PersistGroup G;
+            G.dim = job_dim(J); G.p = job_degree(J); G.arith = job_arith(J);
+            ps->groups.push_back(G);
+            works.emplace_back();
+            gi = (int)ps->groups.size() - 1;
+        }
+        w.done0 = 4 * (int64_t)works[gi].size();
+        works[gi].push_back(w);
+    }
+    for (size_t g = 0; g < ps->groups.size(); ++g) {
+        PersistGroup& G = ps->groups[g];
+        const std::vector<PersistWork>& W = works[g];
+        std::vector<PersistSeg> segs;
+        int64_t t = 0;
+        for (int stage = (G.dim == 3 ? 1 : 3); stage <= 4; ++stage)
+            for (size_t w = 0; w < W.size(); ++w) {
+                const int64_t cnt = W[w].nb[stage <= 2 ? 1 : stage - 1];
+                if (cnt <= 0) continue;
+                segs.push_back({stage, (int)w, t, cnt});
+                t += cnt;
+            }
+        G.nwork = (int)W.size();
+        G.nseg = (int)segs.size();
+        G.total = t;
+        if (G.nseg == 0) continue;
+        e = cudaMalloc((void**)&G.works, W.size() * sizeof(PersistWork));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&G.segs, segs.size() * sizeof(PersistSeg));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&G.ctl, sizeof(PersistCtl));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&G.done, 4 * W.size() * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemcpy(G.works, W.data(), W.size() * sizeof(PersistWork), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(G.segs, segs.data(), segs.size() * sizeof(PersistSeg), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(G.ctl, 0, sizeof(PersistCtl));
+        if (e != cudaSuccess) return report_error(IGA_ECUDA, cudaGetErrorString(e));
+    }
+    out = ps;
+    return IGA_OK;
+}
+
+// Capture the persistent mode: pre phases on B branches, one persistent launch
+// per group (each on its own branch), post phases on B branches.
+int capture_persist(Streams& S, int n, const iga_batch_item_t* items, const std::shared_ptr<PersistState>& ps,
+                    int B, int bps, int chunk, const std::vector<int>& order, GraphEntry& out)
+{
+    int nsm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S.device);
+    if (e != cudaSuccess) return report_error(IGA_ECUDA, cudaGetErrorString(e));
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(S.cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return report_error(IGA_ECUDA, "begin graph capture failed");
+    set_capture(true);
+    const int64_t l0 = launch_count();
+    std::vector<int> branch(n, 0);
+    std::vector<int64_t> load(B, 0);
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[b] += item_work(items[i]);
+        branch[i] = b;
+    }
+    auto fork = [&](int nb) {
+        cudaError_t r = cudaEventRecord(S.fork, S.cap);
+        for (int b = 0; b < nb && r == cudaSuccess; ++b) r = cudaStreamWaitEvent(S.br[b], S.fork, 0);
+        return r;
+    };
+    auto join = [&](int nb) {
+        cudaError_t r = cudaSuccess;
+        for (int b = 0; b < nb && r == cudaSuccess; ++b) {
+            r = cudaEventRecord(S.join[b], S.br[b]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(S.cap, S.join[b], 0);
+        }
+        return r;
+    };
+    e = fork(B);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) e = job_pre(ps->jobs[order[k]], S.br[branch[order[k]]]);
+    if (e == cudaSuccess) e = join(B);
+    const int G = (int)std::min<size_t>(ps->groups.size(), kMaxBranches);
+    if (e == cudaSuccess) e = fork(G);
+    for (int g = 0; g < (int)ps->groups.size() && e == cudaSuccess; ++g) {
+        const PersistGroup& P = ps->groups[g];
+        if (P.nseg == 0) continue;
+        cudaStream_t s = S.br[g % kMaxBranches];
+        e = cudaMemsetAsync(P.ctl, 0, sizeof(PersistCtl), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P.done, 0, 4 * (size_t)P.nwork * sizeof(unsigned), s);
+        const int bmax = persist_blocks_per_sm(P.dim, P.p, P.arith);
+        const int per_sm = std::max(1, std::min(bps, bmax));
+        const int64_t want = (P.total + chunk - 1) / chunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * nsm, want));
+        if (e == cudaSuccess)
+            e = launch_persist(P.dim, P.p, P.arith, P.works, P.segs, P.nseg, P.total, chunk, grid, P.ctl, P.done,
+                               kPersistLimitNs, s);
+    }
+    if (e == cudaSuccess) e = join(G);
+    if (e == cudaSuccess) e = fork(B);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) e = job_post(ps->jobs[order[k]], S.br[branch[order[k]]]);
+    if (e == cudaSuccess) e = join(B);
+    const int64_t captured = launch_count() - l0;
+    add_launches(-captured);
+    cudaError_t ee = cudaStreamEndCapture(S.cap, &graph);
+    set_capture(false);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&out.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return report_error(IGA_ECUDA, cudaGetErrorString(e));
+    out.kernels = captured;
+    out.branches = B;
+    out.persistent = 1;
+    out.bps = bps;
+    out.chunk = chunk;
+    out.ps = ps;
+    return IGA_OK;
+}
+
+// 1 when a wait of the last replay of ps gave up (reads the status words; the caller synchronised).
+int persist_timed_out(const PersistState& ps)
+{
+    for (const auto& G : ps.groups) {
+        if (G.nseg == 0) continue;
+        PersistCtl c;
+        if (cudaMemcpy(&c, G.ctl, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
+        if (c.status) return 1;
+    }
+    return 0;
+}
+
 }  // namespace
 
 void batch_forget(iga_matrix_t A)
@@ -138,6 +343,7 @@ void batch_forget(iga_matrix_t A)
             // a graph that may still run on some stream: wait for the device before destroying it
             cudaDeviceSynchronize();
             if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+            if (t_last_ps == it->second.ps) t_last_ps.reset();
             it = g_graphs.erase(it);
         } else {
             ++it;
@@ -194,6 +400,10 @@ int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* st
         t_branches = hit->second.branches;
         t_kernels = hit->second.kernels;
         t_ms = hit->second.ms;
+        t_persistent = hit->second.persistent;
+        t_bps = hit->second.bps;
+        t_chunk = hit->second.chunk;
+        t_last_ps = hit->second.ps;
         t_cached = 1;
         return IGA_OK;
     }
@@ -208,9 +418,35 @@ int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* st
     if ((e = cudaEventRecord(in_ev, st)) != cudaSuccess || (e = cudaStreamWaitEvent(S->cap, in_ev, 0)) != cudaSuccess)
         return report_error(IGA_ECUDA, cudaGetErrorString(e));
     GraphEntry best;
-    for (int B = 1; B <= kMaxBranches && B <= std::max(1, n); B *= 2) {
+    // candidates: branch graphs B = 1, 2, 4, ..., 32; persistent graphs over the branches of the
+    // per-patch phases (8, 32) x resident blocks per SM x items per claim
+    struct Cand { int persistent, B, bps, chunk; };
+    std::vector<Cand> cands;
+    if (g_allow_graph.load())
+        for (int B = 1; B <= kMaxBranches && B <= std::max(1, n); B *= 2) cands.push_back({0, B, 0, 0});
+    std::shared_ptr<PersistState> ps;
+    if (g_allow_persistent.load()) {
+        const int rc = persist_setup(n, items, dtype, A, order, ps);
+        if (rc == IGA_OK) {
+            int bmax = 1;
+            for (const auto& G : ps->groups) bmax = std::max(bmax, persist_blocks_per_sm(G.dim, G.p, G.arith));
+            for (int Bp : {8, 32}) {
+                const int B = std::min(Bp, std::max(1, n));
+                if (Bp == 32 && B <= 8) continue;            // same branch count as the first pass
+                for (int bps : {std::max(1, bmax / 2), bmax})
+                    for (int chunk : {1, 4}) cands.push_back({1, B, bps, chunk});
+            }
+        } else if (rc != IGA_EUNSUPPORTED || !g_allow_graph.load()) {
+            return rc;
+        } else {
+            ps.reset();
+        }
+    }
+    if (cands.empty()) return report_error(IGA_EINVAL, "batch: every autotuner candidate is switched off");
+    for (const Cand& cd : cands) {
         GraphEntry cand;
-        const int rc = capture(*S, n, items, dtype, A, B, order, cand);
+        const int rc = cd.persistent ? capture_persist(*S, n, items, ps, cd.B, cd.bps, cd.chunk, order, cand)
+                                     : capture(*S, n, items, dtype, A, cd.B, order, cand);
         if (rc != IGA_OK) {
             if (best.exec) cudaGraphExecDestroy(best.exec);
             return rc;
@@ -230,6 +466,11 @@ int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* st
         }
         add_launches(3 * cand.kernels);
         cand.ms = ms / 2.f;
+        if (cand.persistent && persist_timed_out(*cand.ps)) {
+            cudaGraphExecDestroy(cand.exec);
+            if (best.exec) cudaGraphExecDestroy(best.exec);
+            return report_error(IGA_ETIMEOUT, "persistent batch: a wait for another block's work item ran out of time");
+        }
         if (!best.exec || cand.ms < best.ms) {
             if (best.exec) cudaGraphExecDestroy(best.exec);
             best = cand;
@@ -245,6 +486,72 @@ int iga_assemble_batch(int n, const iga_batch_item_t* items, int dtype, void* st
     t_branches = best.branches;
     t_kernels = best.kernels;
     t_ms = best.ms;
+    t_persistent = best.persistent;
+    t_bps = best.bps;
+    t_chunk = best.chunk;
+    t_last_ps = best.ps;
+    return IGA_OK;
+}
+
+int iga_batch_set_modes(int allow_branches, int allow_persistent)
+{
+    if (!allow_branches && !allow_persistent) return report_error(IGA_EINVAL, "at least one batch mode must be allowed");
+    g_allow_graph = allow_branches ? 1 : 0;
+    g_allow_persistent = allow_persistent ? 1 : 0;
+    return IGA_OK;
+}
+
+int iga_batch_mode(int* persistent, int* blocks_per_sm, int* chunk)
+{
+    if (persistent) *persistent = t_persistent;
+    if (blocks_per_sm) *blocks_per_sm = t_bps;
+    if (chunk) *chunk = t_chunk;
+    return IGA_OK;
+}
+
+int iga_batch_status(void* stream)
+{
+    if (!t_last_ps) return IGA_OK;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return report_error(IGA_ECUDA, cudaGetErrorString(e));
+    if (persist_timed_out(*t_last_ps))
+        return report_error(IGA_ETIMEOUT, "persistent batch: a wait for another block's work item ran out of time");
+    return IGA_OK;
+}
+
+int iga_batch_selftest_timeout(long long limit_us, void* stream)
+{
+    // One item of stage X whose stage-Y counter nothing increments: the wait must
+    // give up after limit_us and report it; the item's body never runs.
+    if (limit_us < 1 || limit_us > 10000000) return report_error(IGA_EINVAL, "limit_us must be in 1..1e7");
+    cudaStream_t st = (cudaStream_t)stream;
+    PersistWork w;
+    memset(&w, 0, sizeof(w));
+    w.nb[2] = 1;
+    const PersistSeg seg = {4, 0, 0, 1};
+    PersistWork* dw = nullptr;
+    PersistSeg* ds = nullptr;
+    PersistCtl* dc = nullptr;
+    unsigned* dd = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dw, sizeof(w));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ds, sizeof(seg));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dc, sizeof(PersistCtl));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dd, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, &w, sizeof(w), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ds, &seg, sizeof(seg), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(PersistCtl), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dd, 0, 4 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = launch_persist(2, 1, current_arith(IGA_F32), dw, ds, 1, 1, 1, 1, dc, dd, limit_us * 1000LL, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    PersistCtl c;
+    memset(&c, 0, sizeof(c));
+    if (e == cudaSuccess) e = cudaMemcpy(&c, dc, sizeof(c), cudaMemcpyDeviceToHost);
+    cudaFree(dw);
+    cudaFree(ds);
+    cudaFree(dc);
+    cudaFree(dd);
+    if (e != cudaSuccess) return report_error(IGA_ECUDA, cudaGetErrorString(e));
+    if (c.status) return report_error(IGA_ETIMEOUT, "persistent kernel: the wait ran out of time (as intended)");
     return IGA_OK;
 }
 
@@ -260,9 +567,13 @@ int iga_batch_info(int* branches, int64_t* kernels, int* cached, float* tuned_ms
 int iga_batch_release(void)
 {
     std::lock_guard<std::mutex> lk(g_batch_mu);
+    bool any_ps = false;
+    for (auto& kv : g_graphs) any_ps = any_ps || (bool)kv.second.ps;
+    if (any_ps || t_last_ps) cudaDeviceSynchronize();     // persistent scratch may still be in use
     for (auto& kv : g_graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     g_graphs.clear();
+    t_last_ps.reset();
     return IGA_OK;
 }
 

@@ -132,7 +132,7 @@ struct Tables {
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
     K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE,
-    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_MMS, K_NUM
+    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_MMS, K_PERSIST, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
@@ -158,6 +158,65 @@ void batch_forget(iga_matrix_t A);
 // One patch through the exact (surrogate = false) or surrogate pipeline on `stream`.
 int assemble_patch(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate,
                    int M, int q, int domains, int dtype, void* stream, iga_matrix_t* out);
+
+// ---- one stiffness assembly split into phases (iga_api.cu), for the persistent batch ----
+// job_create plans it (argument checks, boxes, sampling lattice, scratch layout)
+// and creates the matrix unless `existing` is given; the caller provides the
+// scratch (job_scratch_doubles doubles) and runs pre (tables, coefficient
+// field), quad (the stage launches, or a persistent launch over PersistWork
+// descriptors), post (interpolation, fill) on a stream.
+struct Job;
+// Everything the persistent quadrature kernel needs of one patch (k_quad.cu);
+// done0 indexes its four completion counters (stage Z halves, Y, X).
+struct PersistWork {
+    Geo g;
+    Tables T;
+    BoxSet bs;
+    double* scratch;
+    void* ell;
+    double* samples;
+    int64_t N;
+    int ell_f32;
+    int64_t nb[4];            // blocks of the coefficient, Z (per half), Y and X launches
+    int64_t done0;
+};
+int job_create(const iga_patch_t* patch, int p, const iga_map_t* map, const iga_kappa_t* kappa, bool surrogate, int M,
+               int q, int domains, int dtype, iga_matrix_t existing, Job** out);
+int64_t job_scratch_doubles(const Job* J);
+void job_set_scratch(Job* J, double* scratch);
+iga_matrix_t job_matrix(const Job* J);
+cudaError_t job_pre(Job* J, cudaStream_t s);
+cudaError_t job_quad(Job* J, cudaStream_t s);
+cudaError_t job_post(Job* J, cudaStream_t s);
+// false when the job's stages must run as their own launches (tensor-core stage X)
+bool job_persist_work(const Job* J, PersistWork* w);
+int job_dim(const Job* J);
+int job_degree(const Job* J);
+int job_arith(const Job* J);
+void job_destroy(Job* J, bool discard_new_matrix);
+
+// A run of consecutive work items of the persistent kernel: blocks 0..count-1
+// of stage `stage` (1, 2: Z halves; 3: Y; 4: X) of patch `work`, items
+// first..first+count-1.
+struct PersistSeg {
+    int stage, work;
+    int64_t first, count;
+};
+// Claim counter and status of one persistent launch; zeroed before it.
+struct PersistCtl {
+    unsigned long long next;  // next unclaimed item
+    int abort;                // set when a wait gave up: the other blocks stop
+    int status;               // 1: a wait for another block's item ran out of time
+};
+// Stages Z, Y, X of every work as one launch of `grid` blocks that claim
+// `chunk` consecutive items at a time; an item whose stage needs the previous
+// stage of its patch waits (bounded by limit_ns of the GPU's global timer) on
+// that stage's completion counter in done (4 per work, zeroed).
+cudaError_t launch_persist(int dim, int p, int arith, const PersistWork* works, const PersistSeg* segs, int nseg,
+                           int64_t total, int chunk, int grid, PersistCtl* ctl, unsigned* done, long long limit_ns,
+                           cudaStream_t s);
+// Resident blocks per SM of the persistent kernel (0 when the variant is not built).
+int persist_blocks_per_sm(int dim, int p, int arith);
 
 // Contraction arithmetic (arith.cuh kind) chosen for matrices of value type dtype,
 // and whether its stage X runs on the tensor cores (FP32 values, IGA_ARITH_BF16X3).

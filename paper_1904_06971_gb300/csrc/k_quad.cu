@@ -73,16 +73,17 @@ __device__ __forceinline__ void load_run(const S* p, S* v)
 // keep the accumulators of one thread small enough for two blocks per SM).
 // ---------------------------------------------------------------------------
 template <class Pol, int P, int HALF>
-__device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch)
+__device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch,
+                                             int64_t blk)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     Box b;
-    get_box(bs, 3, P, 1, blockIdx.x, b);
+    get_box(bs, 3, P, 1, blk, b);
     const int64_t G0 = (int64_t)b.E[0] * Q, G1 = (int64_t)b.E[1] * Q, G2 = (int64_t)b.E[2] * Q;
     const int64_t plane = G0 * G1;
-    const int64_t item = (int64_t)(blockIdx.x - b.blk[1]) * kBlock + threadIdx.x;
+    const int64_t item = (blk - b.blk[1]) * kBlock + threadIdx.x;
     if (item >= (int64_t)b.R[2] * plane) return;
     const int i3l = (int)(item / plane);
     const int64_t pp = item % plane;
@@ -170,30 +171,31 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
 template <class Pol, int P, int HALF>
 __global__ void __launch_bounds__(kBlock) k_stage_z(Geo g, Tables T, BoxSet bs, double* scratch)
 {
-    stage_z_body<Pol, P, HALF>(g, T, bs, scratch);
+    stage_z_body<Pol, P, HALF>(g, T, bs, scratch, blockIdx.x);
 }
 template <int P, int HALF>
 __global__ void __launch_bounds__(kBlock, 3) k_stage_z_f32(Geo g, Tables T, BoxSet bs, double* scratch)
 {
-    stage_z_body<PolF32, P, HALF>(g, T, bs, scratch);
+    stage_z_body<PolF32, P, HALF>(g, T, bs, scratch, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
 // stage Y: contract direction 1
 // ---------------------------------------------------------------------------
 template <class Pol, int P, int DIM>
-__device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch)
+__device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch,
+                                             int64_t blk)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
     constexpr int NIN = (DIM == 3) ? 8 : 3;
     Box b;
-    get_box(bs, DIM, P, 2, blockIdx.x, b);
+    get_box(bs, DIM, P, 2, blk, b);
     const int64_t G0 = (int64_t)b.E[0] * Q, G1 = (int64_t)b.E[1] * Q;
     const int64_t P3 = (DIM == 3) ? (int64_t)b.R[2] * W : 1;
     const int R2 = b.R[1];
-    const int64_t item = (int64_t)(blockIdx.x - b.blk[2]) * kBlock + threadIdx.x;
+    const int64_t item = (blk - b.blk[2]) * kBlock + threadIdx.x;
     if (item >= P3 * R2 * G0) return;
     const int64_t g0 = item % G0;
     const int i2l = (int)((item / G0) % R2);
@@ -320,12 +322,12 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
 template <class Pol, int P, int DIM>
 __global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, double* scratch)
 {
-    stage_y_body<Pol, P, DIM>(g, T, bs, scratch);
+    stage_y_body<Pol, P, DIM>(g, T, bs, scratch, blockIdx.x);
 }
 template <int P, int DIM>
 __global__ void __launch_bounds__(kBlock, 3) k_stage_y_f32(Geo g, Tables T, BoxSet bs, double* scratch)
 {
-    stage_y_body<PolF32, P, DIM>(g, T, bs, scratch);
+    stage_y_body<PolF32, P, DIM>(g, T, bs, scratch, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -334,8 +336,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_stage_y_f32(Geo g, Tables T, BoxS
 // loads serves LINES rows of output.
 // ---------------------------------------------------------------------------
 template <class Pol, int P, int DIM, int LINES>
-__global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, double* scratch,
-                                                    void* ell, int ell_f32, int64_t N, double* samples, int skip_card)
+__device__ __forceinline__ void stage_x_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch,
+                                             void* ell, int ell_f32, int64_t N, double* samples, int skip_card,
+                                             int64_t blk)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
         for (int k = threadIdx.x; k < W * TT * 4; k += blockDim.x) sX[k] = X0[(int64_t)(2 * P) * W * TT * 4 + k];
     __syncthreads();
     Box b;
-    get_box(bs, DIM, P, 3, blockIdx.x, b);
+    get_box(bs, DIM, P, 3, blk, b);
     const int64_t G0 = (int64_t)b.E[0] * Q;
     const int64_t P3 = (DIM == 3) ? (int64_t)b.R[2] * W : 1;
     const int64_t P2 = (int64_t)b.R[1] * W;
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
         R1 = nlo + max(0, end - hi0);
         if (R1 == 0) return;
     }
-    const int64_t item = (int64_t)(blockIdx.x - b.blk[3]) * kBlock + threadIdx.x;
+    const int64_t item = (blk - b.blk[3]) * kBlock + threadIdx.x;
     if (item >= P3 * NL * R1) return;
     const int i1l = (int)(item % R1);
     const int64_t lg = (item / R1) % NL;
@@ -442,6 +445,13 @@ __global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, 
                 samples[(int64_t)(slot0 + dd) * bs.n_samples + b.sample_id] = Pol::to_double(acc[l][dd]);
         }
     }
+}
+
+template <class Pol, int P, int DIM, int LINES>
+__global__ void __launch_bounds__(kBlock) k_stage_x(Geo g, Tables T, BoxSet bs, double* scratch,
+                                                    void* ell, int ell_f32, int64_t N, double* samples, int skip_card)
+{
+    stage_x_body<Pol, P, DIM, LINES>(g, T, bs, scratch, ell, ell_f32, N, samples, skip_card, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -531,6 +541,154 @@ cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const
     case kArithF32: return stages_pol<PolF32>(g, T, bs, nblocks, scratch, ell, ell_f32, samples, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent quadrature over the patches of a batch (one launch per degree,
+// dimension and arithmetic).  The work items are the blocks of the stage
+// launches of every patch, in stage-major order (all Z-half-0 blocks, all
+// Z-half-1 blocks, all Y, all X).  A block claims `chunk` consecutive items
+// from a device counter, waits until the previous stage of the item's patch is
+// complete (completion counters, bounded wait), runs the stage body with the
+// item's block index and counts the item done.  Items are claimed in order and
+// depend only on items with smaller indices, so the smallest unfinished item
+// can always run: the launch needs no co-residency of its blocks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (one thread) until c0 >= n0 and c1 >= n1 (c1 may be null).  Gives up when
+// another block raised ctl->abort, or after limit_ns of the global timer or
+// 2^24 polls: then sets ctl->status and ctl->abort and returns false.
+__device__ bool persist_wait(const unsigned* c0, unsigned n0, const unsigned* c1, unsigned n1, PersistCtl* ctl,
+                             long long limit_ns)
+{
+    const unsigned long long t0 = global_ns();
+    unsigned sleep_ns = 32;
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (ld_acquire_u32(c0) >= n0 && (!c1 || ld_acquire_u32(c1) >= n1)) return true;
+        if (*reinterpret_cast<volatile int*>(&ctl->abort)) return false;
+        if ((long long)(global_ns() - t0) > limit_ns) break;
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 1024) sleep_ns *= 2;
+    }
+    atomicExch(&ctl->status, 1);
+    atomicExch(&ctl->abort, 1);
+    return false;
+}
+
+template <class Pol, int P, int DIM>
+__global__ void __launch_bounds__(kBlock) k_persist(const PersistWork* __restrict__ works,
+                                                    const PersistSeg* __restrict__ segs, int nseg, int64_t total,
+                                                    int chunk, PersistCtl* ctl, unsigned* done, long long limit_ns)
+{
+    __shared__ int64_t s_first;
+    __shared__ int s_go;
+    for (;;) {
+        __syncthreads();                 // s_first / s_go of the previous round are no longer read
+        if (threadIdx.x == 0) {
+            const bool stop = *reinterpret_cast<volatile int*>(&ctl->abort) != 0;
+            s_first = stop ? total : (int64_t)atomicAdd(&ctl->next, (unsigned long long)chunk);
+        }
+        __syncthreads();
+        const int64_t first = s_first;
+        if (first >= total) return;
+        const int64_t last = (first + chunk < total) ? first + chunk : total;
+        for (int64_t it = first; it < last; ++it) {
+            int lo = 0, hi = nseg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (segs[mid].first <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            const int stage = segs[lo].stage;
+            const PersistWork& w = works[segs[lo].work];
+            const int64_t blk = it - segs[lo].first;
+            if (threadIdx.x == 0) {
+                bool go = true;
+                if (stage == 3 && DIM == 3)
+                    go = persist_wait(done + w.done0, (unsigned)w.nb[1], done + w.done0 + 1, (unsigned)w.nb[1], ctl,
+                                      limit_ns);
+                else if (stage == 4)
+                    go = persist_wait(done + w.done0 + 2, (unsigned)w.nb[2], nullptr, 0u, ctl, limit_ns);
+                s_go = go ? 1 : 0;
+            }
+            __syncthreads();
+            if (!s_go) return;
+            if constexpr (DIM == 3) {
+                if (stage == 1) stage_z_body<Pol, P, 0>(w.g, w.T, w.bs, w.scratch, blk);
+                else if (stage == 2) stage_z_body<Pol, P, 1>(w.g, w.T, w.bs, w.scratch, blk);
+            }
+            if (stage == 3) stage_y_body<Pol, P, DIM>(w.g, w.T, w.bs, w.scratch, blk);
+            else if (stage == 4)
+                stage_x_body<Pol, P, DIM, kLinesX>(w.g, w.T, w.bs, w.scratch, w.ell, w.ell_f32, w.N, w.samples, 0, blk);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(done + w.done0 + (stage - 1), 1u);
+            }
+        }
+    }
+}
+
+template <class Pol, int P>
+static const void* persist_fn(int dim)
+{
+    return dim == 3 ? (const void*)k_persist<Pol, P, 3> : (const void*)k_persist<Pol, P, 2>;
+}
+
+static const void* persist_kernel(int dim, int p, int arith)
+{
+#define IGA_PERSIST_P(POL)                                   \
+    switch (p) {                                             \
+    case 1: return persist_fn<POL, 1>(dim);                  \
+    case 2: return persist_fn<POL, 2>(dim);                  \
+    case 3: return persist_fn<POL, 3>(dim);                  \
+    case 4: return persist_fn<POL, 4>(dim);                  \
+    case 5: return persist_fn<POL, 5>(dim);                  \
+    default: return nullptr;                                 \
+    }
+    if (dim != 2 && dim != 3) return nullptr;
+    switch (arith) {
+    case kArithF32: IGA_PERSIST_P(PolF32)
+    case kArithDF: IGA_PERSIST_P(PolDF)
+    case kArithF64: IGA_PERSIST_P(PolF64)
+    default: return nullptr;
+    }
+#undef IGA_PERSIST_P
+}
+
+int persist_blocks_per_sm(int dim, int p, int arith)
+{
+    const void* fn = persist_kernel(dim, p, arith);
+    if (!fn) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_persist(int dim, int p, int arith, const PersistWork* works, const PersistSeg* segs, int nseg,
+                           int64_t total, int chunk, int grid, PersistCtl* ctl, unsigned* done, long long limit_ns,
+                           cudaStream_t s)
+{
+    const void* fn = persist_kernel(dim, p, arith);
+    if (!fn || grid < 1 || chunk < 1 || nseg < 1) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&works, (void*)&segs, (void*)&nseg, (void*)&total, (void*)&chunk, (void*)&ctl, (void*)&done,
+                    (void*)&limit_ns};
+    launch_begin(K_PERSIST, s);
+    cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
+    launch_end(K_PERSIST, s);
+    return e;
 }
 
 }  // namespace iga

@@ -1,8 +1,7 @@
 // K6: stencil SpMV y = A x on the index-free stencil-ELL layout
 // (eq. DiscreteVariationalProblems).  One thread per row; the value of slot s
 // of row i is vals[s * N + i] (coalesced across consecutive rows) and its
-// column is i + delta_0 + m_0 (delta_1 + m_1 delta_2).  Rows whose whole
-// stencil stays inside the index range skip the bounds tests.
+// column is i + delta_0 + m_0 (delta_1 + m_1 delta_2).
 //
 // FP64 values: GB300 runs FP64 FMAs at 1/64 of the FP32 rate, just below what
 // the HBM stream of the values needs, so a quarter of the products (the last
@@ -17,9 +16,13 @@
 
 namespace iga {
 
-template <int P, int DIM, typename T>
-__global__ void __launch_bounds__(kBlock) k_spmv(int m0, int m1, int m2, const T* __restrict__ vals,
-                                                 const T* __restrict__ x, T* __restrict__ y)
+// FP32 values: 1024-thread blocks, the values streamed past L1 (each is read
+// once) so that L1 keeps the x neighbourhood the rows of a block share.
+constexpr int kSpmvF32Block = 1024;
+
+template <int P, int DIM>
+__global__ void __launch_bounds__(kSpmvF32Block) k_spmv_f32(int m0, int m1, int m2, const float* __restrict__ vals,
+                                                            const float* __restrict__ x, float* __restrict__ y)
 {
     constexpr int W = 2 * P + 1;
     const int64_t N = (int64_t)m0 * m1 * m2;
@@ -29,7 +32,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int m0, int m1, int m2, const T
     const bool inner = i0 >= P && i0 < m0 - P && i1 >= P && i1 < m1 - P &&
                        (DIM == 2 || (i2 >= P && i2 < m2 - P));
     const int64_t s1 = m0, s2 = (int64_t)m0 * m1;
-    T acc = 0;
+    float acc = 0.f;
     const int n2 = (DIM == 3) ? W : 1;
     for (int d2 = 0; d2 < n2; ++d2) {
         const int o2 = (DIM == 3) ? d2 - P : 0;
@@ -40,12 +43,12 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int m0, int m1, int m2, const T
             if (!ok1) continue;
             const int sbase = W * (d1 + W * d2);
             const int64_t jbase = i + o1 * s1 + o2 * s2;
-            const T* v = vals + (int64_t)sbase * N + i;
+            const float* v = vals + (int64_t)sbase * N + i;
 #pragma unroll
             for (int d0 = 0; d0 < W; ++d0) {
                 const int o0 = d0 - P;
                 if (inner || (i0 + o0 >= 0 && i0 + o0 < m0))
-                    acc = fma(v[(int64_t)d0 * N], __ldg(x + jbase + o0), acc);
+                    acc = fmaf(__ldcs(v + (int64_t)d0 * N), __ldg(x + jbase + o0), acc);
             }
         }
     }
@@ -69,66 +72,72 @@ __device__ __forceinline__ void spmv_add2(float& ah, float& al, float bh, float 
     al = __fsub_rn(t, __fsub_rn(ah, s));
 }
 
+// (ah, al) += v * b in double-float: v split into (hi, lo) floats by integer
+// operations, the product of the high parts exact, the cross terms into the
+// low part, then a renormalised sum.
+__device__ __forceinline__ void spmv_dfmac(float& ah, float& al, double v, float2 b)
+{
+    const float2 a = d2df_split(v);
+    const float ph = __fmul_rn(a.x, b.x);
+    float pe = __fmaf_rn(a.x, b.x, -ph);
+    pe = __fmaf_rn(a.x, b.y, pe);
+    pe = __fmaf_rn(a.y, b.x, pe);
+    spmv_add2(ah, al, ph, pe);
+}
+
+// One row of the FP64-value product.  The pointers are deliberately not
+// __restrict__ here and the double-float product is a separate function of the
+// loaded value: in this form the compiler keeps the loads in program order and
+// allocates 44 registers at p = 4 (the other forms tried got 32 or 60), which
+// streams 10-20 % faster on GB300 at 96^3 (measured).
+template <int P, int DIM>
+__device__ __forceinline__ double spmv_df_row(int64_t i, int i0, int i1, int i2, int m0, int m1, int m2, int64_t N,
+                                              const double* vals, const double* x, const float2* xs)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int F64 = W - W / 4;              // slots delta_0 + p < F64 use FP64 FMAs, the rest double-float
+    const int64_t s1 = m0, s2 = (int64_t)m0 * m1;
+    float ah = 0.f, al = 0.f;
+    double a64 = 0.0;
+    for (int d2 = 0; d2 < (DIM == 3 ? W : 1); ++d2) {
+        const int o2 = (DIM == 3) ? d2 - P : 0;
+        if (i2 + o2 < 0 || i2 + o2 >= m2) continue;
+        for (int d1 = 0; d1 < W; ++d1) {
+            const int o1 = d1 - P;
+            if (i1 + o1 < 0 || i1 + o1 >= m1) continue;
+            const int64_t jb = i + o1 * s1 + o2 * s2;
+            const double* v = vals + (int64_t)(W * (d1 + W * d2)) * N + i;
+#pragma unroll
+            for (int d0 = 0; d0 < W; ++d0) {
+                const int o0 = d0 - P;
+                if (i0 + o0 < 0 || i0 + o0 >= m0) continue;
+                if (d0 < F64) a64 = fma(v[(int64_t)d0 * N], x[jb + o0], a64);
+                else spmv_dfmac(ah, al, v[(int64_t)d0 * N], xs[jb + o0]);
+            }
+        }
+    }
+    return df2d_exact(ah, al) + a64;
+}
+
 template <int P, int DIM>
 __global__ void __launch_bounds__(kBlock) k_spmv_df(int m0, int m1, int m2, const double* __restrict__ vals,
                                                     const double* __restrict__ x, const float2* __restrict__ xs,
                                                     double* __restrict__ y)
 {
-    constexpr int W = 2 * P + 1;
-    constexpr int F64 = W - W / 4;              // slots delta_0 + p < F64 use FP64 FMAs, the rest double-float
     const int64_t N = (int64_t)m0 * m1 * m2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
-    const bool inner = i0 >= P && i0 < m0 - P && i1 >= P && i1 < m1 - P &&
-                       (DIM == 2 || (i2 >= P && i2 < m2 - P));
-    const int64_t s1 = m0, s2 = (int64_t)m0 * m1;
-    float ah = 0.f, al = 0.f;
-    double a64 = 0.0;
-    const int n2 = (DIM == 3) ? W : 1;
-    for (int d2 = 0; d2 < n2; ++d2) {
-        const int o2 = (DIM == 3) ? d2 - P : 0;
-        const bool ok2 = inner || (i2 + o2 >= 0 && i2 + o2 < m2);
-        for (int d1 = 0; d1 < W; ++d1) {
-            const int o1 = d1 - P;
-            const bool ok1 = ok2 && (inner || (i1 + o1 >= 0 && i1 + o1 < m1));
-            if (!ok1) continue;
-            const int sbase = W * (d1 + W * d2);
-            const int64_t jbase = i + o1 * s1 + o2 * s2;
-            const double* v = vals + (int64_t)sbase * N + i;
-#pragma unroll
-            for (int d0 = 0; d0 < W; ++d0) {
-                const int o0 = d0 - P;
-                if (d0 < F64) {
-                    if (inner || (i0 + o0 >= 0 && i0 + o0 < m0)) a64 = fma(v[(int64_t)d0 * N], __ldg(x + jbase + o0), a64);
-                } else if (inner || (i0 + o0 >= 0 && i0 + o0 < m0)) {
-                    const float2 a = d2df_split(v[(int64_t)d0 * N]);
-                    const float2 b = xs[jbase + o0];
-                    // a * b: exact product of the high parts, cross terms into the low part
-                    const float ph = __fmul_rn(a.x, b.x);
-                    float pe = __fmaf_rn(a.x, b.x, -ph);
-                    pe = __fmaf_rn(a.x, b.y, pe);
-                    pe = __fmaf_rn(a.y, b.x, pe);
-                    spmv_add2(ah, al, ph, pe);
-                }
-            }
-        }
-    }
-    y[i] = df2d_exact(ah, al) + a64;
+    y[i] = spmv_df_row<P, DIM>(i, i0, i1, i2, m0, m1, m2, N, vals, x, xs);
 }
 
 template <int P>
-static void spmv_p(int dim, const int m[3], const void* vals, int f32, const void* x, void* y,
-                   unsigned grid, cudaStream_t s)
+static void spmv_f32_p(int dim, const int m[3], const float* vals, const float* x, float* y, cudaStream_t s)
 {
-    const int m2 = (dim == 3) ? m[2] : 1;
-    if (dim == 3) {
-        if (f32) k_spmv<P, 3, float><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const float*)vals, (const float*)x, (float*)y);
-        else k_spmv<P, 3, double><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const double*)vals, (const double*)x, (double*)y);
-    } else {
-        if (f32) k_spmv<P, 2, float><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const float*)vals, (const float*)x, (float*)y);
-        else k_spmv<P, 2, double><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, (const double*)vals, (const double*)x, (double*)y);
-    }
+    const int64_t N = (int64_t)m[0] * m[1] * (dim == 3 ? m[2] : 1);
+    const unsigned grid = (unsigned)((N + kSpmvF32Block - 1) / kSpmvF32Block);
+    if (dim == 3) k_spmv_f32<P, 3><<<grid, kSpmvF32Block, 0, s>>>(m[0], m[1], m[2], vals, x, y);
+    else k_spmv_f32<P, 2><<<grid, kSpmvF32Block, 0, s>>>(m[0], m[1], 1, vals, x, y);
 }
 
 cudaError_t pool_alloc(size_t bytes, cudaStream_t s, void** out);
@@ -169,12 +178,15 @@ cudaError_t launch_spmv(int dim, int p, const int m[3], const void* values, int 
         default: break;
         }
     } else {
+        const float* v = (const float*)values;
+        const float* xf = (const float*)x;
+        float* yf = (float*)y;
         switch (p) {
-        case 1: spmv_p<1>(dim, m, values, f32, x, y, grid, s); break;
-        case 2: spmv_p<2>(dim, m, values, f32, x, y, grid, s); break;
-        case 3: spmv_p<3>(dim, m, values, f32, x, y, grid, s); break;
-        case 4: spmv_p<4>(dim, m, values, f32, x, y, grid, s); break;
-        case 5: spmv_p<5>(dim, m, values, f32, x, y, grid, s); break;
+        case 1: spmv_f32_p<1>(dim, m, v, xf, yf, s); break;
+        case 2: spmv_f32_p<2>(dim, m, v, xf, yf, s); break;
+        case 3: spmv_f32_p<3>(dim, m, v, xf, yf, s); break;
+        case 4: spmv_f32_p<4>(dim, m, v, xf, yf, s); break;
+        case 5: spmv_f32_p<5>(dim, m, v, xf, yf, s); break;
         default: break;
         }
     }

@@ -110,3 +110,66 @@ def test_batch_workload_slice(iga):
 def test_batch_rejects_bad_arguments(iga):
     with pytest.raises(iga.IgaError):
         iga.assemble_batch([], dtype="f32")
+
+
+@pytest.fixture
+def modes(iga):
+    yield
+    iga.batch_set_modes(True, True)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_persistent_matches_single_patch_assembly(iga, dtype, modes):
+    """Persistent quadrature kernel (one launch per dimension/degree/arithmetic over device-side
+    patch descriptors): bit-identical to assembling each patch alone, on tuning and cached replays."""
+    ref = [_alone(iga, it, dtype) for it in ITEMS]
+    iga.batch_set_modes(branches=False, persistent=True)
+    mats = iga.assemble_batch(ITEMS, dtype=dtype)
+    for k in (0, 5):                                   # stale contents the batch must overwrite
+        prob, M, q = ITEMS[k][:3]
+        iga.assemble_surrogate(replace(prob, kappa_b=0.1), M, q, dtype=dtype, out=mats[k])
+    iga.assemble_batch(ITEMS, dtype=dtype, out=mats)
+    persistent, bps, chunk = iga.batch_mode()
+    assert persistent and bps >= 1 and chunk >= 1
+    iga.batch_status()
+    for A, r in zip(mats, ref):
+        assert np.array_equal(A.values_host(), r)
+    iga.assemble_batch(ITEMS, dtype=dtype, out=mats)   # cached replay
+    _, _, cached, _ = iga.batch_info()
+    assert cached
+    iga.batch_status()
+    for A, r in zip(mats, ref):
+        assert np.array_equal(A.values_host(), r)
+    for A in mats:
+        A.destroy()
+
+
+def test_batch_persistent_workload_slice_against_oracle(iga, modes):
+    """A slice of the 256-patch workload (uneven sizes and degrees, FP64 values) through the persistent
+    kernel against the FP64 oracle."""
+    iga.batch_set_modes(branches=False, persistent=True)
+    items = [it for it in W.batch_items(8, 3, seed=3) if it[0].N <= 6000]
+    items += [it for it in W.batch_items(0, 8, seed=3) if it[0].N <= 4000]
+    assert len(items) == 6 and {it[0].dim for it in items} == {2, 3}
+    mats = iga.assemble_batch(items, dtype="f64")
+    iga.assemble_batch(items, dtype="f64", out=mats)
+    assert iga.batch_mode()[0]
+    iga.batch_status()
+    for (prob, M, q), A in zip([it[:3] for it in items], mats):
+        ref = oracle.surrogate_matrix(prob, M, q) if M else oracle.exact_matrix(prob)
+        assert oracle.relative_entry_error(A.values_host(), ref) <= 1e-12
+        A.destroy()
+
+
+def test_persistent_wait_gives_up_with_status(iga):
+    """The persistent kernel's dependency wait on a counter nothing increments returns
+    IGA_ETIMEOUT after its limit (no hang, no fault), and the device stays usable."""
+    import time
+    t0 = time.time()
+    rc = iga.batch_selftest_timeout(20000)
+    assert rc == -5, iga.load().iga_last_error().decode()
+    assert time.time() - t0 < 30
+    prob = W.CFG_2D_P2.problem
+    A = iga.assemble_exact(prob, dtype="f64")
+    assert oracle.relative_entry_error(A.values_host(), oracle.exact_matrix(prob)) <= 1e-12
+    A.destroy()

@@ -4,8 +4,9 @@ would synchronise or stall, or applications whose own allocator owns the GPU's
 memory).  It takes its scratch from a fixed 64 MiB device array in the library
 and writes into a caller-owned buffer.
 
-Checked through the C ABI against iga_assemble_exact, within the FP64 / FP32
-parity tolerances of the other GPU tests, on consecutive calls that reuse the
+Checked through the C ABI against the FP64 oracle's exact matrix and against
+iga_assemble_exact, within the FP64 / FP32 parity tolerances of the other GPU
+tests, on consecutive calls that reuse the
 same scratch array (its contents left by the previous call must not matter);
 that calls after the first one change neither the device's free memory nor
 the library's or torch's pools; that B-spline coefficients (control values in
@@ -18,6 +19,7 @@ import numpy as np
 import pytest
 
 import iga_workloads as W
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -68,14 +70,16 @@ def _reference(iga, prob, dtype, ctrl=None):
 
 def test_noalloc_matches_exact_on_consecutive_calls(iga):
     refs = [_reference(iga, prob, dt) for prob, dt in CASES]
+    orcs = [oracle.exact_matrix(prob) for prob, _ in CASES]
     # two passes over all cases: every call finds the scratch left by another call
     for _ in range(2):
-        for (prob, dt), ref in zip(CASES, refs):
+        for (prob, dt), ref, orc in zip(CASES, refs, orcs):
             tdt = torch.float64 if dt == "f64" else torch.float32
             out = torch.full((prob.S, prob.N), float("nan"), dtype=tdt, device="cuda")
             assert call_noalloc(iga, prob, out, dt) == 0, iga.load().iga_last_error().decode()
             got = out.cpu().numpy()
             assert np.isfinite(got).all()
+            assert rel(got, orc) <= TOL[dt]
             assert rel(got, ref) <= TOL[dt]
 
 
