@@ -56,8 +56,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
+    # the largest translation units first, so that the longest compiles overlap the rest
+    srcs = sorted(sources(), key=lambda f: -os.path.getsize(f))
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, sources()))
+        objs = list(ex.map(compile_one, srcs))
     tmp = SO + f".tmp{os.getpid()}"
     cmd = [exe] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)

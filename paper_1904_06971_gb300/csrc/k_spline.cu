@@ -447,19 +447,26 @@ __global__ void __launch_bounds__(kBlock) k_fill_common(Geo g, SplinePlan sp, Sp
 // block stages in shared memory the partially evaluated field of every
 // interpolated slot at its own line (upper entries, Phi~_delta at x~_i) and at
 // the neighbouring line of each lower slot (Phi~_{-delta} at x~_j), plus the
-// direction-0 evaluation table.  Thread (ty, x0) then takes row x0 and the
-// offset pairs (delta_1, delta_2) number ty, ty + Y, ...: for each pair it
-// writes the 2p+1 slots delta_0 = -p..p (consecutive rows of one slot are
-// contiguous), gathering the frame columns, with the upper evaluation row held
-// in registers, and sums the row for the diagonal.  FP64 values: the
-// interpolant in double-float, converted by integer operations (df2d_exact),
-// the row sum in renormalised double-float (interpolated entries) and FP64
-// (frame entries, a minority), the Y partial sums of a row added in FP64.
-// FP32 values: FP32 evaluation and a compensated FP32 row sum.
+// direction-0 evaluation table.  The line's rows are cut into chunks of 32 and
+// each warp owns one chunk (lane = row) and a share of the offset pairs
+// (delta_1, delta_2): everything that depends on the pair or on the slot --
+// frame or interpolated column block, upper or lower slot, partial row -- is
+// the same for all lanes, so the warp never diverges except at the two ends
+// of the line.  For each pair it writes the 2p+1 slots delta_0 = -p..p
+// (consecutive rows of one slot are contiguous: coalesced), gathering the frame
+// columns, and adds the row sum for the diagonal.  FP64 values: the interpolant
+// in double-float (the first product starts the sum exactly), converted with
+// one FP64 add of the two exactly converted halves (measured faster than the
+// integer-only df2d_exact here, although the adds keep GB300's FP64 pipe ~60 %
+// busy); the row sum in renormalised
+// double-float (interpolated entries) and FP64 (frame entries, a minority); the
+// warps' partial sums of a row added in FP64 in a fixed order.  FP32 values:
+// FP32 evaluation and a compensated FP32 row sum.
 constexpr int kFillLineThreads = 512;
+constexpr int kFillLineWarps = kFillLineThreads / 32;
 
 struct FillLineSmem {
-    int U, nu0, R0, XR, Y;
+    int U, nu0, R0, nch, wpc;
     size_t bytes;
 };
 __host__ __device__ inline FillLineSmem fill_line_smem(int S, int first, int nu0, int R0, int Q1)
@@ -468,9 +475,9 @@ __host__ __device__ inline FillLineSmem fill_line_smem(int S, int first, int nu0
     f.U = S - first;
     f.nu0 = nu0;
     f.R0 = R0;
-    f.XR = R0 < kFillLineThreads ? R0 : kFillLineThreads;
-    f.Y = kFillLineThreads / f.XR;
-    // partial rows (upper, lower), evaluation table, spans (padded to 16 bytes), two doubles per thread
+    f.nch = (R0 + 31) / 32;                                   // chunks of 32 rows
+    f.wpc = f.nch > 0 ? kFillLineWarps / f.nch : 0;           // warps per chunk (0: too long a line)
+    // partial rows (upper, lower), evaluation table [R0][Q1], spans (padded to 16 bytes), two doubles per thread
     f.bytes = ((size_t)2 * f.U * nu0 + (size_t)Q1 * R0) * sizeof(float2) + (size_t)((R0 + 3) / 4) * 16 +
               (size_t)kFillLineThreads * 2 * sizeof(double);
     return f;
@@ -487,8 +494,160 @@ __device__ __forceinline__ void df_add2(float& ah, float& al, float bh, float bl
     al = __fsub_rn(t, __fsub_rn(ah, s));
 }
 
+// sum_k E[k] row[k] in double-float: the first product exactly, then PolDF::mac
+template <int Q1>
+__device__ __forceinline__ DFAcc fill_eval_df(const float2* E, const float2* row)
+{
+    DFAcc acc;
+    acc.h = __fmul_rn(E[0].x, row[0].x);
+    float pe = __fmaf_rn(E[0].x, row[0].x, -acc.h);
+    pe = __fmaf_rn(E[0].x, row[0].y, pe);
+    acc.l = __fmaf_rn(E[0].y, row[0].x, pe);
+#pragma unroll
+    for (int k = 1; k < Q1; ++k) PolDF::mac(acc, E[k], row[k]);
+    return acc;
+}
+
 template <int P, int DIM, typename T, int Q1>
 __global__ void __launch_bounds__(kFillLineThreads) k_fill_line(Geo g, SplinePlan sp, SplineBufs sb, T* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    constexpr int NPAIR = (DIM == 3) ? W * W : W;
+    extern __shared__ __align__(16) unsigned char fl_smem[];
+    const int R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
+    const int R2 = (DIM == 3) ? sp.r1[2] - sp.r0[2] + 1 : 1;
+    const int first = sp.first;
+    const bool kp = first > C;                     // kernel-preserving: the diagonal is minus the row sum
+    const FillLineSmem f = fill_line_smem(S, first, sp.nu[0], R0, Q1);
+    const int nu0 = f.nu0, U = f.U;
+    float2* sPu = reinterpret_cast<float2*>(fl_smem);
+    float2* sPl = sPu + (size_t)U * nu0;
+    float2* sE = sPl + (size_t)U * nu0;            // [x0][k]
+    int* sSp = reinterpret_cast<int*>(sE + (size_t)Q1 * R0);
+    double* sD = reinterpret_cast<double*>(fl_smem + (f.bytes - (size_t)kFillLineThreads * 2 * sizeof(double)));
+    const int x1 = (int)(blockIdx.x % (unsigned)R1), x2 = (int)(blockIdx.x / (unsigned)R1);
+    const int tid = threadIdx.x;
+    const int L0 = sp.L[0][P], L1x = sp.Lmax[1], L2x = (DIM == 3) ? sp.Lmax[2] : 1;
+    const int64_t slot_stride = (int64_t)L2x * L1x * nu0;
+    // stage the partial-field rows, the evaluation table and the spans
+    for (int idx = tid; idx < U * nu0; idx += kFillLineThreads) {
+        const int u = idx / nu0, a = idx - u * nu0;
+        sPu[idx] = sb.partial[(int64_t)u * slot_stride + ((int64_t)x2 * L1x + x1) * nu0 + a];
+        const int sl = S - 1 - first - u;          // lower slot whose mirror is u
+        const int d1 = (sl / W) % W, d2 = (DIM == 3) ? sl / (W * W) : P;
+        const int y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;
+        if (y1 >= 0 && y1 < R1 && y2 >= 0 && y2 < R2)
+            sPl[idx] = sb.partial[(int64_t)u * slot_stride + ((int64_t)y2 * L1x + y1) * nu0 + a];
+    }
+    for (int idx = tid; idx < Q1 * R0; idx += kFillLineThreads) {
+        const int x0 = idx / Q1, k = idx - x0 * Q1;
+        sE[idx] = sb.eval0[P][(int64_t)k * L0 + x0];
+    }
+    for (int x0 = tid; x0 < R0; x0 += kFillLineThreads) sSp[x0] = sb.espan[0][P][x0];
+    __syncthreads();
+
+    const int m0 = g.m[0], m1 = g.m[1];
+    const int64_t N = (int64_t)m0 * m1 * ((DIM == 3) ? g.m[2] : 1);
+    const int i1 = sp.r0[1] + x1, i2 = (DIM == 3) ? sp.r0[2] + x2 : 0;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wpc = f.wpc, ch = warp / wpc, wi = warp - ch * wpc;
+    const bool wact = ch < f.nch;                  // warps past nch * wpc idle
+    const int x0 = ch * 32 + lane;
+    const bool act = wact && x0 < R0;
+    const int x0c = act ? x0 : 0;
+    const int64_t i = sp.r0[0] + x0 + (int64_t)m0 * (i1 + (int64_t)m1 * i2);
+    float dh = 0.f, dl = 0.f;                      // double-float / compensated FP32 row sum
+    double dframe = 0.0;                           // FP64 sum of gathered frame entries (FP64 values)
+    if (wact) {
+        const int sp0 = sSp[x0c];
+        float2 Eu[Q1];                             // direction-0 evaluation row of the upper entries (at x~_i)
+#pragma unroll
+        for (int k = 0; k < Q1; ++k) Eu[k] = sE[x0c * Q1 + k];
+        for (int pr = wi; pr < NPAIR; pr += wpc) {
+            const int d1 = pr % W, d2 = (DIM == 3) ? pr / W : P;
+            const int y1 = x1 + d1 - P, y2 = (DIM == 3) ? x2 + d2 - P : 0;
+            const bool in12 = y1 >= 0 && y1 < R1 && y2 >= 0 && y2 < R2;
+            const int sbase = W * (d1 + W * ((DIM == 3) ? d2 : 0));
+            // frame columns of the pair (the exact A_ji of frame row j), all loads issued before the
+            // pair's stores: they read frame rows, which this kernel never writes
+            const int64_t jb = i - P + (int64_t)m0 * ((d1 - P) + (int64_t)m1 * (d2 - P));
+            T gv[W];
+#pragma unroll
+            for (int d0 = 0; d0 < W; ++d0) {
+                const int y0 = x0 + d0 - P;
+                const bool gat = act && !(in12 && y0 >= 0 && y0 < R0) && !(kp && sbase + d0 == C);
+                gv[d0] = gat ? vals[(int64_t)(S - 1 - sbase - d0) * N + jb + d0] : (T)0;
+            }
+#pragma unroll
+            for (int d0 = 0; d0 < W; ++d0) {
+                const int s = sbase + d0;
+                if (kp && s == C) continue;
+                const int y0 = x0 + d0 - P;
+                T out;
+                if (in12 && y0 >= 0 && y0 < R0) {
+                    // upper slot: this line's partial row at x~_i; lower slot: the mirror's at x~_j
+                    const bool upper = s >= first;
+                    const int y0c = act ? y0 : 0;
+                    const float2* row = upper ? sPu + (size_t)(s - first) * nu0 + sp0
+                                              : sPl + (size_t)(S - 1 - s - first) * nu0 + sSp[y0c];
+                    float2 E[Q1];
+#pragma unroll
+                    for (int k = 0; k < Q1; ++k) E[k] = upper ? Eu[k] : sE[y0c * Q1 + k];
+                    if constexpr (sizeof(T) == 4) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int k = 0; k < Q1; ++k) acc = __fmaf_rn(E[k].x, row[k].x, acc);
+                        out = acc;
+                        const float t = __fadd_rn(dh, acc);
+                        const float z = __fsub_rn(t, dh);
+                        dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(acc, z)));
+                        dh = t;
+                    } else {
+                        const DFAcc acc = fill_eval_df<Q1>(E, row);
+                        out = f2d_exact(acc.h) + f2d_exact(acc.l);
+                        if (kp) df_add2(dh, dl, acc.h, acc.l);
+                    }
+                } else {
+                    out = gv[d0];
+                    if constexpr (sizeof(T) == 4) {
+                        const float v = (float)out;
+                        const float t = __fadd_rn(dh, v);
+                        const float z = __fsub_rn(t, dh);
+                        dl = __fadd_rn(dl, __fadd_rn(__fsub_rn(dh, __fsub_rn(t, z)), __fsub_rn(v, z)));
+                        dh = t;
+                    } else {
+                        dframe += (double)out;
+                    }
+                }
+                if (act) vals[(int64_t)s * N + i] = out;
+            }
+        }
+    }
+    if (kp) {
+        // the partial sums of a row (one per warp of its chunk), added in a fixed order by the chunk's first warp
+        if (sizeof(T) == 4) { sD[2 * tid] = (double)dh; sD[2 * tid + 1] = (double)dl; }
+        else { sD[2 * tid] = df2d_exact(dh, dl); sD[2 * tid + 1] = dframe; }
+        __syncthreads();
+        if (act && wi == 0) {
+            double sum = 0.0, lo = 0.0;
+            for (int w = 0; w < wpc; ++w) {
+                const int t = (ch * wpc + w) * 32 + lane;
+                sum += sD[2 * t];
+                lo += sD[2 * t + 1];
+            }
+            vals[(int64_t)C * N + i] = (T)(-(sum + lo));
+        }
+    }
+}
+
+// FP32 values: the same pass with thread (ty, x0) taking row x0 of the line and
+// the offset pairs ty, ty + Y, ... (evaluation table [k][x0]).  For FP32 values
+// it is faster than the warp-per-chunk kernel above (1.10 against 1.42 ms at
+// 96^3 p = 4); for FP64 values slower (2.73 against 2.50 ms).
+template <int P, int DIM, typename T, int Q1>
+__global__ void __launch_bounds__(kFillLineThreads) k_fill_line_rows(Geo g, SplinePlan sp, SplineBufs sb, T* vals)
 {
     constexpr int W = 2 * P + 1;
     constexpr int S = (DIM == 3) ? W * W * W : W * W;
@@ -500,6 +659,7 @@ __global__ void __launch_bounds__(kFillLineThreads) k_fill_line(Geo g, SplinePla
     const bool kp = first > C;                     // kernel-preserving: the diagonal is minus the row sum
     const FillLineSmem f = fill_line_smem(S, first, sp.nu[0], R0, Q1);
     const int nu0 = f.nu0, U = f.U;
+    const int XR = R0 < kFillLineThreads ? R0 : kFillLineThreads, Y = kFillLineThreads / XR;
     float2* sPu = reinterpret_cast<float2*>(fl_smem);
     float2* sPl = sPu + (size_t)U * nu0;
     float2* sE = sPl + (size_t)U * nu0;
@@ -529,7 +689,6 @@ __global__ void __launch_bounds__(kFillLineThreads) k_fill_line(Geo g, SplinePla
     const int m0 = g.m[0], m1 = g.m[1];
     const int64_t N = (int64_t)m0 * m1 * ((DIM == 3) ? g.m[2] : 1);
     const int i1 = sp.r0[1] + x1, i2 = (DIM == 3) ? sp.r0[2] + x2 : 0;
-    const int XR = f.XR, Y = f.Y;
     const int ty = tid / XR, tx = tid - ty * XR;
     for (int xb = 0; xb < R0; xb += XR) {
         const int x0 = xb + tx;
@@ -628,18 +787,23 @@ static bool fill_line_launch(const Geo& g, const SplinePlan& sp, const SplineBuf
     const int R0 = sp.r1[0] - sp.r0[0] + 1, R1 = sp.r1[1] - sp.r0[1] + 1;
     const int R2 = (DIM == 3) ? sp.r1[2] - sp.r0[2] + 1 : 1;
     const FillLineSmem f = fill_line_smem(S, sp.first, sp.nu[0], R0, Q1);
-    if (f.bytes > (size_t)160 * 1024) return false;
+    constexpr bool rows = sizeof(T) == 4;
+    if (f.bytes > (size_t)160 * 1024 || (!rows && f.wpc < 1)) return false;
     static bool attr_set = false;          // the attribute is idempotent; setting it twice is harmless
     if (!attr_set) {
         // set once outside any stream capture (a capture then uses the fallback kernels until then)
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-        if (cudaFuncSetAttribute(k_fill_line<P, DIM, T, Q1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 160 * 1024) != cudaSuccess)
+        const void* fn = nullptr;
+        if constexpr (rows) fn = (const void*)k_fill_line_rows<P, DIM, T, Q1>;
+        else fn = (const void*)k_fill_line<P, DIM, T, Q1>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) != cudaSuccess)
             return false;
         attr_set = true;
     }
-    k_fill_line<P, DIM, T, Q1><<<(unsigned)((int64_t)R1 * R2), kFillLineThreads, f.bytes, s>>>(g, sp, sb, vals);
+    const unsigned grid = (unsigned)((int64_t)R1 * R2);
+    if constexpr (rows) k_fill_line_rows<P, DIM, T, Q1><<<grid, kFillLineThreads, f.bytes, s>>>(g, sp, sb, vals);
+    else k_fill_line<P, DIM, T, Q1><<<grid, kFillLineThreads, f.bytes, s>>>(g, sp, sb, vals);
     return true;
 }
 
@@ -657,37 +821,91 @@ static bool fill_line_q(const Geo& g, const SplinePlan& sp, const SplineBufs& sb
 
 // The kernel-preserving diagonal of the frame rows only (rows with an index
 // outside [r0, r1] in some direction), after k_fill_line wrote those of Omega~.
+// Thread t takes the t-th frame row: first the planes i2 outside [r0_2, r1_2],
+// then the lines i1 outside [r0_1, r1_1] of the other planes, then the rows i0
+// outside [r0_0, r1_0] of the remaining lines (consecutive threads take
+// consecutive rows of one line: coalesced), so that every thread of the grid has
+// a row (0.65 against 0.98 ms for a grid over all rows at 96^3 p = 4).  FP64
+// sums (splitting the values into double-float pairs by integer operations took
+// twice as long).
+struct FrameRows {
+    int m0, m1, m2;
+    int r0[3], r1[3];
+    int64_t nA, nB, nC;       // frame rows in the outer planes, outer lines, outer row runs
+};
+
+__device__ __forceinline__ int frame_index(int k, int lo, int hi)   // k-th index outside [lo, hi]
+{
+    return k < lo ? k : hi + 1 + (k - lo);
+}
+
 template <int P, int DIM, typename T>
-__global__ void __launch_bounds__(kBlock) k_diag_frame(int m0, int m1, int64_t N, int r0_0, int r1_0, int r0_1,
-                                                       int r1_1, int r0_2, int r1_2, T* vals)
+__global__ void __launch_bounds__(kBlock) k_diag_frame(FrameRows fr, T* vals)
 {
     constexpr int W = 2 * P + 1;
     constexpr int S = (DIM == 3) ? W * W * W : W * W;
     constexpr int C = (S - 1) / 2;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= fr.nA + fr.nB + fr.nC) return;
+    const int64_t plane = (int64_t)fr.m0 * fr.m1;
+    int i0, i1, i2;
+    if (t < fr.nA) {
+        i2 = frame_index((int)(t / plane), fr.r0[2], fr.r1[2]);
+        const int64_t r = t % plane;
+        i1 = (int)(r / fr.m0);
+        i0 = (int)(r % fr.m0);
+    } else if ((t -= fr.nA) < fr.nB) {
+        const int nb1 = fr.r0[1] + fr.m1 - 1 - fr.r1[1];
+        const int64_t per = (int64_t)nb1 * fr.m0;
+        i2 = fr.r0[2] + (int)(t / per);
+        const int64_t r = t % per;
+        i1 = frame_index((int)(r / fr.m0), fr.r0[1], fr.r1[1]);
+        i0 = (int)(r % fr.m0);
+    } else {
+        t -= fr.nB;
+        const int nc0 = fr.r0[0] + fr.m0 - 1 - fr.r1[0];
+        const int R1 = fr.r1[1] - fr.r0[1] + 1;
+        const int64_t line = t / nc0;
+        i2 = fr.r0[2] + (int)(line / R1);
+        i1 = fr.r0[1] + (int)(line % R1);
+        i0 = frame_index((int)(t % nc0), fr.r0[0], fr.r1[0]);
+    }
+    const int64_t N = plane * fr.m2;
+    const int64_t i = i0 + (int64_t)fr.m0 * (i1 + (int64_t)fr.m1 * i2);
+    // four interleaved partial sums keep more loads in flight; combined in a fixed order
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int s = 0; s < S; ++s)
+        if (s != C) part[s & 3] += (double)vals[(int64_t)s * N + i];
+    vals[(int64_t)C * N + i] = (T)(-((part[0] + part[1]) + (part[2] + part[3])));
+}
+
+// FP32 values: one thread per row of the whole patch, the rows of Omega~ leaving
+// at once (measured faster for FP32 values than the frame-row enumeration above,
+// 0.38 against 0.69 ms at 96^3 p = 4; for FP64 values the enumeration wins).
+template <int P, int DIM>
+__global__ void __launch_bounds__(kBlock) k_diag_frame_f32(FrameRows fr, float* vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    const int64_t N = (int64_t)fr.m0 * fr.m1 * fr.m2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
-    if (i0 >= r0_0 && i0 <= r1_0 && i1 >= r0_1 && i1 <= r1_1 && (DIM == 2 || (i2 >= r0_2 && i2 <= r1_2))) return;
-    if constexpr (sizeof(T) == 4) {
-        float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+    const int i0 = (int)(i % fr.m0), i1 = (int)((i / fr.m0) % fr.m1), i2 = (int)(i / ((int64_t)fr.m0 * fr.m1));
+    if (i0 >= fr.r0[0] && i0 <= fr.r1[0] && i1 >= fr.r0[1] && i1 <= fr.r1[1] && i2 >= fr.r0[2] && i2 <= fr.r1[2]) return;
+    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
 #pragma unroll 4
-        for (int s = 0; s < S; ++s) {
-            if (s == C) continue;
-            const float v = (float)vals[(int64_t)s * N + i];
-            const int k = s & 1;
-            const float t = __fadd_rn(hi[k], v);
-            const float z = __fsub_rn(t, hi[k]);
-            lo[k] = __fadd_rn(lo[k], __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(v, z)));
-            hi[k] = t;
-        }
-        vals[(int64_t)C * N + i] = (T)(-((double)hi[0] + (double)hi[1] + ((double)lo[0] + (double)lo[1])));
-    } else {
-        double part[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
-        for (int s = 0; s < S; ++s)
-            if (s != C) part[s & 3] += (double)vals[(int64_t)s * N + i];
-        vals[(int64_t)C * N + i] = (T)(-((part[0] + part[1]) + (part[2] + part[3])));
+    for (int s = 0; s < S; ++s) {
+        if (s == C) continue;
+        const float v = vals[(int64_t)s * N + i];
+        const int k = s & 1;
+        const float t = __fadd_rn(hi[k], v);
+        const float z = __fsub_rn(t, hi[k]);
+        lo[k] = __fadd_rn(lo[k], __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, z)), __fsub_rn(v, z)));
+        hi[k] = t;
     }
+    vals[(int64_t)C * N + i] = (float)(-((double)hi[0] + (double)hi[1] + ((double)lo[0] + (double)lo[1])));
 }
 
 template <int P, int DIM, typename T>
@@ -784,13 +1002,23 @@ static void fill_p(const Geo& g, const SplinePlan& sp, int empty_box, const Spli
     if (g.form == kFormMass) return;                  // mass matrix with an empty Omega~: all rows exact
     launch_begin(K_DIAG, s);
     if (line) {
-        const int r02 = g.dim == 3 ? sp.r0[2] : 0, r12 = g.dim == 3 ? sp.r1[2] : 0;
-        if (g.dim == 3) {
-            if (f32) k_diag_frame<P, 3, float><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (float*)ell);
-            else k_diag_frame<P, 3, double><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (double*)ell);
-        } else {
-            if (f32) k_diag_frame<P, 2, float><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (float*)ell);
-            else k_diag_frame<P, 2, double><<<gdiag, kBlock, 0, s>>>(g.m[0], g.m[1], N, sp.r0[0], sp.r1[0], sp.r0[1], sp.r1[1], r02, r12, (double*)ell);
+        FrameRows fr;
+        fr.m0 = g.m[0]; fr.m1 = g.m[1]; fr.m2 = g.dim == 3 ? g.m[2] : 1;
+        for (int d = 0; d < 3; ++d) {
+            fr.r0[d] = d < g.dim ? sp.r0[d] : 0;
+            fr.r1[d] = d < g.dim ? sp.r1[d] : 0;
+        }
+        const int64_t R[3] = {fr.r1[0] - fr.r0[0] + 1, fr.r1[1] - fr.r0[1] + 1, fr.r1[2] - fr.r0[2] + 1};
+        fr.nA = (int64_t)(fr.m2 - R[2]) * fr.m0 * fr.m1;
+        fr.nB = R[2] * (fr.m1 - R[1]) * fr.m0;
+        fr.nC = R[2] * R[1] * (fr.m0 - R[0]);
+        const unsigned gframe = (unsigned)((fr.nA + fr.nB + fr.nC + kBlock - 1) / kBlock);
+        if (f32) {
+            if (g.dim == 3) k_diag_frame_f32<P, 3><<<gdiag, kBlock, 0, s>>>(fr, (float*)ell);
+            else k_diag_frame_f32<P, 2><<<gdiag, kBlock, 0, s>>>(fr, (float*)ell);
+        } else if (gframe > 0) {
+            if (g.dim == 3) k_diag_frame<P, 3, double><<<gframe, kBlock, 0, s>>>(fr, (double*)ell);
+            else k_diag_frame<P, 2, double><<<gframe, kBlock, 0, s>>>(fr, (double*)ell);
         }
     } else if (g.dim == 3) {
         if (f32) k_diag<P, 3, float><<<gdiag, kBlock, 0, s>>>(N, (float*)ell);
