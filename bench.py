@@ -238,14 +238,19 @@ def alu_peak_tflops(pipe: str, sm_mhz: float) -> float:
     return 152 * per_clk * sm_mhz * 1e6 / 1e12
 
 
-def source_hash(rel_path: str) -> str:
-    with open(os.path.join(ROOT, rel_path), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def source_hash(rel_paths) -> str:
+    """Hash of the source files that define a kernel (a path or a list of paths)."""
+    h = hashlib.sha256()
+    for rel in ([rel_paths] if isinstance(rel_paths, str) else rel_paths):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-KERNEL_SOURCE = {"stage_z": "paper_1904_06971_gb300/csrc/k_quad.cu", "stage_y": "paper_1904_06971_gb300/csrc/k_quad.cu",
-                 "stage_x": "paper_1904_06971_gb300/csrc/k_quad.cu", "coef": "paper_1904_06971_gb300/csrc/k_tables.cu",
-                 "fill": "paper_1904_06971_gb300/csrc/k_spline.cu", "spmv": "paper_1904_06971_gb300/csrc/k_spmv.cu"}
+_CSRC = "paper_1904_06971_gb300/csrc/"
+_QUAD = [_CSRC + "quad_bodies.cuh", _CSRC + "k_quad.cu", _CSRC + "arith.cuh"]
+KERNEL_SOURCE = {"stage_z": _QUAD, "stage_y": _QUAD, "stage_x": _QUAD, "coef": _CSRC + "k_tables.cu",
+                 "fill": _CSRC + "k_spline.cu", "spmv": _CSRC + "k_spmv.cu"}
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -746,7 +751,10 @@ def run_gpu(args, wl):
     import paper_1904_06971_gb300 as iga
     iga.load()
     if args.arith:
-        iga.set_arithmetic("f64", args.arith)
+        # the contraction arithmetic of the workload's value type
+        if wl.dtype == "f64" and args.arith in ("fp32", "bf16x3"):
+            raise SystemExit("--arith fp32 / bf16x3 apply to FP32-value workloads")
+        iga.set_arithmetic(wl.dtype, args.arith)
     prob = wl.problem
     stream = torch.cuda.current_stream()
     primary = args.domains
@@ -987,8 +995,8 @@ def main(argv=None):
                     help="skip the FP32-tier and 64^3 p = 3 reports beside the headline")
     ap.add_argument("--cg-tol", type=float, default=1e-10)
     ap.add_argument("--cg-maxit", type=int, default=20000)
-    ap.add_argument("--arith", default=None, choices=["df64", "df64_tc", "fp64"],
-                    help="contraction arithmetic of FP64 values (default: the library's)")
+    ap.add_argument("--arith", default=None, choices=["df64", "df64_tc", "fp64", "fp32", "bf16x3"],
+                    help="contraction arithmetic of the workload's value type (default: the library's)")
     ap.add_argument("--domains", choices=["common", "per_offset"], default="common",
                     help="interpolation domains of the headline surrogate (the other is reported beside it)")
     ap.add_argument("--mode", choices=["both", "surrogate", "exact"], default="both",
