@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "dfmath.cuh"
+
 namespace iga {
 
 __device__ __forceinline__ int cubic_knot_pos(int j, int ne) { return j <= 3 ? 0 : (j >= ne + 3 ? ne : j - 3); }
@@ -31,6 +33,37 @@ __device__ __forceinline__ void cubic_open_basis(int ne, double x, int& first, d
             const double tmp = N[r] * (fne * rc);
             N[r] = saved + right[r + 1] * tmp;
             saved = left[k - r] * tmp;
+        }
+        N[k] = saved;
+    }
+    first = e;
+}
+
+// The same four values in double-float arithmetic on the FP32 pipe (dfmath.cuh):
+// in the scaled coordinate t = x ne the knots are the integers kp(j) and every
+// denominator of the recursion is 1, 2 or 3, so a step is a multiplication by
+// 1, 1/2 or 1/3 (the last as a double-float constant).  first comes from the
+// FP64 x exactly as in cubic_open_basis; x_df is x split into a float pair.
+__device__ __forceinline__ void cubic_open_basis_df(int ne, double x, df2 x_df, int& first, df2 N[4])
+{
+    int e = (int)(x * ne);
+    e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
+    const int mu = e + 3;
+    const df2 t = df_mul(x_df, df2{(float)ne, 0.f});
+    const df2 third = df2{0.333333343267f, -9.93410742e-09f};     // 1/3 = hi + lo
+    df2 left[4], right[4];
+    N[0] = df2{1.f, 0.f};
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+        left[k] = df_sub(t, df2{(float)cubic_knot_pos(mu + 1 - k, ne), 0.f});
+        right[k] = df_sub(df2{(float)cubic_knot_pos(mu + k, ne), 0.f}, t);
+        df2 saved = df2{0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < k; ++r) {
+            const int cnt = cubic_knot_pos(mu + r + 1, ne) - cubic_knot_pos(mu + 1 - k + r, ne);
+            const df2 tmp = cnt == 1 ? N[r] : (cnt == 2 ? df2{0.5f * N[r].h, 0.5f * N[r].l} : df_mul(N[r], third));
+            N[r] = df_add(saved, df_mul(right[r + 1], tmp));
+            saved = df_mul(left[k - r], tmp);
         }
         N[k] = saved;
     }

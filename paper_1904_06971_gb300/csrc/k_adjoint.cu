@@ -19,9 +19,13 @@
 // field w_g grad B_s^T G grad u_{w_s} with w_s = sum_delta Phibar_delta(s) e_{s+delta}
 // on the support of B_s.  Finally dL/dc_k = sum_g N_k(phi(g)) s(g).
 //
-// The basis tables are recomputed by every call; everything is FP64.
+// The basis tables are recomputed by every call.  The sum-factorised fields and
+// the geometry are FP64; the point field's gradients and quadratic forms and
+// the scatter to the control values (cubic basis and window sums) run in
+// double-float arithmetic on the FP32 pipe (GB300's FP64 pipe bounded them).
 #include <math_constants.h>
 
+#include "arith.cuh"
 #include "bspline3.cuh"
 #include "iga_internal.cuh"
 
@@ -158,36 +162,51 @@ __global__ void k_adj_pass1(Geo g, AdjTables T, const double* W0, double* W1)
         a1 += bv * W0[tot0 + o];
         a2 += bd * W0[o];
     }
-    W1[idx] = a0;
-    W1[tot + idx] = a1;
-    W1[2 * tot + idx] = a2;
+    // stored as double-float pairs (same 8 bytes) for the point field, which works in double-float
+    float2* W1f = reinterpret_cast<float2*>(W1);
+    W1f[idx] = d2df_split(a0);
+    W1f[tot + idx] = d2df_split(a1);
+    W1f[2 * tot + idx] = d2df_split(a2);
 }
 
-// gradient of u at point (g0, g1, g2) from its W1 array (3-D) or directly (2-D)
-__device__ __forceinline__ void adj_grad(const Geo& g, const AdjTables& T, const double* W1, int64_t tot1,
-                                         int g0, int g1, int g2, double* du)
+// gradient of u at point (g0, g1, g2) from its W1 array (3-D) or directly (2-D), in
+// double-float; bv2 / bd2 are the direction-2 basis values and derivatives at g2
+__device__ __forceinline__ void adj_grad_df(const Geo& g, const df2* bv2, const df2* bd2, const float2* W1,
+                                            int64_t tot1, int g0, int g1, int g2, df2* du)
 {
     const int Q = g.p + 1;
     const int G0 = g.n_el[0] * Q, G1 = g.n_el[1] * Q;
+    auto ld = [](float2 v) { return df2{v.x, v.y}; };
     if (g.dim == 2) {
         const int64_t o = (int64_t)g1 * G0 + g0;
-        du[0] = W1[tot1 + o];
-        du[1] = W1[2 * tot1 + o];
+        du[0] = ld(W1[tot1 + o]);
+        du[1] = ld(W1[2 * tot1 + o]);
         return;
     }
     const int e2 = g2 / Q;
-    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    df2 d0 = {0.f, 0.f}, d1 = {0.f, 0.f}, d2 = {0.f, 0.f};
     for (int c = 0; c < Q; ++c) {
         const int64_t o = ((int64_t)(e2 + c) * G1 + g1) * G0 + g0;
-        const double bv = T.bv[2][g2 * Q + c], bd = T.bd[2][g2 * Q + c];
-        d0 += bv * W1[tot1 + o];
-        d1 += bv * W1[2 * tot1 + o];
-        d2 += bd * W1[o];
+        d0 = df_add(d0, df_mul(bv2[c], ld(W1[tot1 + o])));
+        d1 = df_add(d1, df_mul(bv2[c], ld(W1[2 * tot1 + o])));
+        d2 = df_add(d2, df_mul(bd2[c], ld(W1[o])));
     }
     du[0] = d0; du[1] = d1; du[2] = d2;
 }
 
-// s(g) = w_g sum_t sign_t grad u_{a_t}^T G grad u_{b_t} at every Gauss point
+__device__ __forceinline__ df2 quad_form_df(int n, const df2 G[3][3], const df2* u, const df2* v)
+{
+    df2 s = {0.f, 0.f};
+    for (int a = 0; a < n; ++a) {
+        df2 t = {0.f, 0.f};
+        for (int b = 0; b < n; ++b) t = df_add(t, df_mul(G[a][b], v[b]));
+        s = df_add(s, df_mul(u[a], t));
+    }
+    return s;
+}
+
+// s(g) = w_g sum_t sign_t grad u_{a_t}^T G grad u_{b_t} at every Gauss point: the geometry in
+// FP64, the gradients and quadratic forms in double-float on the FP32 pipe
 __global__ void k_adj_points(Geo g, AdjTables T, AdjTerms terms, double* spt)
 {
     const int Q = g.p + 1;
@@ -208,14 +227,30 @@ __global__ void k_adj_points(Geo g, AdjTables T, AdjTerms terms, double* spt)
         w *= T.wq[d][gg[d]];
     }
     adj_geometry(g, xi, s1, c1, x, G);
-    double s = 0.0;
+    df2 Gd[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const float2 v = (a < g.dim && b < g.dim) ? d2df_split(G[a][b]) : make_float2(0.f, 0.f);
+            Gd[a][b] = df2{v.x, v.y};
+        }
+    df2 bv2[kMaxP + 1], bd2[kMaxP + 1];
+    if (g.dim == 3)
+        for (int c = 0; c < Q; ++c) {
+            const float2 v = d2df_split(T.bv[2][g2 * Q + c]), dd = d2df_split(T.bd[2][g2 * Q + c]);
+            bv2[c] = df2{v.x, v.y};
+            bd2[c] = df2{dd.x, dd.y};
+        }
+    df2 sacc = {0.f, 0.f};
     for (int t = 0; t < terms.n; ++t) {
-        double du[3] = {0, 0, 0}, dv[3] = {0, 0, 0};
-        adj_grad(g, T, terms.Wa[t], terms.tot1, g0, g1, g2, du);
-        adj_grad(g, T, terms.Wb[t], terms.tot1, g0, g1, g2, dv);
-        s += terms.sign[t] * quad_form(g.dim, G, du, dv);
+        df2 du[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, dv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        adj_grad_df(g, bv2, bd2, reinterpret_cast<const float2*>(terms.Wa[t]), terms.tot1, g0, g1, g2, du);
+        adj_grad_df(g, bv2, bd2, reinterpret_cast<const float2*>(terms.Wb[t]), terms.tot1, g0, g1, g2, dv);
+        const df2 q = quad_form_df(g.dim, Gd, du, dv);
+        sacc = df_add(sacc, terms.sign[t] < 0.0 ? df_neg(q) : q);
     }
-    spt[idx] = w * s;
+    const float2 ws = d2df_split(w);
+    const df2 r = df_mul(df2{ws.x, ws.y}, sacc);
+    spt[idx] = df2d_exact(r.h, r.l);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,7 +447,8 @@ constexpr int kStage = 64;
 __global__ void __launch_bounds__(32 * kScatterWarps) k_adj_scatter(Geo g, AdjTables T, const double* spt,
                                                                     double* grad)
 {
-    __shared__ double sN[kScatterWarps][kStage][13];   // s(g) then N0[4], N1[4], N2[4]
+    // s(g) then N0[4], N1[4], N2[4], as double-float pairs
+    __shared__ df2 sN[kScatterWarps][kStage][13];
     __shared__ int sO[kScatterWarps][kStage];          // window offsets o0 + 4 o1 + 16 o2, or -1
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int p = g.p, Q = p + 1, n = g.dim;
@@ -447,7 +483,9 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_adj_scatter(Geo g, AdjTa
             }
         }
         for (int d = 0; d < n; ++d) flo[d] = __reduce_min_sync(0xffffffffu, flo[d]);
-        double acc[5] = {0, 0, 0, 0, 0};
+        df2 acc[5];
+#pragma unroll
+        for (int ka = 0; ka < 5; ++ka) acc[ka] = df2{0.f, 0.f};
         for (int base = 0; base < npt; base += kStage) {
             __syncwarp();
             for (int tl = lane; tl < kStage; tl += 32) {
@@ -466,24 +504,35 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_adj_scatter(Geo g, AdjTa
                     adj_point(g, xi, s1, x);
                     const double sv = spt[gd[0] + (int64_t)G0 * (gd[1] + (int64_t)G1 * gd[2])];
                     int f[3] = {0, 0, 0};
-                    double N[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
+                    df2 N[3][4];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        N[d][0] = df2{1.f, 0.f};
+                        N[d][1] = N[d][2] = N[d][3] = df2{0.f, 0.f};
+                    }
                     bool inwin = true;
                     for (int d = 0; d < n; ++d) {
-                        cubic_open_basis(g.knc[d] - 3, fmin(fmax(x[d], 0.0), 1.0), f[d], N[d]);
+                        const double xc = fmin(fmax(x[d], 0.0), 1.0);
+                        const float2 xs = d2df_split(xc);
+                        cubic_open_basis_df(g.knc[d] - 3, xc, df2{xs.x, xs.y}, f[d], N[d]);
                         inwin = inwin && (f[d] - flo[d] <= 1);
                     }
                     if (inwin) {
                         o = (f[0] - flo[0]) + 4 * (f[1] - flo[1]) + 16 * (n == 3 ? f[2] - flo[2] : 0);
-                        sN[wid][tl][0] = sv;
+                        const float2 svs = d2df_split(sv);
+                        sN[wid][tl][0] = df2{svs.x, svs.y};
                         for (int d = 0; d < 3; ++d)
                             for (int a = 0; a < 4; ++a) sN[wid][tl][1 + 4 * d + a] = N[d][a];
                     } else {
+                        // a point outside the element's window: its 4^n contributions directly (rare)
                         const int cmax = (n == 3) ? 4 : 1;
                         for (int c = 0; c < cmax; ++c)
                             for (int b = 0; b < 4; ++b)
-                                for (int a = 0; a < 4; ++a)
+                                for (int a = 0; a < 4; ++a) {
+                                    const df2 w = df_mul(df_mul(N[0][a], N[1][b]), N[2][c]);
                                     atomicAdd(grad + (f[0] + a) + (int64_t)n0 * ((f[1] + b) + (int64_t)n1 * (f[2] + c)),
-                                              sv * N[0][a] * N[1][b] * N[2][c]);
+                                              sv * df2d_exact(w.h, w.l));
+                                }
                     }
                 }
                 sO[wid][tl] = o;
@@ -496,12 +545,12 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_adj_scatter(Geo g, AdjTa
                     if (o < 0) continue;
                     const int b = kb - ((o >> 2) & 3), c = kc - (o >> 4), o0 = o & 3;
                     if (b < 0 || b > 3 || c < 0 || c > 3) continue;
-                    const double* D = sN[wid][tl];
-                    const double w = D[0] * D[5 + b] * D[9 + c];
+                    const df2* D = sN[wid][tl];
+                    const df2 w = df_mul(df_mul(D[0], D[5 + b]), D[9 + c]);
 #pragma unroll
                     for (int ka = 0; ka < 5; ++ka) {
                         const int a = ka - o0;
-                        if (a >= 0 && a <= 3) acc[ka] += w * D[1 + a];
+                        if (a >= 0 && a <= 3) acc[ka] = df_add(acc[ka], df_mul(w, D[1 + a]));
                     }
                 }
             }
@@ -511,7 +560,8 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_adj_scatter(Geo g, AdjTa
             if (kbg < g.knc[1] && (n == 2 || kcg < g.knc[2]))
                 for (int ka = 0; ka < 5; ++ka) {
                     const int kag = flo[0] + ka;
-                    if (acc[ka] != 0.0 && kag < g.knc[0]) atomicAdd(grad + kag + (int64_t)n0 * (kbg + (int64_t)n1 * kcg), acc[ka]);
+                    if ((acc[ka].h != 0.f || acc[ka].l != 0.f) && kag < g.knc[0])
+                        atomicAdd(grad + kag + (int64_t)n0 * (kbg + (int64_t)n1 * kcg), df2d_exact(acc[ka].h, acc[ka].l));
                 }
         }
     }
