@@ -43,11 +43,12 @@ __device__ __forceinline__ void cubic_open_basis(int ne, double x, int& first, d
 // in the scaled coordinate t = x ne the knots are the integers kp(j) and every
 // denominator of the recursion is 1, 2 or 3, so a step is a multiplication by
 // 1, 1/2 or 1/3 (the last as a double-float constant).  first comes from the
-// FP64 x exactly as in cubic_open_basis; x_df is x split into a float pair.
-__device__ __forceinline__ void cubic_open_basis_df(int ne, double x, df2 x_df, int& first, df2 N[4])
+// FP64 x exactly as in cubic_open_basis (cubic_open_basis_df), or is given
+// (cubic_open_basis_df_span: a span chosen from a rounded x may be the
+// neighbouring one at a knot, where both pieces agree to C^2); x_df is x as a
+// float pair.
+__device__ __forceinline__ void cubic_open_basis_df_span(int ne, int e, df2 x_df, df2 N[4])
 {
-    int e = (int)(x * ne);
-    e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
     const int mu = e + 3;
     const df2 t = df_mul(x_df, df2{(float)ne, 0.f});
     const df2 third = df2{0.333333343267f, -9.93410742e-09f};     // 1/3 = hi + lo
@@ -67,6 +68,13 @@ __device__ __forceinline__ void cubic_open_basis_df(int ne, double x, df2 x_df, 
         }
         N[k] = saved;
     }
+}
+
+__device__ __forceinline__ void cubic_open_basis_df(int ne, double x, df2 x_df, int& first, df2 N[4])
+{
+    int e = (int)(x * ne);
+    e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
+    cubic_open_basis_df_span(ne, e, x_df, N);
     first = e;
 }
 

@@ -330,6 +330,7 @@ struct iga::Job {
     int64_t nblk[4] = {0, 0, 0, 0};
     int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3], o_Xs[3], o_tdf[3];
     int64_t o_gshift = -1, o_ex_lo = -1, o_ex_hi = -1, o_samples = 0, o_partial = 0, o_mid = 0;
+    int64_t o_kdf = -1, nctrl = 0;       // double-float copy of the B-spline coefficient's control values
     iga_matrix* A = nullptr;
     double* scratch = nullptr;
     double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
@@ -441,6 +442,12 @@ int job_plan(Job& J, const iga_patch_t* patch, int p, const iga_map_t* map, cons
         J.o_Xs[d] = (arith == kArithF64) ? J.o_X[d] : lay.take(nX);
         J.o_tdf[d] = lay.take(4 * G);
     }
+    if (g.kappa_kind == IGA_KAPPA_BSPLINE3 && arith != kArithF64 && form == kFormStiffness) {
+        J.nctrl = 1;
+        for (int d = 0; d < dim; ++d) J.nctrl *= g.knc[d];
+        J.o_kdf = lay.take(J.nctrl);                 // one float pair per control value
+        g.kctrl_split = 1;
+    }
     prepare_coef_df(g, arith);
     int64_t* nblk = J.nblk;
     bs.nb = (int)boxes.size();
@@ -528,6 +535,7 @@ void job_bind(Job& J, double* scratch)
     T.tc64 = J.tc64;
     T.gshift = J.tc64 ? reinterpret_cast<const int*>(P(J.o_gshift)) : nullptr;
     J.samples = J.do_spline ? P(J.o_samples) : nullptr;
+    J.g.kctrl_df = J.o_kdf >= 0 ? reinterpret_cast<const float2*>(P(J.o_kdf)) : nullptr;
     memset(&J.sb, 0, sizeof(J.sb));
     if (J.do_spline) {
         spline_bufs(scratch, J.sp, J.slo, J.sb);
@@ -540,6 +548,10 @@ cudaError_t job_pre_impl(Job& J, cudaStream_t st, const char** stage)
 {
     *stage = "basis tables";
     cudaError_t ce = launch_basis(J.g, J.gx, J.sx, J.cx, J.bv, J.bd, J.wq, J.tdf, st);
+    if (ce == cudaSuccess && J.o_kdf >= 0) {
+        *stage = "coefficient control values";
+        ce = launch_split_ctrl(J.g.kctrl, J.nctrl, reinterpret_cast<float2*>(J.scratch + J.o_kdf), st);
+    }
     if (ce == cudaSuccess) { *stage = "pair tables"; ce = launch_pairs(J.g, J.bv, J.bd, J.wq, J.X, J.Xs, J.arith, st); }
     if (ce == cudaSuccess && J.tc64) {
         *stage = "tensor-core stage X set-up";

@@ -26,6 +26,8 @@ struct Geo {
     double poly[64];
     int knc[3];               // IGA_KAPPA_BSPLINE3: control values per direction
     const double* kctrl;      // IGA_KAPPA_BSPLINE3: control values (device)
+    const float2* kctrl_df;   // IGA_KAPPA_BSPLINE3: the same as double-float pairs (scratch), or null
+    int kctrl_split;          // the assembly provides kctrl_df (set before prepare_coef_df)
     // double-float copies (hi, lo) of amp, ka, kb for the double-float coefficient path
     float amp_df[2], ka_df[2], kb_df[2];
     int coef_df;              // evaluate the coefficient tensor in double-float arithmetic
@@ -229,8 +231,12 @@ cudaError_t launch_basis(const Geo& g, double* gx[3], double* sx[3], double* cx[
 
 // Fill the double-float copies of the map / coefficient constants and decide
 // whether the coefficient tensor can be evaluated in double-float arithmetic
-// (sine-product map with |amp| <= 0.07, kappa constant / SIN2D / EXPSIN3D with |b| <= 1).
+// (sine-product map with |amp| <= 0.07, kappa constant / SIN2D / EXPSIN3D with
+// |b| <= 1, or BSPLINE3 when g.kctrl_split says the assembly provides kctrl_df).
 void prepare_coef_df(Geo& g, int arith);
+// The double-float copy of the B-spline coefficient's control values (n values) for the
+// double-float coefficient path (k_tables.cu).
+cudaError_t launch_split_ctrl(const double* ctrl, int64_t n, float2* out, cudaStream_t s);
 cudaError_t launch_pairs(const Geo& g, double* const bv[3], double* const bd[3],
                          double* const wq[3], double* X[3], void* Xs[3], int arith, cudaStream_t s);
 cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t nblocks,

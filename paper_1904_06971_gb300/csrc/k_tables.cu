@@ -272,6 +272,56 @@ __device__ double kappa_at(const Geo& g, const double* x)
     }
 }
 
+// kappa at the physical point x (double-float) for IGA_KAPPA_BSPLINE3: the cubic
+// basis per direction in double-float and the 4^n control values from their
+// double-float copy.
+__device__ df2 kappa_bspline_df(const Geo& g, const df2* x)
+{
+    int f[3] = {0, 0, 0};
+    df2 N[3][4];
+    for (int d = 0; d < 3; ++d) {
+        N[d][0] = df2{1.f, 0.f};
+        N[d][1] = N[d][2] = N[d][3] = df2{0.f, 0.f};
+    }
+    for (int d = 0; d < g.dim; ++d) {
+        const int ne = g.knc[d] - 3;
+        df2 xc = x[d];
+        if (xc.h <= 0.f) xc = df2{0.f, 0.f};
+        else if (xc.h >= 1.f) xc = df2{1.f, 0.f};
+        int e = (int)(xc.h * (float)ne);
+        e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
+        cubic_open_basis_df_span(ne, e, xc, N[d]);
+        f[d] = e;
+    }
+    const int n0 = g.knc[0], n1 = g.knc[1];
+    const int nc2 = (g.dim == 3) ? 4 : 1;
+    df2 v = {0.f, 0.f};
+    for (int c = 0; c < nc2; ++c)
+        for (int b = 0; b < 4; ++b) {
+            const float2* row = g.kctrl_df + f[0] + (int64_t)n0 * ((f[1] + b) + (int64_t)n1 * (f[2] + c));
+            df2 r = df_mul(df2{row[0].x, row[0].y}, N[0][0]);
+#pragma unroll
+            for (int a = 1; a < 4; ++a) r = df_fma(df2{row[a].x, row[a].y}, N[0][a], r);
+            v = df_fma(df_mul(N[1][b], N[2][c]), r, v);
+        }
+    return v;
+}
+
+__global__ void k_split_ctrl(const double* ctrl, int64_t n, float2* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = d2df_split(ctrl[i]);
+}
+
+cudaError_t launch_split_ctrl(const double* ctrl, int64_t n, float2* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    launch_begin(K_COEF, s);
+    k_split_ctrl<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(ctrl, n, out);
+    launch_end(K_COEF, s);
+    return cudaGetLastError();
+}
+
 template <int DIM, class Pol>
 __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, double* scratch)
 {
@@ -428,7 +478,15 @@ __global__ void __launch_bounds__(kBlock) k_coef(Geo g, Tables T, BoxSet bs, dou
         const df2 cc = df_div(amp, det);
         const df2 c2g = df_mul(df_mul(cc, cc), gg2);
         df2 kap = df2{g.ka_df[0], g.ka_df[1]};
-        if (g.kappa_kind == IGA_KAPPA_SIN2D || g.kappa_kind == IGA_KAPPA_EXPSIN3D) {
+        if (g.kappa_kind == IGA_KAPPA_BSPLINE3) {
+            // the physical point x_a = xi_a + amp P, then the spline
+            df2 x[3];
+            for (int a = 0; a < DIM; ++a) {
+                const float2 xs = d2df_split(xi[a]);
+                x[a] = df_fma(amp, P, df2{xs.x, xs.y});
+            }
+            kap = kappa_bspline_df(g, x);
+        } else if (g.kappa_kind == IGA_KAPPA_SIN2D || g.kappa_kind == IGA_KAPPA_EXPSIN3D) {
             const df2 th = df_add(amp, amp);
             df2 st, ct;
             df_sincospi_small(df_mul(th, P), st, ct);
@@ -552,7 +610,8 @@ void prepare_coef_df(Geo& g, int arith)
     split(g.ka, g.ka_df);
     split(g.kb, g.kb_df);
     const bool kappa_ok = g.kappa_kind == IGA_KAPPA_CONST || g.kappa_kind == IGA_KAPPA_SIN2D ||
-                          (g.kappa_kind == IGA_KAPPA_EXPSIN3D && fabs(g.kb) <= 1.0);
+                          (g.kappa_kind == IGA_KAPPA_EXPSIN3D && fabs(g.kb) <= 1.0) ||
+                          (g.kappa_kind == IGA_KAPPA_BSPLINE3 && g.kctrl_split);
     g.coef_df = (arith != kArithF64 && g.map_kind == IGA_MAP_SINPROD && fabs(g.amp) <= 0.07 && kappa_ok) ? 1 : 0;
 }
 

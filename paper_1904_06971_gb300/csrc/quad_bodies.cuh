@@ -375,24 +375,51 @@ __device__ __forceinline__ void stage_x_body(const Geo& g, const Tables& T, cons
         const int e1 = i1 - P + a;
         if (e1 < b.elo[0] || e1 >= b.elo[0] + b.E[0]) continue;
         const int64_t o = (int64_t)(e1 - b.elo[0]) * Q;
-        __align__(16) S v[LINES][4][Q];
+        if constexpr (Pol::kind == kArithF32) {
+            __align__(16) S v[LINES][4][Q];
 #pragma unroll
-        for (int l = 0; l < LINES; ++l)
+            for (int l = 0; l < LINES; ++l)
 #pragma unroll
-            for (int gr = 0; gr < 4; ++gr) load_run<S, Q>(T2[l] + gr * gs + o, v[l][gr]);
+                for (int gr = 0; gr < 4; ++gr) load_run<S, Q>(T2[l] + gr * gs + o, v[l][gr]);
 #pragma unroll
-        for (int r = 0; r < Q; ++r) {
-            const int t = a * Q + r;
+            for (int r = 0; r < Q; ++r) {
+                const int t = a * Q + r;
 #pragma unroll
-            for (int dd = a; dd <= a + P; ++dd) {
-                S x00, x01, x10, x11;
-                load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+                for (int dd = a; dd <= a + P; ++dd) {
+                    S x00, x01, x10, x11;
+                    load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
 #pragma unroll
-                for (int l = 0; l < LINES; ++l) {
-                    Pol::mac(acc[l][dd], x11, v[l][0][r]);   // group 0: pattern 11
-                    Pol::mac(acc[l][dd], x10, v[l][1][r]);   // group 1: pattern 10
-                    Pol::mac(acc[l][dd], x01, v[l][2][r]);   // group 2: pattern 01
-                    Pol::mac(acc[l][dd], x00, v[l][3][r]);   // group 3: pattern 00
+                    for (int l = 0; l < LINES; ++l) {
+                        Pol::mac(acc[l][dd], x11, v[l][0][r]);   // group 0: pattern 11
+                        Pol::mac(acc[l][dd], x10, v[l][1][r]);   // group 1: pattern 10
+                        Pol::mac(acc[l][dd], x01, v[l][2][r]);   // group 2: pattern 01
+                        Pol::mac(acc[l][dd], x00, v[l][3][r]);   // group 3: pattern 00
+                    }
+                }
+            }
+        } else {
+            // double-float and FP64 bodies are ~12x longer per multiply-add: with the Gauss-point
+            // loop unrolled too the kernel outgrew the instruction cache (ncu: "no instruction" the
+            // largest stall), so it stays rolled and the T2 values are loaded per point
+#pragma unroll 1
+            for (int r = 0; r < Q; ++r) {
+                const int t = a * Q + r;
+                S v[LINES][4];
+#pragma unroll
+                for (int l = 0; l < LINES; ++l)
+#pragma unroll
+                    for (int gr = 0; gr < 4; ++gr) v[l][gr] = T2[l][gr * gs + o + r];
+#pragma unroll
+                for (int dd = a; dd <= a + P; ++dd) {
+                    S x00, x01, x10, x11;
+                    load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
+#pragma unroll
+                    for (int l = 0; l < LINES; ++l) {
+                        Pol::mac(acc[l][dd], x11, v[l][0]);   // group 0: pattern 11
+                        Pol::mac(acc[l][dd], x10, v[l][1]);   // group 1: pattern 10
+                        Pol::mac(acc[l][dd], x01, v[l][2]);   // group 2: pattern 01
+                        Pol::mac(acc[l][dd], x00, v[l][3]);   // group 3: pattern 00
+                    }
                 }
             }
         }
