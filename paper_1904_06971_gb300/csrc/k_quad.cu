@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_stage_z_f32(Geo g, Tables T, BoxS
 }
 
 template <class Pol, int P, int DIM>
-__global__ void __launch_bounds__(kBlock) k_stage_y(Geo g, Tables T, BoxSet bs, double* scratch)
+__global__ void __launch_bounds__(kBlock, DIM == 3 ? 2 : 1) k_stage_y(Geo g, Tables T, BoxSet bs, double* scratch)
 {
     stage_y_body<Pol, P, DIM>(g, T, bs, scratch, blockIdx.x);
 }

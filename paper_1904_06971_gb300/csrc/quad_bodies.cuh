@@ -131,13 +131,20 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
             }
         }
         } else {
+            // the rolled Gauss-point loop loads the next point's fields before this point's
+            // multiply-adds, so that their latency overlaps the arithmetic
+            auto load_c = [&](int r, S& c0, S& c1, S& c2, S& c3) {
+                const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + r) * plane + pp;
+                if (HALF == 0) { c0 = C[o]; c1 = C[fs + o]; c2 = C[3 * fs + o]; c3 = C[2 * fs + o]; }
+                else { c0 = C[2 * fs + o]; c1 = C[4 * fs + o]; c2 = C[5 * fs + o]; c3 = c0; }
+            };
+            S n0, n1, n2, n3;
+            load_c(0, n0, n1, n2, n3);
 #pragma unroll 1
         for (int r = 0; r < Q; ++r) {
             const int t = a * Q + r;
-            const int64_t o = (int64_t)((e3 - b.elo[2]) * Q + r) * plane + pp;
-            S c0, c1, c2, c3;
-            if (HALF == 0) { c0 = C[o]; c1 = C[fs + o]; c2 = C[3 * fs + o]; c3 = C[2 * fs + o]; }
-            else { c0 = C[2 * fs + o]; c1 = C[4 * fs + o]; c2 = C[5 * fs + o]; c3 = c0; }
+            const S c0 = n0, c1 = n1, c2 = n2, c3 = n3;
+            if (r + 1 < Q) load_c(r + 1, n0, n1, n2, n3);
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
                 S x00, x01, x10, x11;
@@ -242,13 +249,24 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
             }
         }
         } else {
+            // the next Gauss point's inputs are loaded before this point's multiply-adds
+            S nv[NIN];
+            {
+                const int64_t o = (int64_t)((e2 - b.elo[1]) * Q) * G0;
+#pragma unroll
+                for (int f = 0; f < NIN; ++f) nv[f] = in[f * fstride + o];
+            }
 #pragma unroll 1
         for (int r = 0; r < Q; ++r) {
             const int t = a * Q + r;
-            const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + r) * G0;
             S v[NIN];
 #pragma unroll
-            for (int f = 0; f < NIN; ++f) v[f] = in[f * fstride + o];
+            for (int f = 0; f < NIN; ++f) v[f] = nv[f];
+            if (r + 1 < Q) {
+                const int64_t o = (int64_t)((e2 - b.elo[1]) * Q + r + 1) * G0;
+#pragma unroll
+                for (int f = 0; f < NIN; ++f) nv[f] = in[f * fstride + o];
+            }
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
                 S x00, x01, x10, x11;
