@@ -62,7 +62,7 @@ thread_local bool t_capture = false;        // inside a graph capture: no profil
 const char* kNames[K_NUM] = {"basis", "pairs", "coef", "stage_z", "stage_y", "stage_x",
                              "spline_setup", "spline_solve", "spline_partial", "fill", "spmv", "diag", "cg",
                              "adj_fields", "adj_points", "adj_interp", "adj_samples", "adj_scatter", "stage_x_tc",
-                             "manufactured", "persist"};
+                             "manufactured", "persist", "mirror"};
 
 cudaEvent_t take_event()
 {
@@ -331,6 +331,10 @@ struct iga::Job {
     int64_t o_gx[3], o_sx[3], o_cx[3], o_wq[3], o_bv[3], o_bd[3], o_X[3], o_Xs[3], o_tdf[3];
     int64_t o_gshift = -1, o_ex_lo = -1, o_ex_hi = -1, o_samples = 0, o_partial = 0, o_mid = 0;
     int64_t o_kdf = -1, nctrl = 0;       // double-float copy of the B-spline coefficient's control values
+    // mirror passes of the symmetric boxes: rows [begin, begin + count), +1 lower from upper, -1 upper from lower
+    int n_mirror = 0;
+    int64_t mir_begin[2] = {0, 0}, mir_count[2] = {0, 0};
+    int mir_dir[2] = {0, 0};
     iga_matrix* A = nullptr;
     double* scratch = nullptr;
     double *gx[3], *sx[3], *cx[3], *wq[3], *bv[3], *bd[3], *X[3];
@@ -455,6 +459,30 @@ int job_plan(Job& J, const iga_patch_t* patch, int p, const iga_map_t* map, cons
     const int tc64 = (form == kFormStiffness && dtype == IGA_F64) ? current_tc(dtype) : 0;
     J.tc64 = tc64;
     if (tc64) J.o_gshift = lay.take(2);
+    // The stiffness matrix is symmetric: boxes whose rows' partners i + delta on one side are rows of
+    // the same box compute the other half of the offsets only, and a mirror pass copies the rest.
+    // Exact (or a surrogate without Omega~): the whole patch (upper offsets).  Surrogate: the two
+    // frame slabs normal to the slowest direction -- the low slab computes its upper offsets (every
+    // lower partner lies in the slab), the high slab its lower ones.  Not with the tensor-core
+    // stage X, which writes every offset of its rows.
+    const bool sym_ok = form == kFormStiffness && !tc64 && !(dtype == IGA_F32 && current_tc(dtype));
+    if (sym_ok && (!surrogate || J.empty)) {
+        boxes[0].sym = 1;
+        J.n_mirror = 1;
+        J.mir_begin[0] = 0; J.mir_count[0] = N; J.mir_dir[0] = 1;
+    } else if (sym_ok && surrogate && !J.empty && boxes.size() >= 2) {
+        // boxes[0], boxes[1]: the slabs below and above Omega~ in the slowest direction, full in the others
+        const int64_t plane = (dim == 3) ? (int64_t)g.m[0] * g.m[1] : (int64_t)g.m[0];
+        boxes[0].sym = 1;
+        boxes[1].sym = -1;
+        J.n_mirror = 2;
+        J.mir_begin[0] = (int64_t)boxes[0].rlo[dim - 1] * plane;
+        J.mir_count[0] = (int64_t)boxes[0].R[dim - 1] * plane;
+        J.mir_dir[0] = 1;
+        J.mir_begin[1] = (int64_t)boxes[1].rlo[dim - 1] * plane;
+        J.mir_count[1] = (int64_t)boxes[1].R[dim - 1] * plane;
+        J.mir_dir[1] = -1;
+    }
     for (int k = 0; k < bs.nb; ++k) {
         Box& b = boxes[k];
         b.out_kind = 0;
@@ -574,7 +602,12 @@ cudaError_t job_quad_impl(Job& J, cudaStream_t st, const char** stage)
 cudaError_t job_post_impl(Job& J, cudaStream_t st, const char** stage)
 {
     cudaError_t ce = cudaSuccess;
-    if (J.do_spline) { *stage = "spline interpolation"; ce = launch_spline(J.g, J.sp, J.samples, J.sb, st); }
+    for (int k = 0; k < J.n_mirror && ce == cudaSuccess; ++k) {
+        *stage = "mirror of the symmetric matrix";
+        ce = launch_mirror(J.g.dim, J.g.p, J.g.m, J.A->values, J.dtype == IGA_F32, J.mir_begin[k], J.mir_count[k],
+                           J.mir_dir[k], st);
+    }
+    if (J.do_spline && ce == cudaSuccess) { *stage = "spline interpolation"; ce = launch_spline(J.g, J.sp, J.samples, J.sb, st); }
     if (J.surrogate && ce == cudaSuccess) {
         *stage = "surrogate fill";
         ce = launch_fill(J.g, J.sp, J.empty, J.sb, J.A->values, J.dtype == IGA_F32, st);

@@ -48,6 +48,12 @@ struct Box {
     int64_t t1_off, t2_off;   // offsets (doubles) of the stage intermediates
     int64_t blk[4];           // first block of this box in the K2 / Z / Y / X launches
     int64_t ex_off;           // offset (doubles) of the per-line exponents of T2 (tensor-core FP64 stage X), or -1
+    // The stiffness matrix is symmetric (A_ij = A_ji).  sym = +1: the stages compute only the
+    // upper offsets of the box's rows (colexicographic slot >= the centre: delta_n > 0, or
+    // delta_n = 0 and the next component > 0, ...), -1: only the lower ones (slot <= the centre),
+    // and a mirror pass copies the rest from the partner rows (which must be rows of the same
+    // kind); 0: every offset.
+    int sym;
 };
 
 constexpr int kMaxBoxes = 7;
@@ -105,6 +111,7 @@ __device__ __forceinline__ void get_box(const BoxSet& bs, int dim, int p, int st
         }
         b.out_kind = 1;
         b.ex_off = -1;
+        b.sym = 0;
         b.sample_id = sid;
         b.c_off = bs.s_c_off + sid * bs.s_c_len;
         b.t1_off = bs.s_t1_off + sid * bs.s_t1_len;
@@ -134,7 +141,7 @@ struct Tables {
 enum KernelId {
     K_BASIS = 0, K_PAIRS, K_COEF, K_STAGE_Z, K_STAGE_Y, K_STAGE_X,
     K_SPLINE_SETUP, K_SPLINE_SOLVE, K_SPLINE_PARTIAL, K_FILL, K_SPMV, K_DIAG, K_SOLVE,
-    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_MMS, K_PERSIST, K_NUM
+    K_ADJ_FIELDS, K_ADJ_POINTS, K_ADJ_INTERP, K_ADJ_SAMPLES, K_ADJ_SCATTER, K_STAGE_X_TC, K_MMS, K_PERSIST, K_MIRROR, K_NUM
 };
 
 // Launch bookkeeping (iga_api.cu): counts launches and, when profiling is on,
@@ -243,6 +250,12 @@ cudaError_t launch_coef(const Geo& g, const Tables& T, const BoxSet& bs, int64_t
                         double* scratch, cudaStream_t s);
 cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const int64_t nblocks[4],
                           double* scratch, void* ell, int ell_f32, double* samples, cudaStream_t s);
+// Mirror of a symmetric matrix over the rows row_begin .. row_begin + count - 1: dir = +1 fills
+// every slot below the centre from the partner's upper slot, values[s][i] = values[S-1-s][i + delta_s];
+// dir = -1 fills the slots above the centre from the partner's lower slot (0 where i + delta_s lies
+// outside the index range).
+cudaError_t launch_mirror(int dim, int p, const int m[3], void* values, int f32, int64_t row_begin,
+                          int64_t count, int dir, cudaStream_t s);
 // Stage X of the cardinal rows of the explicit boxes on the tensor cores: FP32
 // values (BF16 parts, FP32 accumulation) or, with T.tc64, FP64 values (six
 // BF16 digits, products accumulated exactly per level); p = 2..5; *used =

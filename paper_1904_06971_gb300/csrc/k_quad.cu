@@ -126,4 +126,63 @@ cudaError_t launch_stages(const Geo& g, const Tables& T, const BoxSet& bs, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mirror of a symmetric matrix (A_ij = A_ji) over a range of rows whose stages
+// computed one half of the offsets: dir = +1 fills slot s below the centre of
+// row i from the mirrored slot S-1-s of row j = i + delta_s, dir = -1 the slots
+// above the centre the same way; 0 when j lies outside the index range.  One
+// thread per (row, slot); consecutive threads take consecutive rows.
+// ---------------------------------------------------------------------------
+template <int P, int DIM, typename T>
+__global__ void __launch_bounds__(kBlock) k_mirror(int m0, int m1, int m2, int64_t row_begin, int64_t count, int dir,
+                                                   T* __restrict__ vals)
+{
+    constexpr int W = 2 * P + 1;
+    constexpr int S = (DIM == 3) ? W * W * W : W * W;
+    constexpr int C = (S - 1) / 2;
+    const int64_t N = (int64_t)m0 * m1 * m2;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    const int64_t i = row_begin + r;
+    const int s = dir > 0 ? (int)blockIdx.y : C + 1 + (int)blockIdx.y;     // the slot written
+    const int o0 = s % W - P, o1 = (s / W) % W - P, o2 = (DIM == 3) ? s / (W * W) - P : 0;
+    const int i0 = (int)(i % m0), i1 = (int)((i / m0) % m1), i2 = (int)(i / ((int64_t)m0 * m1));
+    const bool in = i0 + o0 >= 0 && i0 + o0 < m0 && i1 + o1 >= 0 && i1 + o1 < m1 && i2 + o2 >= 0 && i2 + o2 < m2;
+    const int64_t j = i + o0 + (int64_t)m0 * (o1 + (int64_t)m1 * o2);
+    vals[(int64_t)s * N + i] = in ? vals[(int64_t)(S - 1 - s) * N + j] : (T)0;
+}
+
+template <int P>
+static void mirror_p(int dim, const int m[3], void* values, int f32, int64_t row_begin, int64_t count, int dir,
+                     cudaStream_t s)
+{
+    const int W = 2 * P + 1;
+    const int S = (dim == 3) ? W * W * W : W * W;
+    const dim3 grid((unsigned)((count + kBlock - 1) / kBlock), (unsigned)((S - 1) / 2));
+    const int m2 = (dim == 3) ? m[2] : 1;
+    if (dim == 3) {
+        if (f32) k_mirror<P, 3, float><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, row_begin, count, dir, (float*)values);
+        else k_mirror<P, 3, double><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, row_begin, count, dir, (double*)values);
+    } else {
+        if (f32) k_mirror<P, 2, float><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, row_begin, count, dir, (float*)values);
+        else k_mirror<P, 2, double><<<grid, kBlock, 0, s>>>(m[0], m[1], m2, row_begin, count, dir, (double*)values);
+    }
+}
+
+cudaError_t launch_mirror(int dim, int p, const int m[3], void* values, int f32, int64_t row_begin,
+                          int64_t count, int dir, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    launch_begin(K_MIRROR, s);
+    switch (p) {
+    case 1: mirror_p<1>(dim, m, values, f32, row_begin, count, dir, s); break;
+    case 2: mirror_p<2>(dim, m, values, f32, row_begin, count, dir, s); break;
+    case 3: mirror_p<3>(dim, m, values, f32, row_begin, count, dir, s); break;
+    case 4: mirror_p<4>(dim, m, values, f32, row_begin, count, dir, s); break;
+    case 5: mirror_p<5>(dim, m, values, f32, row_begin, count, dir, s); break;
+    default: break;
+    }
+    launch_end(K_MIRROR, s);
+    return cudaGetLastError();
+}
 }  // namespace iga

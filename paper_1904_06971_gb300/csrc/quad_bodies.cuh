@@ -115,6 +115,7 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
             else { c0 = C[2 * fs + o]; c1 = C[4 * fs + o]; c2 = C[5 * fs + o]; c3 = c0; }
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
+                if ((b.sym > 0 && dd < P) || (b.sym < 0 && dd > P)) continue;   // symmetric: one sign of delta_2
                 S x00, x01, x10, x11;
                 load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
                 if (HALF == 0) {
@@ -147,6 +148,7 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
             if (r + 1 < Q) load_c(r + 1, n0, n1, n2, n3);
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
+                if ((b.sym > 0 && dd < P) || (b.sym < 0 && dd > P)) continue;   // symmetric: one sign of delta_2
                 S x00, x01, x10, x11;
                 load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
                 if (HALF == 0) {
@@ -170,7 +172,8 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
     for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
-            T1[((int64_t)(4 * HALF + k) * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
+            if (!((b.sym > 0 && dd < P) || (b.sym < 0 && dd > P)))
+                T1[((int64_t)(4 * HALF + k) * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -194,6 +197,11 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
     const int64_t g0 = item % G0;
     const int i2l = (int)((item / G0) % R2);
     const int64_t pair3 = item / (G0 * R2);
+    // symmetric box: lines of the other sign of delta_2 are not needed; with delta_2 = 0 only one
+    // sign of delta_1 (cut_lo: delta_1 >= 0, cut_hi: delta_1 <= 0)
+    const int dz = (DIM == 3) ? (int)(pair3 % W) : P;
+    if ((b.sym > 0 && dz < P) || (b.sym < 0 && dz > P)) return;
+    const bool cut_lo = b.sym > 0 && dz == P, cut_hi = b.sym < 0 && dz == P;
     const int i2 = b.rlo[1] + i2l;
     const S* Xi = reinterpret_cast<const S*>(T.Xs[1]) + (int64_t)i2 * W * TT * 4;
 
@@ -228,6 +236,7 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
             for (int f = 0; f < NIN; ++f) v[f] = in[f * fstride + o];
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
+                if ((cut_lo && dd < P) || (cut_hi && dd > P)) continue;
                 S x00, x01, x10, x11;
                 load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
                 if (DIM == 3) {
@@ -269,6 +278,7 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
             }
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
+                if ((cut_lo && dd < P) || (cut_hi && dd > P)) continue;
                 S x00, x01, x10, x11;
                 load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
                 if (DIM == 3) {
@@ -297,7 +307,8 @@ __device__ __forceinline__ void stage_y_body(const Geo& g, const Tables& T, cons
     for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
-            T2[(((int64_t)k * P3 + pair3) * P2 + (int64_t)i2l * W + dd) * G0 + g0] = Pol::to_store(acc[dd][k]);
+            if (!((cut_lo && dd < P) || (cut_hi && dd > P)))
+                T2[(((int64_t)k * P3 + pair3) * P2 + (int64_t)i2l * W + dd) * G0 + g0] = Pol::to_store(acc[dd][k]);
     if constexpr (Pol::kind == kArithDF) {
         if (T.tc64 && b.out_kind == 0 && b.ex_off >= 0) {
             // largest exponent of each T2 line (pair3, i2l W + dd), the groups shifted by sigma_g, for the
@@ -373,11 +384,23 @@ __device__ __forceinline__ void stage_x_body(const Geo& g, const Tables& T, cons
     const int i1 = (i1l < nlo) ? b.rlo[0] + i1l : hi0 + (i1l - nlo);
     const int i3 = (DIM == 3) ? b.rlo[2] + (int)(pair3 / W) : 0;
     const int d3 = (DIM == 3) ? (int)(pair3 % W) : 0;
+    // symmetric box: only the upper (sym = +1) or lower (-1) offsets
+    const int dz = (DIM == 3) ? d3 : P;
+    if ((b.sym > 0 && dz < P) || (b.sym < 0 && dz > P)) return;
     const bool card = has_card && i1 >= 2 * P && i1 <= m0 - 2 * P - 1;
     const S* Xi = card ? sX : X0 + (int64_t)i1 * W * TT * 4;
     const int64_t gs = P3 * P2 * G0;        // group stride
     int nl = (int)(P2 - lg * LINES);
     if (nl > LINES) nl = LINES;
+    if (b.sym != 0 && dz == P) {
+        // lines of the other sign of delta_1 are mirrored: nothing to do when all of this thread's are
+        bool any = false;
+        for (int l = 0; l < nl; ++l) {
+            const int d = (int)((lg * LINES + l) % W);
+            any = any || (b.sym > 0 ? d >= P : d <= P);
+        }
+        if (!any) return;
+    }
     const S* T2[LINES];
 #pragma unroll
     for (int l = 0; l < LINES; ++l)
@@ -449,16 +472,20 @@ __device__ __forceinline__ void stage_x_body(const Geo& g, const Tables& T, cons
         const int i2 = b.rlo[1] + (int)(pair2 / W);
         const int d2 = (int)(pair2 % W);
         const int slot0 = W * (d2 + W * d3);
+        if (b.sym != 0 && dz == P && (b.sym > 0 ? d2 < P : d2 > P)) continue;   // mirrored line
+        // the centre line: one sign of delta_0
+        const int dlo = (b.sym > 0 && dz == P && d2 == P) ? P : 0;
+        const int dhi = (b.sym < 0 && dz == P && d2 == P) ? P : W - 1;
         if (b.out_kind == 0) {
             const int64_t row = i1 + (int64_t)m0 * (i2 + (int64_t)g.m[1] * i3);
             if (ell_f32) {
                 float* out = (float*)ell;
 #pragma unroll
-                for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = (float)Pol::to_double(acc[l][dd]);
+                for (int dd = 0; dd < W; ++dd) if (dd >= dlo && dd <= dhi) out[(int64_t)(slot0 + dd) * N + row] = (float)Pol::to_double(acc[l][dd]);
             } else {
                 double* out = (double*)ell;
 #pragma unroll
-                for (int dd = 0; dd < W; ++dd) out[(int64_t)(slot0 + dd) * N + row] = Pol::to_double(acc[l][dd]);
+                for (int dd = 0; dd < W; ++dd) if (dd >= dlo && dd <= dhi) out[(int64_t)(slot0 + dd) * N + row] = Pol::to_double(acc[l][dd]);
             }
         } else {
 #pragma unroll
