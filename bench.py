@@ -179,14 +179,36 @@ def _boxes(prob, M, surrogate, domains="common"):
     return boxes, int(np.prod(ns))
 
 
-def stage_fmas(prob, M, surrogate, domains="common"):
-    """FP64 FMAs executed by stage Z / Y / X (per launch), closed form over the boxes."""
+def box_sym(n_boxes, surrogate, symmetric=True):
+    """Symmetry mode of each explicit box (the order of `_boxes`): +1 computes the upper offsets,
+    -1 the lower ones, 0 all.  The stiffness matrix is symmetric; exact assembly (or a surrogate
+    without Omega~) mirrors over the whole patch, the surrogate over the two frame slabs normal to
+    the slowest direction (the first two boxes).  Off with the tensor-core stage X."""
+    sym = [0] * n_boxes
+    if not symmetric:
+        return sym
+    if not surrogate or n_boxes == 1:
+        sym[0] = 1
+    elif n_boxes >= 2:
+        sym[0], sym[1] = 1, -1
+    return sym
+
+
+def stage_fmas(prob, M, surrogate, domains="common", symmetric=True):
+    """Multiply-adds that stage Z / Y / X need (per launch), closed form over the boxes.  A symmetric
+    box needs the partial sums of the offsets on its side only: stage Z the delta_2 of that sign,
+    stage Y with delta_2 = 0 the delta_1 of that sign, stage X on the centre line (delta_2 = delta_1
+    = 0) the delta_0 of that sign."""
     p, dim = prob.p, prob.dim
     Q, Wd = p + 1, 2 * p + 1
     n_el = list(prob.n_el)
 
-    def nvalid(i, ne):        # elements of supp(B_i) inside the mesh
-        return sum(1 for a in range(p + 1) if 0 <= i - p + a < ne)
+    def cnt(i, ne, mode):     # Gauss point x partner pairs of row i: mode 0 all, +1 delta >= 0, -1 delta <= 0
+        n = 0
+        for a in range(p + 1):
+            if 0 <= i - p + a < ne:
+                n += Q * (Q if mode == 0 else (a + 1 if mode > 0 else p - a + 1))
+        return n
 
     def G(lo, R, ne):         # Gauss points of the box in one direction
         elo = max(0, lo - p)
@@ -194,19 +216,26 @@ def stage_fmas(prob, M, surrogate, domains="common"):
         return (ehi - elo + 1) * Q
 
     boxes, nsamp = _boxes(prob, M, surrogate, domains)
+    syms = box_sym(len(boxes), surrogate and nsamp > 0, symmetric)
     samp_box = [(2 * p, 1)] * dim           # every sample box: one row, p + 1 elements per direction
     tot = {"stage_z": 0, "stage_y": 0, "stage_x": 0}
-    for bx, mult in [(b, 1) for b in boxes] + ([(samp_box, nsamp)] if nsamp else []):
-        sv = [sum(nvalid(i, n_el[d]) for i in range(bx[d][0], bx[d][0] + bx[d][1])) for d in range(dim)]
+    items = [(b, 1, sg) for b, sg in zip(boxes, syms)] + ([(samp_box, nsamp, 0)] if nsamp else [])
+    for bx, mult, sg in items:
+        rows = [range(bx[d][0], bx[d][0] + bx[d][1]) for d in range(dim)]
+        s_all = [sum(cnt(i, n_el[d], 0) for i in rows[d]) for d in range(dim)]
+        s_sym = [sum(cnt(i, n_el[d], sg) for i in rows[d]) for d in range(dim)]
         g = [G(bx[d][0], bx[d][1], n_el[d]) for d in range(dim)]
         R = [bx[d][1] for d in range(dim)]
+        # lines of the slower offsets: (full, centre) = delta strictly on the box's side, delta = 0
+        nf, nc = (Wd, 0) if sg == 0 else (p, 1)
         if dim == 3:
-            tot["stage_z"] += mult * 8 * Q * Q * sv[2] * g[1] * g[0]
-            tot["stage_y"] += mult * 9 * Q * Q * sv[1] * (R[2] * Wd) * g[0]
-            tot["stage_x"] += mult * 4 * Q * Q * sv[0] * (R[2] * Wd) * (R[1] * Wd)
+            tot["stage_z"] += mult * 8 * s_sym[2] * g[1] * g[0]
+            tot["stage_y"] += mult * 9 * g[0] * R[2] * (nf * s_all[1] + nc * s_sym[1])
+            tot["stage_x"] += mult * 4 * R[2] * (nf * R[1] * Wd * s_all[0]
+                                                 + nc * R[1] * (nf * s_all[0] + nc * s_sym[0]))
         else:
-            tot["stage_y"] += mult * 4 * Q * Q * sv[1] * g[0]
-            tot["stage_x"] += mult * 4 * Q * Q * sv[0] * (R[1] * Wd)
+            tot["stage_y"] += mult * 4 * g[0] * s_sym[1]
+            tot["stage_x"] += mult * 4 * R[1] * (nf * s_all[0] + nc * s_sym[0])
     return tot
 
 
@@ -220,7 +249,8 @@ def kernel_work(prob, wl, arith: str, surrogate=True, domains="common"):
     """Per-launch algorithmic work: flops of the contraction stages in the arithmetic
     they run in, bytes for the SpMV."""
     esz = 8 if wl.dtype == "f64" else 4
-    fm = stage_fmas(prob, wl.M, surrogate, domains)
+    # the tensor-core stage X (df64_tc, bf16x3) writes every offset: no symmetric boxes
+    fm = stage_fmas(prob, wl.M, surrogate, domains, symmetric=arith not in ("df64_tc", "bf16x3"))
     if arith == "fp64":
         work = {k: {"bound": "alu", "pipe": "fp64", "flops": 2.0 * v} for k, v in fm.items() if v}
     elif arith == "df64":

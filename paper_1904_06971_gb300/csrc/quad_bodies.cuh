@@ -74,15 +74,22 @@ __device__ __forceinline__ void load_run(const S* p, S* v)
 // stage Z: contract direction 2.  HALF selects combos 0..3 or 4..7 (two launches
 // keep the accumulators of one thread small enough for two blocks per SM).
 // ---------------------------------------------------------------------------
-template <class Pol, int P, int HALF>
-__device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch,
-                                             int64_t blk)
+// SYM is the box's symmetry mode (Box::sym) as a template argument, so that the offsets a
+// symmetric box skips leave no branch in the unrolled offset loops; SYM = 2 reads it at run time
+// (the FP32 body, whose three copies would spill at its three-blocks-per-SM register budget).
+template <int SYM, int P>
+__device__ __forceinline__ bool z_skip(int sym, int dd)
+{
+    if constexpr (SYM == 2) return (sym > 0 && dd < P) || (sym < 0 && dd > P);
+    else return (SYM > 0 && dd < P) || (SYM < 0 && dd > P);
+}
+
+template <class Pol, int P, int HALF, int SYM>
+__device__ __forceinline__ void stage_z_box(const Tables& T, const Box& b, double* scratch, int64_t blk)
 {
     using S = typename Pol::store;
     using A = typename Pol::acc;
     constexpr int Q = P + 1, W = 2 * P + 1, TT = Q * Q;
-    Box b;
-    get_box(bs, 3, P, 1, blk, b);
     const int64_t G0 = (int64_t)b.E[0] * Q, G1 = (int64_t)b.E[1] * Q, G2 = (int64_t)b.E[2] * Q;
     const int64_t plane = G0 * G1;
     const int64_t item = (blk - b.blk[1]) * kBlock + threadIdx.x;
@@ -115,7 +122,7 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
             else { c0 = C[2 * fs + o]; c1 = C[4 * fs + o]; c2 = C[5 * fs + o]; c3 = c0; }
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
-                if ((b.sym > 0 && dd < P) || (b.sym < 0 && dd > P)) continue;   // symmetric: one sign of delta_2
+                if (z_skip<SYM, P>(b.sym, dd)) continue;   // symmetric: one sign of delta_2
                 S x00, x01, x10, x11;
                 load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
                 if (HALF == 0) {
@@ -148,7 +155,7 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
             if (r + 1 < Q) load_c(r + 1, n0, n1, n2, n3);
 #pragma unroll
             for (int dd = a; dd <= a + P; ++dd) {
-                if ((b.sym > 0 && dd < P) || (b.sym < 0 && dd > P)) continue;   // symmetric: one sign of delta_2
+                if (z_skip<SYM, P>(b.sym, dd)) continue;   // symmetric: one sign of delta_2
                 S x00, x01, x10, x11;
                 load_pats(Xi + (dd * TT + t) * 4, x00, x01, x10, x11);
                 if (HALF == 0) {
@@ -172,8 +179,20 @@ __device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, cons
     for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int dd = 0; dd < W; ++dd)
-            if (!((b.sym > 0 && dd < P) || (b.sym < 0 && dd > P)))
+            if (!z_skip<SYM, P>(b.sym, dd))
                 T1[((int64_t)(4 * HALF + k) * P3 + (int64_t)i3l * W + dd) * plane + pp] = Pol::to_store(acc[dd][k]);
+}
+
+template <class Pol, int P, int HALF>
+__device__ __forceinline__ void stage_z_body(const Geo& g, const Tables& T, const BoxSet& bs, double* scratch,
+                                             int64_t blk)
+{
+    Box b;
+    get_box(bs, 3, P, 1, blk, b);
+    if constexpr (Pol::kind == kArithF32) stage_z_box<Pol, P, HALF, 2>(T, b, scratch, blk);
+    else if (b.sym > 0) stage_z_box<Pol, P, HALF, 1>(T, b, scratch, blk);
+    else if (b.sym < 0) stage_z_box<Pol, P, HALF, -1>(T, b, scratch, blk);
+    else stage_z_box<Pol, P, HALF, 0>(T, b, scratch, blk);
 }
 
 // ---------------------------------------------------------------------------

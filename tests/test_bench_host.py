@@ -52,11 +52,31 @@ def test_max_over_ranks_gloo_two_ranks():
     assert [o[2] for o in out] == [100.0, 100.0]      # 100 units x 2 ranks / 2 s
 
 
-def _brute_stage_fmas(prob, M, surrogate, domains="common"):
-    """Count the FMAs of the three stage loops literally (tiny problems)."""
+def _needed(prefix, sym):
+    """Whether the partial sum of the offset components `prefix` (slowest direction first) is needed
+    by some offset the box computes: sym +1 keeps the offsets at or after the centre in colexicographic
+    slot order (first non-zero component from the slowest direction positive), -1 those at or before."""
+    if sym == 0:
+        return True
+    for d in prefix:
+        if d != 0:
+            return (d > 0) == (sym > 0)
+    return True
+
+
+def _brute_stage_fmas(prob, M, surrogate, domains="common", symmetric=True):
+    """Count the multiply-adds the three stage loops need literally (tiny problems)."""
     p, dim = prob.p, prob.dim
     Q, Wd = p + 1, 2 * p + 1
     boxes, ns = bench._boxes(prob, M, surrogate, domains)
+    # symmetric stiffness: exact (or no Omega~) over the whole patch, else the two slabs normal to
+    # the slowest direction, the low one upper offsets and the high one lower
+    syms = [0] * len(boxes)
+    if symmetric:
+        if not ns:
+            syms[0] = 1
+        else:
+            syms[0], syms[1] = 1, -1
     if ns:
         if domains == "per_offset":
             samples = [po.union_samples(p, prob.m[d], M) for d in range(dim)]
@@ -72,15 +92,16 @@ def _brute_stage_fmas(prob, M, surrogate, domains="common"):
         import itertools
         for c in itertools.product(*samples):
             boxes = boxes + [[(ci, 1) for ci in c]]
+            syms = syms + [0]
     tot = {"stage_z": 0, "stage_y": 0, "stage_x": 0}
-    for bx in boxes:
+    for bx, sym in zip(boxes, syms):
         G = []
         for d in range(dim):
             lo, R = bx[d]
             elo, ehi = max(0, lo - p), min(prob.n_el[d] - 1, lo + R - 1)
             G.append((ehi - elo + 1) * Q)
 
-        def per_row(i, d):
+        def per_row(i, d, keep):
             n = 0
             for t in range(Q * Q):
                 e = i - p + t // Q
@@ -88,17 +109,28 @@ def _brute_stage_fmas(prob, M, surrogate, domains="common"):
                     continue
                 for dd in range(Wd):
                     dl = dd - p
-                    if max(0, dl) <= t // Q <= p + min(0, dl):
+                    if max(0, dl) <= t // Q <= p + min(0, dl) and keep(dl):
                         n += 1
             return n
         rows = [range(bx[d][0], bx[d][0] + bx[d][1]) for d in range(dim)]
+        offs = range(-p, p + 1)
         if dim == 3:
-            tot["stage_z"] += 8 * sum(per_row(i, 2) for i in rows[2]) * G[1] * G[0]
-            tot["stage_y"] += 9 * sum(per_row(i, 1) for i in rows[1]) * bx[2][1] * Wd * G[0]
-            tot["stage_x"] += 4 * sum(per_row(i, 0) for i in rows[0]) * bx[2][1] * Wd * bx[1][1] * Wd
+            tot["stage_z"] += 8 * sum(per_row(i, 2, lambda d2: _needed((d2,), sym)) for i in rows[2]) * G[1] * G[0]
+            for _ in rows[2]:
+                for d2 in offs:
+                    tot["stage_y"] += 9 * sum(per_row(i, 1, lambda d1: _needed((d2, d1), sym))
+                                              for i in rows[1]) * G[0]
+                    for _ in rows[1]:
+                        for d1 in offs:
+                            if _needed((d2, d1), sym):
+                                tot["stage_x"] += 4 * sum(per_row(i, 0, lambda d0: _needed((d2, d1, d0), sym))
+                                                          for i in rows[0])
         else:
-            tot["stage_y"] += 4 * sum(per_row(i, 1) for i in rows[1]) * G[0]
-            tot["stage_x"] += 4 * sum(per_row(i, 0) for i in rows[0]) * bx[1][1] * Wd
+            tot["stage_y"] += 4 * sum(per_row(i, 1, lambda d1: _needed((d1,), sym)) for i in rows[1]) * G[0]
+            for _ in rows[1]:
+                for d1 in offs:
+                    if _needed((d1,), sym):
+                        tot["stage_x"] += 4 * sum(per_row(i, 0, lambda d0: _needed((d1, d0), sym)) for i in rows[0])
     return tot
 
 
@@ -108,11 +140,24 @@ def _brute_stage_fmas(prob, M, surrogate, domains="common"):
     (W.Problem(dim=2, p=2, n_el=(20, 23)), 4, True, "common"),
     (W.Problem(dim=3, p=2, n_el=(13, 12, 14)), 3, True, "per_offset"),
     (W.Problem(dim=2, p=3, n_el=(25, 22)), 4, True, "per_offset"),
+    (W.Problem(dim=2, p=2, n_el=(7, 9)), 2, False, "common"),
+    (W.Problem(dim=3, p=2, n_el=(5, 4, 6)), 2, True, "common"),      # no Omega~: the whole patch
 ])
-def test_stage_fma_model_matches_loop_count(prob, M, surr, domains):
-    got = bench.stage_fmas(prob, M, surr, domains)
-    ref = _brute_stage_fmas(prob, M, surr, domains)
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_stage_fma_model_matches_loop_count(prob, M, surr, domains, symmetric):
+    got = bench.stage_fmas(prob, M, surr, domains, symmetric)
+    ref = _brute_stage_fmas(prob, M, surr, domains, symmetric)
     assert got == ref
+
+
+def test_symmetric_boxes_need_about_half_the_offsets():
+    # the exact 3-D patch needs (S + 1) / 2 of the S offsets in stage X, up to the boundary rows
+    prob = W.Problem(dim=3, p=2, n_el=(9, 8, 10))
+    full = bench.stage_fmas(prob, 2, False, symmetric=False)
+    half = bench.stage_fmas(prob, 2, False, symmetric=True)
+    S = 5 ** 3
+    assert half["stage_x"] < full["stage_x"] * ((S + 1) / (2 * S) + 0.05)
+    assert half["stage_x"] > full["stage_x"] * ((S + 1) / (2 * S) - 0.05)
 
 
 def test_reference_arm_prints_one_json_line():
