@@ -307,6 +307,20 @@ def test_full_size_surrogate_sampled_rows(iga, wl, arith):
         worst = max(worst, d)
     # frame rows are exact quadrature rows, symmetric only up to the rounding of the contractions
     assert worst <= tol * scale
+    if arith in ("df64", "fp32"):
+        # the two frame slabs normal to the slowest direction compute one half of their offsets and
+        # mirror the other (A_ij = A_ji): the low slab's lower slots and the high slab's upper slots
+        # equal their partners' (rows of the same slab) bit for bit
+        k0, k1 = oracle.omega_box(prob.p, int(m[-1]))
+        mi_t = torch.from_numpy(mi).cuda()
+        m_t = torch.from_numpy(m).cuda()
+        stride = torch.from_numpy(np.cumprod([1] + list(m[:-1]))).cuda()
+        low, high = mi_t[:, -1] < k0, mi_t[:, -1] > k1
+        for s in list(range(prob.S // 2)) + list(range(prob.S // 2 + 1, prob.S)):
+            mj = mi_t + torch.from_numpy(offs[s]).cuda()
+            ok = ((mj >= 0) & (mj < m_t)).all(dim=1) & (low if s < prob.S // 2 else high)
+            j = (mj * stride).sum(dim=1)
+            assert torch.equal(vals[s][ok], vals[prob.S - 1 - s][j[ok]]), s
     A.destroy()
 
 
@@ -336,6 +350,18 @@ def test_full_size_exact_sampled_rows(iga, wl, arith):
         j = torch.from_numpy(oracle.surrogate.flat_index(mj[ok], m)).cuda()
         worst = max(worst, (vals[s, i] - vals[prob.S - 1 - s, j]).abs().max().item())
     assert worst <= TOL64 * scale
+    if arith != "df64_tc":
+        # the stages compute the upper offsets only and the lower half is their mirror (A_ij = A_ji):
+        # every lower slot equals its partner bit for bit, and is 0 where the partner is outside
+        mi_t = torch.from_numpy(mi).cuda()
+        m_t = torch.from_numpy(m).cuda()
+        stride = torch.from_numpy(np.cumprod([1] + list(m[:-1]))).cuda()
+        for s in range(prob.S // 2):
+            mj = mi_t + torch.from_numpy(offs[s]).cuda()
+            ok = ((mj >= 0) & (mj < m_t)).all(dim=1)
+            j = (mj * stride).sum(dim=1)
+            assert torch.equal(vals[s][ok], vals[prob.S - 1 - s][j[ok]]), s
+            assert bool((vals[s][~ok] == 0).all()), s
     A.destroy()
 
 
