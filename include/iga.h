@@ -132,9 +132,16 @@ typedef struct iga_matrix* iga_matrix_t;   /* opaque; owns device storage */
 /*
  * Exact assembly (Sec. 6: the matrix A every entry of which comes from
  * quadrature; eq. ChangeOfVars).  Every row is computed by sum-factorised
- * Gauss quadrature on the GPU.
+ * Gauss quadrature on the GPU.  A is symmetric (A_ij = A_ji: the bilinear form
+ * of Sec. 2 with a symmetric coefficient tensor), so the quadrature computes
+ * the upper offsets of every row and the lower ones are copied from the partner
+ * rows: values[s][i] equals values[S-1-s][i + delta_s] bit for bit (except with
+ * IGA_ARITH_BF16X3 / IGA_ARITH_DF64_TC, whose tensor-core stage computes every
+ * offset).
  *   patch, map, kappa: host pointers, read during the call only.
- *   p: degree 1..5.  dtype: IGA_F64 or IGA_F32 (quadrature is FP64 either way).
+ *   p: degree 1..5.  dtype: IGA_F64 or IGA_F32; the contraction arithmetic is the
+ *   one iga_set_arithmetic selects for that dtype (FP64 values: double-float by
+ *   default; FP32 values: FP32).
  *   A: in/out.  *A == NULL: a new matrix is created.  *A != NULL: a matrix
  *   from an earlier call with the same patch, p and dtype, whose storage is
  *   reused (its previous values are overwritten); otherwise IGA_EINVAL.
