@@ -427,7 +427,9 @@ int iga_manufactured_load(const iga_patch_t* patch, int p, const iga_map_t* map,
  *   float), written with the stencil-ELL layout above; the other arguments
  *   are those of iga_assemble_exact and are checked the same way (every map
  *   and coefficient kind, IGA_KAPPA_BSPLINE3 included: its control values are
- *   the caller's device memory), and the result equals its values.
+ *   the caller's device memory).  Its quadrature computes every offset of
+ *   every row (no mirror pass), so its values equal those of iga_assemble_exact
+ *   to rounding, not bit for bit in the lower half.
  * Scratch: one file-scope device array of 64 MiB that every GPU which loads
  * this library reserves until the process exits.  A patch whose quadrature
  * scratch exceeds 64 MiB is rejected with IGA_EUNSUPPORTED before any work
