@@ -250,10 +250,15 @@ def kernel_work(prob, wl, arith: str, surrogate=True, domains="common"):
     they run in, bytes for the SpMV."""
     esz = 8 if wl.dtype == "f64" else 4
     # the tensor-core stage X (df64_tc, bf16x3) writes every offset: no symmetric boxes
-    fm = stage_fmas(prob, wl.M, surrogate, domains, symmetric=arith not in ("df64_tc", "bf16x3"))
+    tc = arith in ("df64_tc", "bf16x3")
+    fm = stage_fmas(prob, wl.M, surrogate, domains, symmetric=not tc)
+    if tc:
+        # stage X runs on the tensor cores (no FP32-pipe figure); stages Z and Y in the CUDA-core
+        # arithmetic of the mode: double-float for df64_tc, FP32 for bf16x3
+        fm = {k: v for k, v in fm.items() if k != "stage_x"}
     if arith == "fp64":
         work = {k: {"bound": "alu", "pipe": "fp64", "flops": 2.0 * v} for k, v in fm.items() if v}
-    elif arith == "df64":
+    elif arith in ("df64", "df64_tc"):
         work = {k: {"bound": "alu", "pipe": "fp32 (double-float)", "flops": float(DF64_FLOPS_PER_MAC) * v}
                 for k, v in fm.items() if v}
     else:

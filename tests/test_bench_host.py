@@ -160,6 +160,26 @@ def test_symmetric_boxes_need_about_half_the_offsets():
     assert half["stage_x"] > full["stage_x"] * ((S + 1) / (2 * S) - 0.05)
 
 
+def test_kernel_work_counts_every_offset_with_the_tensor_core_stage():
+    # the tensor-core stage X writes every offset of its rows, so the assembly uses no symmetric
+    # boxes and stages Z and Y count every offset, in the arithmetic they run in; the CUDA-core
+    # modes count the needed half
+    wl = W.CFG_3D_P4_F64
+    prob = W.Problem(dim=3, p=2, n_el=(13, 12, 14))
+    full = bench.stage_fmas(prob, wl.M, True, symmetric=False)
+    half = bench.stage_fmas(prob, wl.M, True, symmetric=True)
+    for arith, want in (("df64_tc", full), ("bf16x3", full), ("df64", half), ("fp64", half), ("fp32", half)):
+        work = bench.kernel_work(prob, wl, arith, surrogate=True)
+        per_mac = bench.DF64_FLOPS_PER_MAC if arith in ("df64", "df64_tc") else 2.0
+        for k in ("stage_z", "stage_y"):
+            assert work[k]["flops"] == per_mac * want[k], (arith, k)
+        # stage X: on the tensor cores no FP32-pipe figure, else the CUDA-core count
+        if arith in ("df64_tc", "bf16x3"):
+            assert "stage_x" not in work
+        else:
+            assert work["stage_x"]["flops"] == per_mac * want["stage_x"]
+
+
 def test_reference_arm_prints_one_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "3", "--workload", W.CFG_2D_P2.name, "--ref-rows", "64"],
